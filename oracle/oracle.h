@@ -1,0 +1,74 @@
+/* CPU oracle for the graph-build and PageRank path.  TEST INFRASTRUCTURE ONLY:
+ * tests, the smoke check and the benchmark's CPU-baseline leg use it; the
+ * library never does.  Plain single-threaded C, FP64, no blocking, fusion or
+ * reordering beyond the definitions below, and no code shared with the CUDA
+ * path.
+ *
+ * What it computes (the paper names PageRank and personalised PageRank among
+ * its graph methods, section 4 Table "snap_methods", and times them in
+ * section 6, but prints no formula; the readings below are the standard
+ * definition with the choices the benchmark configurations fix):
+ *
+ *   Graph: a simple directed graph (section 3, the TNGraph container, and
+ *   section 5, "Representation of Graphs and Networks": no multi-edges,
+ *   edges are (source, destination) pairs).  From a raw COO stream, E is the
+ *   set of distinct pairs (u, v) with u != v.  The in-adjacency of each node
+ *   is kept sorted (section 5: adjacency vectors are sorted), giving the CSC
+ *   arrays col_ptr[n + 1], row_idx[m] (sources grouped by destination, each
+ *   group ascending) and outdeg[n].
+ *
+ *   PageRank with damping d and teleport vector t (sum 1):
+ *     D_k      = sum over u with outdeg(u) = 0 of x_k[u]
+ *     x_{k+1}[v] = (1 - d) t[v] + d ( sum_{(u, v) in E} x_k[u] / outdeg(u) + D_k t[v] )
+ *   Plain PageRank: t = x_0 = 1/N everywhere.  Personalised PageRank for seed
+ *   s: t = x_0 = e_s (dangling mass returns to the seed).
+ *
+ * Parity pins for every function are in the repository's CPU test suite
+ * (closed forms, brute force, dense solves, invariants).
+ */
+#ifndef GPR_ORACLE_H
+#define GPR_ORACLE_H
+
+#include <stdint.h>
+
+/* Build the CSC of the simple directed graph of a raw COO stream.
+ * row_idx needs room for m_raw entries.  Returns m (distinct non-loop
+ * edges) or -1 if an id is outside [0, n) or n <= 0, -2 on allocation
+ * failure. */
+int64_t oracle_build_csc(int32_t n, int64_t m_raw, const int32_t* src, const int32_t* dst,
+                         int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg);
+
+/* Power iteration from x0 with teleport t (both length n, FP64).
+ * Runs max_iters steps, or stops after the first step k with
+ * (d / (1 - d)) * ||x_{k+1} - x_k||_1 <= tol when tol > 0.
+ * resid (nullable, length max_iters) receives ||x_{k+1} - x_k||_1 per step.
+ * Returns the number of steps run, or -1 on bad arguments. */
+int32_t oracle_pagerank(int32_t n, const int32_t* col_ptr, const int32_t* row_idx,
+                        const int32_t* outdeg, double d, const double* t, const double* x0,
+                        int32_t max_iters, double tol, double* x_out, double* resid);
+
+/* Plain PageRank: t = x0 = 1/N, fixed iteration count. */
+int32_t oracle_pagerank_uniform(int32_t n, const int32_t* col_ptr, const int32_t* row_idx,
+                                const int32_t* outdeg, double d, int32_t iters, double* x_out,
+                                double* resid);
+
+/* Personalised PageRank for one seed node: t = x0 = e_seed. */
+int32_t oracle_ppr(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
+                   double d, int32_t seed, int32_t max_iters, double tol, double* x_out);
+
+/* Sampled rows of the CSC straight from the raw COO, for graphs too large to
+ * sort on the host: for each of the k listed destination nodes, the sorted
+ * distinct sources u != v.  rows must be distinct.  row_off has k + 1
+ * entries; row_src has room for cap entries.  Returns the total number of
+ * sources written, or -1 on bad arguments, -2 if cap is too small. */
+int64_t oracle_sample_in_rows(int32_t n, int64_t m_raw, const int32_t* src, const int32_t* dst,
+                              int32_t k, const int32_t* rows, int64_t* row_off, int32_t* row_src,
+                              int64_t cap);
+
+/* Out-degree (distinct destinations v != u) of each of the k listed nodes,
+ * straight from the raw COO.  nodes must be distinct.  Returns 0, or -1 on
+ * bad arguments, -2 on allocation failure. */
+int32_t oracle_sample_outdeg(int32_t n, int64_t m_raw, const int32_t* src, const int32_t* dst,
+                             int32_t k, const int32_t* nodes, int32_t* outdeg_out);
+
+#endif /* GPR_ORACLE_H */

@@ -1,0 +1,350 @@
+"""Pins for the CPU oracle against what mathematics fixes (no GPU).
+
+The paper prints no PageRank values, no worked example and no error bound
+(section 6 reports only timings), so every pin here is a closed form, a brute
+force, an independent dense linear solve or an invariant.  Each is chosen so
+that a plausible slip in the oracle (a dropped dangling term, a wrong
+teleport, a transposed adjacency, an off-by-one in the CSC) fails one of them.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+D = 0.85
+
+
+# ---------------------------------------------------------------- helpers --
+
+def brute_csc(n, src, dst):
+    """Simple directed graph by Python sets: distinct (u, v), u != v."""
+    edges = sorted({(int(u), int(v)) for u, v in zip(src, dst) if u != v}, key=lambda e: (e[1], e[0]))
+    col_ptr = [0] * (n + 1)
+    for _, v in edges:
+        col_ptr[v + 1] += 1
+    for v in range(n):
+        col_ptr[v + 1] += col_ptr[v]
+    row_idx = [u for u, _ in edges]
+    outdeg = [0] * n
+    for u, _ in edges:
+        outdeg[u] += 1
+    return np.array(col_ptr), np.array(row_idx, dtype=np.int64), np.array(outdeg), edges
+
+
+def dense_google(n, edges, t):
+    """Column-stochastic M with M[v, u] = 1/outdeg(u) for u -> v and the
+    column of a dangling u replaced by the teleport vector t."""
+    outdeg = np.zeros(n)
+    for u, _ in edges:
+        outdeg[u] += 1
+    M = np.zeros((n, n))
+    for u, v in edges:
+        M[v, u] += 1.0 / outdeg[u]
+    for u in range(n):
+        if outdeg[u] == 0:
+            M[:, u] = t
+    return M
+
+
+def dense_fixed_point(n, edges, t, d=D):
+    """Solve (I - d M) x = (1 - d) t."""
+    M = dense_google(n, edges, t)
+    return np.linalg.solve(np.eye(n) - d * M, (1.0 - d) * t)
+
+
+def dense_power(n, edges, t, x0, k, d=D):
+    M = dense_google(n, edges, t)
+    x = x0.copy()
+    for _ in range(k):
+        x = (1.0 - d) * t + d * (M @ x)
+    return x
+
+
+def csc_from_edges(n, edges):
+    src = np.array([u for u, _ in edges], np.int32)
+    dst = np.array([v for _, v in edges], np.int32)
+    return oracle.build_csc(n, src, dst)
+
+
+def random_coo(rng, n, m_raw, p_loop=0.1, p_dup=0.2):
+    src = rng.integers(0, n, m_raw)
+    dst = rng.integers(0, n, m_raw)
+    for i in range(m_raw):
+        r = rng.random()
+        if r < p_loop:
+            dst[i] = src[i]
+        elif r < p_loop + p_dup and i > 0:
+            j = rng.integers(0, i)
+            src[i], dst[i] = src[j], dst[j]
+    return src.astype(np.int32), dst.astype(np.int32)
+
+
+# ------------------------------------------------------------- CSC build --
+
+@pytest.mark.parametrize("seed", range(40))
+def test_build_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 14))
+    m_raw = int(rng.integers(0, 70))
+    src, dst = random_coo(rng, n, m_raw)
+    g = oracle.build_csc(n, src, dst)
+    cp, ri, od, edges = brute_csc(n, src, dst)
+    assert g.m == len(edges)
+    np.testing.assert_array_equal(g.col_ptr, cp)
+    np.testing.assert_array_equal(g.row_idx, ri)
+    np.testing.assert_array_equal(g.outdeg, od)
+    assert g.outdeg.sum() == g.m == g.col_ptr[-1]
+
+
+def test_build_invariant_under_coo_order_duplicates_and_loops():
+    rng = np.random.default_rng(7)
+    n, m_raw = 50, 400
+    src, dst = random_coo(rng, n, m_raw, p_loop=0.0, p_dup=0.0)
+    g0 = oracle.build_csc(n, src, dst)
+    perm = rng.permutation(m_raw)
+    loops = rng.integers(0, n, 60).astype(np.int32)
+    src2 = np.concatenate([src[perm], src[:100], loops])
+    dst2 = np.concatenate([dst[perm], dst[:100], loops])
+    g1 = oracle.build_csc(n, src2, dst2)
+    np.testing.assert_array_equal(g0.col_ptr, g1.col_ptr)
+    np.testing.assert_array_equal(g0.row_idx, g1.row_idx)
+    np.testing.assert_array_equal(g0.outdeg, g1.outdeg)
+
+
+def test_build_edge_cases():
+    # empty edge list: all nodes isolated
+    g = oracle.build_csc(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert g.m == 0 and list(g.col_ptr) == [0] * 6 and list(g.outdeg) == [0] * 5
+    # only self-loops
+    g = oracle.build_csc(3, np.array([0, 1, 2, 2], np.int32), np.array([0, 1, 2, 2], np.int32))
+    assert g.m == 0
+    # one node
+    g = oracle.build_csc(1, np.array([0], np.int32), np.array([0], np.int32))
+    assert g.m == 0 and list(g.col_ptr) == [0, 0]
+    # largest id n - 1
+    g = oracle.build_csc(4, np.array([3, 3, 0], np.int32), np.array([0, 0, 3], np.int32))
+    assert list(g.col_ptr) == [0, 1, 1, 1, 2] and list(g.row_idx) == [3, 0] and list(g.outdeg) == [1, 0, 0, 1]
+
+
+def test_build_rejects_out_of_range_ids():
+    for s, d in [([0, 5], [1, 1]), ([0, 1], [1, -1]), ([-1], [0])]:
+        with pytest.raises(ValueError):
+            oracle.build_csc(5, np.array(s, np.int32), np.array(d, np.int32))
+
+
+def test_sampled_rows_and_outdeg_match_full_build():
+    src, dst = gen.rmat_coo(3000, 40000, seed=11)
+    g = oracle.build_csc(3000, src, dst)
+    rows = np.array([0, 5, 17, 2999, 1234, 777], np.int32)
+    lists = oracle.sample_in_rows(3000, src, dst, rows)
+    for v, lst in zip(rows, lists):
+        np.testing.assert_array_equal(lst, g.row_idx[g.col_ptr[v]:g.col_ptr[v + 1]])
+    od = oracle.sample_outdeg(3000, src, dst, rows)
+    np.testing.assert_array_equal(od, g.outdeg[rows])
+
+
+# -------------------------------------------------------- closed forms --
+
+@pytest.mark.parametrize("N", [1, 2, 3, 10, 257])
+def test_cycle_uniform_every_iteration(N):
+    edges = [(i, (i + 1) % N) for i in range(N)] if N > 1 else []
+    g = csc_from_edges(N, edges)
+    for k in [0, 1, 2, 7, 50]:
+        x = oracle.pagerank_uniform(g, D, k)
+        np.testing.assert_allclose(x, 1.0 / N, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [2, 3, 6, 20])
+def test_complete_digraph_uniform(N):
+    edges = [(u, v) for u in range(N) for v in range(N) if u != v]
+    g = csc_from_edges(N, edges)
+    x = oracle.pagerank_uniform(g, D, 30)
+    np.testing.assert_allclose(x, 1.0 / N, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 40])
+def test_in_star_fixed_point(N):
+    # leaves -> hub 0; the hub is dangling.  x_hub = (1 + (N-1)d) / (N + (N-1)d)
+    edges = [(i, 0) for i in range(1, N)]
+    g = csc_from_edges(N, edges)
+    x = oracle.pagerank_uniform(g, D, 250)
+    hub = (1 + (N - 1) * D) / (N + (N - 1) * D)
+    leaf = (1 - hub) / (N - 1)
+    assert abs(x[0] - hub) < 1e-13
+    np.testing.assert_allclose(x[1:], leaf, rtol=0, atol=1e-13)
+
+
+def test_in_star_two_nodes_value():
+    # N = 2, d = 0.85: 1.85 / 2.85 and 1 / 2.85
+    g = csc_from_edges(2, [(1, 0)])
+    x = oracle.pagerank_uniform(g, D, 250)
+    assert abs(x[0] - 1.85 / 2.85) < 1e-14 and abs(x[1] - 1.0 / 2.85) < 1e-14
+    assert abs(x[0] - 0.6491228070175439) < 1e-13
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 40])
+def test_out_star_fixed_point(N):
+    # hub 0 -> leaves; the leaves are dangling.  x_hub = 1 / (N + d)
+    edges = [(0, i) for i in range(1, N)]
+    g = csc_from_edges(N, edges)
+    x = oracle.pagerank_uniform(g, D, 250)
+    assert abs(x[0] - 1.0 / (N + D)) < 1e-13
+    np.testing.assert_allclose(x[1:], (N + D - 1) / ((N - 1) * (N + D)), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("N,s", [(5, 0), (7, 3), (30, 29)])
+def test_ppr_cycle_closed_form(N, s):
+    # x_v = (1 - d) d^j / (1 - d^N), j = forward distance from s to v
+    edges = [(i, (i + 1) % N) for i in range(N)]
+    g = csc_from_edges(N, edges)
+    x, k = oracle.ppr(g, s, D, 400)
+    j = (np.arange(N) - s) % N
+    np.testing.assert_allclose(x, (1 - D) * D ** j / (1 - D ** N), rtol=0, atol=1e-14)
+
+
+def test_ppr_dangling_mass_returns_to_seed():
+    # 0 -> 1, 1 dangling, seed 0: x0 = (1-d) + d x1, x1 = d x0 -> x0 = (1-d)/(1-d^2)
+    g = csc_from_edges(3, [(0, 1)])
+    x, _ = oracle.ppr(g, 0, D, 400)
+    assert abs(x[0] - (1 - D) / (1 - D * D)) < 1e-14
+    assert abs(x[1] - D * (1 - D) / (1 - D * D)) < 1e-14
+    assert x[2] == 0.0
+
+
+# --------------------------------------------------------- dense solves --
+
+def _random_small_graph(rng, n):
+    m = int(rng.integers(0, 3 * n + 1))
+    src, dst = random_coo(rng, n, m, p_loop=0.1, p_dup=0.1)
+    _, _, _, edges = brute_csc(n, src, dst)
+    return src, dst, edges
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_fixed_point_matches_dense_solve(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 65))
+    src, dst, edges = _random_small_graph(rng, n)
+    g = oracle.build_csc(n, src, dst)
+    t = np.full(n, 1.0 / n)
+    xs = dense_fixed_point(n, edges, t)
+    x = oracle.pagerank_uniform(g, D, 250)
+    assert np.abs(x - xs).sum() <= 1e-12
+    # personalised, random seed
+    s = int(rng.integers(0, n))
+    e = np.zeros(n)
+    e[s] = 1.0
+    xs = dense_fixed_point(n, edges, e)
+    xp, _ = oracle.ppr(g, s, D, 250)
+    assert np.abs(xp - xs).sum() <= 1e-12
+    # another damping
+    xs = dense_fixed_point(n, edges, t, d=0.5)
+    x = oracle.pagerank(g, d=0.5, iters=120)
+    assert np.abs(x - xs).sum() <= 1e-12
+
+
+@pytest.mark.parametrize("seed", range(15))
+def test_finite_k_matches_dense_power_iteration(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(1, 65))
+    src, dst, edges = _random_small_graph(rng, n)
+    g = oracle.build_csc(n, src, dst)
+    t = np.full(n, 1.0 / n)
+    for k in [1, 2, 5, 50]:
+        x = oracle.pagerank_uniform(g, D, k)
+        xd = dense_power(n, edges, t, t, k)
+        assert np.abs(x - xd).sum() <= 1e-13
+
+
+# ---------------------------------------------------------- invariants --
+
+def test_mass_and_lower_bound_every_iterate():
+    src, dst = gen.rmat_coo(2000, 16000, seed=5)
+    g = oracle.build_csc(2000, src, dst)
+    assert (g.outdeg == 0).any()  # dangling nodes present
+    for k in range(0, 12):
+        x = oracle.pagerank_uniform(g, D, k)
+        assert abs(x.sum() - 1.0) <= 1e-12
+        assert x.min() >= (1 - D) / 2000 - 1e-18
+
+
+def test_geometric_convergence_bound():
+    rng = np.random.default_rng(9)
+    n = 60
+    src, dst, edges = _random_small_graph(rng, n)
+    g = oracle.build_csc(n, src, dst)
+    xs = dense_fixed_point(n, edges, np.full(n, 1.0 / n))
+    for k in range(1, 40):
+        x = oracle.pagerank_uniform(g, D, k)
+        assert np.abs(x - xs).sum() <= 2 * D ** k + 1e-14
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-6, 1e-9])
+def test_tolerance_stop_rule_bounds_error(tol):
+    rng = np.random.default_rng(21)
+    n = 50
+    src, dst, edges = _random_small_graph(rng, n)
+    g = oracle.build_csc(n, src, dst)
+    for s in [0, 7, 49]:
+        e = np.zeros(n)
+        e[s] = 1.0
+        xs = dense_fixed_point(n, edges, e)
+        x, k = oracle.ppr(g, s, D, 1000, tol)
+        assert k < 1000
+        assert np.abs(x - xs).sum() <= tol + 1e-13
+        # and it stopped at the first step that met the rule
+        _, resid, k2 = oracle.pagerank(g, D, 1000, t=e, tol=tol, with_resid=True)
+        assert k2 == k and (D / (1 - D)) * resid[-1] <= tol
+        assert all((D / (1 - D)) * r > tol for r in resid[:-1])
+
+
+def test_per_step_residual_is_l1_change():
+    src, dst = gen.rmat_coo(500, 3000, seed=3)
+    g = oracle.build_csc(500, src, dst)
+    prev = oracle.pagerank_uniform(g, D, 0)
+    _, resid, k = oracle.pagerank(g, D, 6, with_resid=True)
+    for i in range(6):
+        cur = oracle.pagerank_uniform(g, D, i + 1)
+        assert abs(np.abs(cur - prev).sum() - resid[i]) <= 1e-13  # summation order differs
+        prev = cur
+
+
+# ------------------------------------------ planted mistakes are caught --
+
+def _mutant_pagerank(g, iters, mutation):
+    """The oracle's update written out in Python with one deliberate slip,
+    to show the pins above would catch it."""
+    n = g.n
+    x = np.full(n, 1.0 / n)
+    t = np.full(n, 1.0 / n)
+    for _ in range(iters):
+        dang = x[g.outdeg == 0].sum()
+        xn = np.empty(n)
+        for v in range(n):
+            srcs = g.row_idx[g.col_ptr[v]:g.col_ptr[v + 1]]
+            pulled = sum(x[u] / g.outdeg[u] for u in srcs)
+            if mutation == "drop_dangling":
+                xn[v] = (1 - D) * t[v] + D * pulled
+            elif mutation == "teleport_sign":
+                xn[v] = (1 + D) * t[v] + D * (pulled + dang * t[v])
+            elif mutation == "no_outdeg":
+                xn[v] = (1 - D) * t[v] + D * (sum(x[u] for u in srcs) + dang * t[v])
+            else:
+                xn[v] = (1 - D) * t[v] + D * (pulled + dang * t[v])
+        x = xn
+    return x
+
+
+@pytest.mark.parametrize("mutation", ["drop_dangling", "teleport_sign", "no_outdeg"])
+def test_pins_catch_planted_mistakes(mutation):
+    # out-star: dangling leaves and a hub of out-degree N - 1
+    N = 6
+    g = csc_from_edges(N, [(0, i) for i in range(1, N)])
+    x = _mutant_pagerank(g, 250, mutation)
+    ok_hub = abs(x[0] - 1.0 / (N + D)) < 1e-13
+    ok_mass = abs(x.sum() - 1.0) <= 1e-12
+    assert not (ok_hub and ok_mass)
+    # and the unmutated transcription passes the same pins
+    x = _mutant_pagerank(g, 250, "none")
+    assert abs(x[0] - 1.0 / (N + D)) < 1e-13 and abs(x.sum() - 1.0) <= 1e-12
