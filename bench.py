@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark: COO -> CSC graph build + PageRank power iteration on one GB300.
+
+One step = the whole hot path once: graph_build from a raw COO edge stream
+already resident in HBM (pack, radix sort, dedupe, CSC offsets, out-degrees,
+execution layout) followed by `iters` PageRank steps (pull SpMV, fused
+teleport / dangling / residual step, FP64 reductions) and the write-back of
+the rank vector.  Default workload: the Twitter2010-scale stand-in, R-MAT
+scale 25 with edge factor 32 (33.5M ids, 2^30 raw edges), 100 iterations.
+
+value = PageRank GTEPS over the whole step = m * iters / (build + iterate
+time), m the deduplicated edge count.  The JSON line also carries the
+iteration-only rate, the build time, an end-to-end figure through the C-ABI
+with host buffers, a roofline object for the PageRank iteration and the CPU
+oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpr|reference]
+Under torchrun (N > 1) each rank runs an independent replica on its own GPU
+(the plain PageRank path is not sharded); value sums all ranks' edges over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+DAMPING = 0.85
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpr", "reference"], default="gpr")
+    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k"], default="rmat25")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-scale", type=int, default=19)
+    return ap.parse_args()
+
+
+def workload(name):
+    from gen import workloads
+    return {"rmat25": workloads.RMAT_25, "rmat-lj": workloads.RMAT_LJ, "er10k": workloads.ER_10K}[name]
+
+
+def src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1606_07550_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(wl_name):
+    """DRAM bytes per PageRank iteration from a committed ncu summary, or None
+    if the kernels changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d.get(wl_name)
+        if e and e.get("src_hash") == src_hash():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            lines = open(self.f.name).read().strip().splitlines()
+            os.unlink(self.f.name)
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(scale, iters, seed=3):
+    """The CPU oracle as it stands (single-threaded FP64 C), on a bounded
+    sample of the same workload recipe: R-MAT scale `scale`, edge factor 32,
+    build + `iters` iterations.  Returns (GTEPS, seconds, m, description)."""
+    import gen
+    import oracle
+    n = 1 << scale
+    src, dst = gen.rmat_coo(n, 32 * n, seed=seed)
+    t0 = time.perf_counter()
+    g = oracle.build_csc(n, src, dst)
+    oracle.pagerank_uniform(g, DAMPING, iters)
+    dt = time.perf_counter() - t0
+    desc = (f"R-MAT scale {scale}, edge factor 32 ({n} ids, {32 * n} raw edges, m={g.m}), same generator "
+            f"recipe; build + {iters} iterations, single-threaded FP64 oracle")
+    return g.m * iters / dt / 1e9, dt, g.m, desc
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    spec = workload(args.workload)
+    scale = min(args.cpu_sample_scale - 1, spec.scale)
+    for _ in range(args.warmup):
+        cpu_baseline(scale, spec.iters)
+    vals, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, dt, m, desc = cpu_baseline(scale, spec.iters)
+        vals.append(v)
+        secs += dt
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": "PageRank GTEPS", "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": spec.name, "sample": desc, "iters": spec.iters},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def make_coo_device(torch, spec):
+    import gen
+    if spec.kind == "rmat":
+        s = torch.empty(spec.m, dtype=torch.int32, device="cuda")
+        d = torch.empty(spec.m, dtype=torch.int32, device="cuda")
+        perm = torch.from_numpy(gen.permutation(spec.n, spec.seed)).cuda()
+        gen.rmat_coo_dev(spec.n, spec.m, spec.seed, s.data_ptr(), d.data_ptr(), perm.data_ptr(),
+                         stream=torch.cuda.current_stream().cuda_stream, abc=spec.abc)
+        torch.cuda.synchronize()
+        return s, d
+    src, dst = gen.er_gnm(spec.n, spec.m, spec.seed)
+    return torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda()
+
+
+def run_gpr(args, world, rank, local):
+    import torch
+
+    import paper_1606_07550_gb300 as gpr
+
+    torch.cuda.set_device(local)
+    spec = workload(args.workload)
+    iters = spec.iters
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu_baseline:
+        # before any GPU work in this process
+        cpu = cpu_baseline(args.cpu_sample_scale, iters)
+
+    stream = torch.cuda.current_stream()
+    src, dst = make_coo_device(torch, spec)
+    out = torch.empty(spec.n, dtype=torch.float32, device="cuda")
+    L = gpr.lib()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        g = gpr.graph_build(src, dst, spec.n, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        gpr.pagerank(g, out, damping=DAMPING, iters=iters, dtype=gpr.FP32, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        return g
+
+    g = None
+    for _ in range(args.warmup):
+        g = step()
+        inf = g.info()
+        g.free()
+    torch.cuda.synchronize()
+    m = inf.m
+    n = spec.n
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    launches0 = L.gpr_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            g = step(evs[k])
+            g.free()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(world)
+    launches = L.gpr_kernel_launches() - launches0
+    t_build = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    t_iter = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    t_step = sum(e[0].elapsed_time(e[2]) for e in evs) / args.steps
+    t_step_max = max_over_ranks(world, t_step)
+    edges_all = sum_over_ranks(world, float(m))
+    value = edges_all * iters / (t_step_max * 1e-3) / 1e9
+    pr_gteps = m * iters / (t_iter * 1e-3) / 1e9
+
+    # roofline of the PageRank iteration: modelled bytes 8m + 12n + 4 per step
+    bytes_per_iter = 8 * m + 12 * n + 4
+    achieved = bytes_per_iter * iters / (t_iter * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    tr = recorded_traffic(spec.name)
+
+    # end to end through the C-ABI with host buffers: H2D of the COO and D2H
+    # of the ranks inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        hs = torch.empty(spec.m, dtype=torch.int32, pin_memory=True)
+        hd = torch.empty(spec.m, dtype=torch.int32, pin_memory=True)
+        hs.copy_(src)
+        hd.copy_(dst)
+        hout = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        del src, dst
+        torch.cuda.empty_cache()
+        g = gpr.graph_build(hs, hd, n, stream=stream)
+        gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream)
+        g.free()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g = gpr.graph_build(hs, hd, n, stream=stream)
+            gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream)
+            g.free()
+        torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / args.e2e_steps
+        t_e2e = max_over_ranks(world, t_e2e)
+        e2e = {"value": edges_all * iters / t_e2e / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": 8 * spec.m, "d2h_bytes_per_step": 4 * n, "ms_per_step": t_e2e * 1e3}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "PageRank GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": spec.name, "n": n, "m_raw": spec.m, "m": m, "iters": iters, "damping": DAMPING,
+            "step": "graph_build (COO resident in HBM) + PageRank iterations + rank write-back",
+            "value_counts": "m * iters / (build + iterate) per step",
+            "l2": "inputs larger than L2 (COO 8 GiB, CSC 4 GiB per replica)" if spec.m > (1 << 25) else
+                  "small graph: L2-resident (launch-bound)",
+            "parallelism": f"replicas x{world}",
+        },
+        "build_ms": t_build, "iterate_ms": t_iter, "pagerank_gteps": pr_gteps,
+        "build_edges_per_s": spec.m / (t_build * 1e-3),
+        "roofline": {
+            "kernel": "PageRank iteration (bucketed pull SpMV + fused step + fold)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "bytes_model": "8m + 12n + 4 per iteration",
+            "traffic": (tr["dram_bytes_per_iter"] if tr else None),
+        },
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "wall_s_timed": wall,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": cpu[3],
+                                "seconds": cpu[1]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpr(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

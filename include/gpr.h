@@ -1,0 +1,131 @@
+/* gpr: GB300-native graph build and PageRank — the C-ABI boundary.
+ *
+ * The paper (SNAP, Leskovec and Sosic) treats a graph as a set of nodes with
+ * non-negative integer ids and edges as (source, destination) pairs
+ * (section 3, "SNAP Foundations"); its simple directed graph container keeps
+ * no multi-edges and stores each node's neighbours in sorted vectors
+ * (section 5, "Representation of Graphs and Networks").  Its methods table
+ * lists PageRank and personalised PageRank among the analytics (section 4,
+ * Table "snap_methods"); section 6 times 10 PageRank iterations on
+ * LiveJournal (Table "exp_algs") and per-iteration PageRank on Twitter2010
+ * (Table "exp_parallel").  Every entry point below computes one of those
+ * operations on the GPU.  No torch types cross this boundary: pointers are
+ * plain host or device addresses, streams are cudaStream_t passed as void*.
+ *
+ * Conventions for every function:
+ *  - Return value: a gpr_status.  Nothing aborts or exits.  On any status
+ *    other than GPR_OK, gpr_last_error() holds a one-line message for the
+ *    calling thread, outputs are unspecified, and no resource the call made
+ *    is left allocated.
+ *  - Invalid arguments are reported as GPR_EINVAL before any device work.
+ *  - `stream` may be NULL (the legacy default stream).  Work is ordered on
+ *    it; functions that return values on the host synchronise it.
+ *  - Device memory a gpr_graph owns is released by graph_free only.
+ */
+#ifndef GPR_H
+#define GPR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GPR_OK = 0,
+  GPR_EINVAL = 1,    /* bad argument: id out of range, n <= 0, damping outside (0, 1), ... */
+  GPR_ENOMEM = 2,    /* device allocation failed, or a request can never fit its budget */
+  GPR_ECUDA = 3,     /* a CUDA runtime call failed */
+  GPR_ETIMEOUT = 4,  /* a bounded device-side wait gave up (the kernel returned, nothing hung) */
+  GPR_EBUSY = 5,     /* queue full */
+  GPR_ENOTREADY = 6, /* result not ready within the poll timeout */
+  GPR_ENOTFOUND = 7  /* unknown ticket or graph id */
+} gpr_status;
+
+/* Storage type of rank vectors.  Accumulation is always FP32; the per-step
+ * mass, dangling-mass and residual reductions are FP64. */
+typedef enum { GPR_FP32 = 0, GPR_BF16 = 1 } gpr_dtype;
+
+/* Pointer-space flags */
+#define GPR_PTR_DEVICE 0 /* arrays are device (or managed) memory */
+#define GPR_PTR_HOST 1   /* arrays are host memory; the library copies them */
+
+/* A directed simple graph resident in device memory: the CSC (in-adjacency,
+ * sources ascending within each destination), out-degrees, and an execution
+ * layout for the PageRank kernels.  Opaque. */
+typedef struct gpr_graph gpr_graph;
+
+typedef struct {
+  int32_t n;             /* nodes (ids 0..n-1; isolated nodes included) */
+  int64_t m_raw;         /* COO length given to graph_build */
+  int64_t m;             /* distinct non-loop edges */
+  int32_t n_dangling;    /* nodes with out-degree 0 */
+  int32_t max_in_degree;
+  int32_t max_out_degree;
+  int64_t device_bytes;  /* device memory the graph holds */
+} gpr_graph_info;
+
+typedef struct {
+  int32_t iters_run;
+  double residual_l1; /* ||x_k - x_{k-1}||_1 of the last step, FP64 sum of FP32 terms */
+  double mass;        /* sum of x_k, FP64 */
+  double dangling;    /* dangling mass of x_k, FP64 */
+} gpr_stats;
+
+/* ---- graph construction ------------------------------------------------
+ * graph_build: the simple directed graph of a raw COO edge stream (section
+ * 3, the directed graph container; section 5, sorted adjacency vectors).
+ *   src, dst : m_raw int32 node ids each (structure of arrays), in host
+ *              memory if flags has GPR_PTR_HOST, else device memory.  Not
+ *              modified; the caller keeps ownership.
+ *   m_raw    : >= 0 and < 2^31.   n : number of nodes, 1 <= n < 2^30.
+ * Duplicate pairs collapse to one edge; self-loops are dropped; nodes
+ * without edges are kept.  The result is bit-identical to sorting the
+ * distinct non-loop pairs by (destination, source).
+ * Errors: GPR_EINVAL if any id is outside [0, n) (detected on the device
+ * during the build; everything allocated is freed before return), or for
+ * bad sizes; GPR_ENOMEM; GPR_ECUDA; GPR_ETIMEOUT.
+ * On success *out owns its device memory until graph_free.  Synchronises
+ * `stream` once (to read the edge count and the error flag). */
+gpr_status graph_build(const int32_t* src, const int32_t* dst, int64_t m_raw, int32_t n, int flags,
+                       void* stream, gpr_graph** out);
+
+/* Releases everything the graph owns.  NULL is accepted.  The caller must
+ * not free a graph while work using it is still queued on a stream. */
+gpr_status graph_free(gpr_graph* g);
+
+gpr_status graph_info(const gpr_graph* g, gpr_graph_info* info);
+
+/* Copies the CSC to caller-owned HOST arrays: col_ptr (n + 1), row_idx (m),
+ * outdeg (n); any pointer may be NULL to skip it.  Synchronous. */
+gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg);
+
+/* ---- PageRank ------------------------------------------------------------
+ * pagerank: `iters` steps of PageRank power iteration (section 4 Table
+ * "snap_methods"; the fixed iteration count follows section 6 Table
+ * "exp_algs", which times 10 iterations):
+ *   x_0 = 1/N;   D_k = sum of x_k over nodes with out-degree 0;
+ *   x_{k+1}[v] = (1 - d)/N + d (sum_{u -> v} x_k[u] / outdeg(u) + D_k / N)
+ * with each step applied to x_k / sum(x_k) (FP64 mass normalisation).
+ *   damping : d in (0, 1).   iters : >= 0.
+ *   dt      : storage of the rank vectors (GPR_FP32 or GPR_BF16).
+ *   x_out   : n floats (FP32 even for BF16 storage), indexed by node id;
+ *             device memory, or host memory if flags has GPR_PTR_HOST.
+ *   st      : optional; filled if non-NULL (this synchronises `stream`).
+ * Calls on one graph must not overlap in time (the graph holds the
+ * iteration workspace); order them on one stream. */
+gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags,
+                    float* x_out, gpr_stats* st, void* stream);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* gpr_last_error(void);
+
+/* Diagnostics (no counterpart in the paper): how many CUDA kernels this
+ * library has launched in this process so far, counted on the host at each
+ * launch (a CUDA graph launch adds its kernel nodes).  Thread-safe. */
+int64_t gpr_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPR_H */

@@ -1,0 +1,198 @@
+"""gpr: GB300-native graph build and PageRank (Python binding).
+
+Thin ctypes marshalling over the C-ABI library ``libgpr.so`` (declared in
+``include/gpr.h``).  Every step of the computation runs in the library's CUDA
+kernels; this module converts arguments only.  PyTorch supplies device memory
+and streams.  There is no fallback: if the library is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_OBJ = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_HERE, "libgpr.so")
+
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
+              "-Xcompiler", "-fPIC", f"-I{os.path.join(_ROOT, 'include')}"]
+
+# status codes (include/gpr.h)
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTREADY, ENOTFOUND = range(8)
+_NAMES = ["GPR_OK", "GPR_EINVAL", "GPR_ENOMEM", "GPR_ECUDA", "GPR_ETIMEOUT", "GPR_EBUSY", "GPR_ENOTREADY",
+          "GPR_ENOTFOUND"]
+FP32, BF16 = 0, 1
+PTR_DEVICE, PTR_HOST = 0, 1
+
+
+def sources():
+    return sorted(os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".cu"))
+
+
+def build(verbose: bool = False) -> str:
+    """Compile every CUDA source for sm_103a (in parallel) and link libgpr.so."""
+    os.makedirs(_OBJ, exist_ok=True)
+    srcs = sources()
+
+    def compile_one(src):
+        obj = os.path.join(_OBJ, os.path.basename(src)[:-3] + ".o")
+        cmd = ["nvcc", *NVCC_FLAGS, "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose and (r.stdout or r.stderr):
+            print(r.stdout, r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LIB_PATH + ".tmp"
+    subprocess.check_call(["nvcc", "-shared", "-gencode", "arch=compute_103a,code=sm_103a", *objs, "-o", tmp,
+                           "-lcudart"])
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class GprError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES[status] if 0 <= status < len(_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m_raw", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("n_dangling", ctypes.c_int32), ("max_in_degree", ctypes.c_int32),
+                ("max_out_degree", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters_run", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
+                ("dangling", ctypes.c_double)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """The loaded C-ABI library; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgpr.so not built ({LIB_PATH}); run paper_1606_07550_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.gpr_last_error.restype = ctypes.c_char_p
+        L.graph_build.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, _VP,
+                                  ctypes.POINTER(_VP)]
+        L.graph_free.argtypes = [_VP]
+        L.graph_info.argtypes = [_VP, ctypes.POINTER(GraphInfo)]
+        L.graph_export.argtypes = [_VP, _VP, _VP, _VP]
+        L.pagerank.argtypes = [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int, ctypes.c_int, _VP,
+                               ctypes.POINTER(Stats), _VP]
+        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise GprError(status, lib().gpr_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr_and_flag(a):
+    """(address, is_host) of a torch tensor or numpy array of int32/float32."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, True
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr(), not a.is_cuda
+
+
+class Graph:
+    """A device-resident simple directed graph (owns its device memory)."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("graph already freed")
+        return self._h
+
+    def info(self) -> GraphInfo:
+        inf = GraphInfo()
+        _check(lib().graph_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def n(self) -> int:
+        return self.info().n
+
+    @property
+    def m(self) -> int:
+        return self.info().m
+
+    def export(self):
+        """Host copies of (col_ptr, row_idx, outdeg)."""
+        inf = self.info()
+        cp = np.empty(inf.n + 1, np.int32)
+        ri = np.empty(max(inf.m, 1), np.int32)
+        od = np.empty(inf.n, np.int32)
+        _check(lib().graph_export(self.handle, cp.ctypes.data, ri.ctypes.data, od.ctypes.data))
+        return cp, ri[: inf.m], od
+
+    def free(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().graph_free(h))
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.graph_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def graph_build(src, dst, n: int, stream=None) -> Graph:
+    """COO -> device CSC.  src/dst: int32 torch CUDA tensors, or host arrays
+    (numpy or CPU tensors), which the library copies to the device."""
+    if len(src) != len(dst):
+        raise ValueError("src and dst differ in length")
+    ps, hs = _ptr_and_flag(src)
+    pd, hd = _ptr_and_flag(dst)
+    if hs != hd:
+        raise ValueError("src and dst must both be host or both be device arrays")
+    h = _VP()
+    _check(lib().graph_build(ps, pd, len(src), n, PTR_HOST if hs else PTR_DEVICE, _stream_ptr(stream),
+                             ctypes.byref(h)))
+    return Graph(h.value)
+
+
+def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int = FP32, stream=None,
+             stats: bool = False):
+    """Writes PageRank (n floats, by node id) into `out` (a CUDA tensor, or a
+    host array / CPU tensor).  Returns a Stats if stats=True."""
+    po, host = _ptr_and_flag(out)
+    st = Stats() if stats else None
+    _check(lib().pagerank(g.handle, damping, iters, dtype, PTR_HOST if host else PTR_DEVICE, po,
+                          ctypes.byref(st) if st is not None else None, _stream_ptr(stream)))
+    return st

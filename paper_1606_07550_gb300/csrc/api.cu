@@ -1,0 +1,147 @@
+// C-ABI entry points (declared and documented in include/gpr.h).
+#include <climits>
+
+#include "gpr_internal.cuh"
+
+namespace gpr {
+const char* last_error_cstr();
+gpr_status build_graph(const int32_t* src, const int32_t* dst, int64_t m_raw, int32_t n, int flags, cudaStream_t s,
+                       gpr_graph** out);
+gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
+                        gpr_stats* st, cudaStream_t s);
+
+void graph_free_device(gpr_graph* g, cudaStream_t s) {
+  if (!g) return;
+  if (g->work) {
+    pagerank_work_free(g->work);
+    g->work = nullptr;
+  }
+  plan_free(g->plan, s);
+  dfree(g->col_ptr, s);
+  dfree(g->row_idx, s);
+  dfree(g->outdeg, s);
+  g->col_ptr = g->row_idx = g->outdeg = nullptr;
+}
+
+static int64_t graph_bytes(const gpr_graph* g) {
+  const int64_t n = g->n, m = g->m;
+  // canonical CSC + relabelled CSC + permutations + inverse degrees
+  return (n + 1) * 4 + m * 4 + n * 4 + (n + 1) * 4 + m * 4 + 2 * n * 4 + n * 4 +
+         (int64_t)g->plan.nchunks * 16 + (int64_t)g->plan.nsplit * 12;
+}
+}  // namespace gpr
+
+using namespace gpr;
+
+extern "C" {
+
+const char* gpr_last_error(void) { return last_error_cstr(); }
+
+int64_t gpr_kernel_launches(void) { return launches_so_far(); }
+
+gpr_status graph_build(const int32_t* src, const int32_t* dst, int64_t m_raw, int32_t n, int flags, void* stream,
+                       gpr_graph** out) {
+  clear_error();
+  if (!out) {
+    set_error("graph_build: out is NULL");
+    return GPR_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n >= (1 << 30)) {
+    set_error("graph_build: n = %d outside [1, 2^30)", (int)n);
+    return GPR_EINVAL;
+  }
+  if (m_raw < 0 || m_raw >= ((int64_t)1 << 31)) {
+    set_error("graph_build: m_raw = %lld outside [0, 2^31)", (long long)m_raw);
+    return GPR_EINVAL;
+  }
+  if (m_raw > 0 && (!src || !dst)) {
+    set_error("graph_build: src or dst is NULL");
+    return GPR_EINVAL;
+  }
+  if (flags & ~GPR_PTR_HOST) {
+    set_error("graph_build: unknown flags 0x%x", flags);
+    return GPR_EINVAL;
+  }
+  gpr_status st = build_graph(src, dst, m_raw, n, flags, (cudaStream_t)stream, out);
+  if (st == GPR_OK) (*out)->device_bytes = graph_bytes(*out);
+  return st;
+}
+
+gpr_status graph_free(gpr_graph* g) {
+  clear_error();
+  if (!g) return GPR_OK;
+  // work on any stream may still read the graph: drain the device first
+  cudaError_t e = cudaDeviceSynchronize();
+  graph_free_device(g, nullptr);
+  cudaError_t e2 = cudaStreamSynchronize(nullptr);
+  if (e == cudaSuccess) e = e2;
+  delete g;
+  if (e != cudaSuccess) {
+    set_error("graph_free: %s", cudaGetErrorString(e));
+    return GPR_ECUDA;
+  }
+  return GPR_OK;
+}
+
+gpr_status graph_info(const gpr_graph* g, gpr_graph_info* info) {
+  clear_error();
+  if (!g || !info) {
+    set_error("graph_info: NULL argument");
+    return GPR_EINVAL;
+  }
+  info->n = g->n;
+  info->m_raw = g->m_raw;
+  info->m = g->m;
+  info->n_dangling = g->n_dangling;
+  info->max_in_degree = g->max_in;
+  info->max_out_degree = g->max_out;
+  info->device_bytes = g->device_bytes;
+  return GPR_OK;
+}
+
+gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg) {
+  clear_error();
+  if (!g) {
+    set_error("graph_export: NULL graph");
+    return GPR_EINVAL;
+  }
+  cudaError_t e = cudaSuccess;
+  if (col_ptr && e == cudaSuccess) e = cudaMemcpy(col_ptr, g->col_ptr, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost);
+  if (row_idx && g->m > 0 && e == cudaSuccess)
+    e = cudaMemcpy(row_idx, g->row_idx, (size_t)g->m * 4, cudaMemcpyDeviceToHost);
+  if (outdeg && e == cudaSuccess) e = cudaMemcpy(outdeg, g->outdeg, (size_t)g->n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error("graph_export: %s", cudaGetErrorString(e));
+    return GPR_ECUDA;
+  }
+  return GPR_OK;
+}
+
+gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
+                    gpr_stats* st, void* stream) {
+  clear_error();
+  if (!g || !x_out) {
+    set_error("pagerank: NULL graph or output");
+    return GPR_EINVAL;
+  }
+  if (!(damping > 0.0 && damping < 1.0)) {
+    set_error("pagerank: damping %g outside (0, 1)", damping);
+    return GPR_EINVAL;
+  }
+  if (iters < 0 || iters > (1 << 20)) {
+    set_error("pagerank: iters %d outside [0, 2^20]", (int)iters);
+    return GPR_EINVAL;
+  }
+  if (dt != GPR_FP32 && dt != GPR_BF16) {
+    set_error("pagerank: unknown dtype %d", (int)dt);
+    return GPR_EINVAL;
+  }
+  if (flags & ~GPR_PTR_HOST) {
+    set_error("pagerank: unknown flags 0x%x", flags);
+    return GPR_EINVAL;
+  }
+  return run_pagerank(const_cast<gpr_graph*>(g), damping, iters, dt, flags, x_out, st, (cudaStream_t)stream);
+}
+
+}  // extern "C"

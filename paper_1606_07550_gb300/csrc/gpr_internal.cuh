@@ -1,0 +1,183 @@
+// Internal declarations of the gpr library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gpr.h"
+
+namespace gpr {
+
+// ---- errors ---------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// Device-side error bits (an int in device memory, OR-ed by kernels).
+enum : int {
+  DERR_BAD_ID = 1,   // an edge endpoint outside [0, n)
+  DERR_TIMEOUT = 2,  // a bounded spin-wait gave up
+};
+
+// Bounded spin: after this many polls a wait reports DERR_TIMEOUT and returns.
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+struct CudaFail {
+  cudaError_t err;
+  const char* what;
+};
+
+#define GPR_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) throw ::gpr::CudaFail{e_, #call}; \
+  } while (0)
+
+struct StatusFail {
+  gpr_status st;
+  std::string msg;
+};
+
+// ---- device memory: stream-ordered allocations ----------------------------
+void* dalloc(size_t bytes, cudaStream_t s);  // throws StatusFail(GPR_ENOMEM)
+void dfree(void* p, cudaStream_t s);
+
+int num_sms();
+int device_ordinal();
+
+// Host-side count of kernels this library has launched (a CUDA graph launch
+// counts its kernel nodes).
+void count_launches(int64_t k);
+int64_t launches_so_far();
+
+// ---- radix sort of 64-bit keys (onesweep-style, build.cu) -----------------
+// Sorts keys[0..n) ascending on the low `bits` bits (stable LSD, 8-bit
+// digits), using `alt` (n entries) as the second buffer.  Returns the buffer
+// holding the result (keys or alt).  hist_ready: the caller already filled
+// `hist` (passes x 256 digit counts, device); otherwise it is computed.
+uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cudaStream_t s,
+                         int* derr, uint32_t* hist = nullptr);
+
+// ---- PageRank execution layout -------------------------------------------
+// Rows of the relabelled CSC are grouped by in-degree bucket; within a
+// bucket, by descending out-degree.  Each bucket runs with a fixed number of
+// lanes per row (1..32), or, for the last bucket, in chunks of edges per
+// thread block.
+constexpr int kMaxBuckets = 6;
+
+struct Bucket {
+  int32_t row_begin, row_end;
+  int lanes;  // 1, 2, 4, 8, 16, 32 lanes per row; 0 = chunked block-per-row
+};
+
+struct Plan {
+  int32_t* new2old = nullptr;  // n: relabelled row p holds original node new2old[p]
+  int32_t* old2new = nullptr;  // n
+  int32_t* col_ptr = nullptr;  // n + 1, relabelled CSC
+  int32_t* row_idx = nullptr;  // m, relabelled source ids
+  float* inv_deg = nullptr;    // n, 1/outdeg (0 for dangling)
+  int nbuckets = 0;
+  Bucket bucket[kMaxBuckets];
+  int32_t deg_threshold[kMaxBuckets];  // upper in-degree bound of each bucket (last: INT_MAX)
+  // chunks of the block bucket: (row, edge_begin, edge_end) and whether the
+  // chunk is the whole row (1) or a piece of a split row (0)
+  int32_t* chunk_row = nullptr;
+  int32_t* chunk_begin = nullptr;
+  int32_t* chunk_end = nullptr;
+  int32_t* chunk_whole = nullptr;
+  int32_t nchunks = 0;
+  int32_t* split_row = nullptr;   // rows split over several chunks
+  int32_t* split_cbeg = nullptr;  // their chunk ranges [cbeg, cend) in the chunk list
+  int32_t* split_cend = nullptr;
+  int32_t nsplit = 0;
+  int32_t chunk_edges = 0;
+};
+
+struct PagerankWork;  // pagerank.cu
+
+}  // namespace gpr
+
+struct gpr_graph {
+  int32_t n = 0;
+  int64_t m_raw = 0;
+  int64_t m = 0;
+  int id_bits = 0;
+  int32_t n_dangling = 0;
+  int32_t max_in = 0, max_out = 0;
+  int device = 0;
+  int32_t* col_ptr = nullptr;  // n + 1
+  int32_t* row_idx = nullptr;  // m
+  int32_t* outdeg = nullptr;   // n
+  gpr::Plan plan;
+  int64_t device_bytes = 0;
+  std::mutex mu;                    // guards `work`
+  gpr::PagerankWork* work = nullptr;  // lazily made by pagerank()
+};
+
+namespace gpr {
+void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
+void plan_free(Plan& p, cudaStream_t s);
+void pagerank_work_free(PagerankWork* w);
+
+// ---- device helpers -----------------------------------------------------
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Look-back status words: [63:60] epoch, [59:58] flag, [57:0] value.
+constexpr uint64_t kFlagAgg = 1, kFlagInc = 2;
+constexpr uint64_t kValMask = (1ull << 58) - 1;
+__device__ __forceinline__ uint64_t lb_word(uint32_t epoch, uint64_t flag, uint64_t v) {
+  return ((uint64_t)epoch << 60) | (flag << 58) | (v & kValMask);
+}
+
+// Decoupled look-back (Merrill and Garland, "Single-pass parallel prefix scan
+// with decoupled look-back", 2016): the exclusive prefix of tile `tile` from
+// the status words of tiles tile-1, tile-2, ... (stride `stride` words apart).
+// Every wait is bounded; on timeout it sets DERR_TIMEOUT and returns what it
+// has.
+__device__ __forceinline__ uint64_t lookback(const uint64_t* status, int64_t tile, int64_t stride,
+                                             uint32_t epoch, int* derr) {
+  uint64_t excl = 0;
+  int64_t k = tile - 1;
+  uint32_t spins = 0;
+  while (k >= 0) {
+    uint64_t w = ld_relaxed_u64(status + k * stride);
+    uint32_t ep = (uint32_t)(w >> 60);
+    uint64_t fl = (w >> 58) & 3;
+    if (ep != epoch || fl == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(derr, DERR_TIMEOUT);
+        return excl;
+      }
+      if (spins > 64) {
+        __nanosleep(64);
+        // once any waiter has given up, the rest of the grid stops waiting too
+        if ((spins & 255) == 0 && (*(volatile int*)derr & DERR_TIMEOUT)) return excl;
+      }
+      continue;
+    }
+    excl += w & kValMask;
+    if (fl == kFlagInc) break;
+    --k;
+  }
+  return excl;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace gpr

@@ -1,0 +1,53 @@
+"""The C-ABI library loads and exports every function include/*.h declares (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1606_07550_gb300 as gpr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            if m.group(1) not in ("if", "while", "for", "return", "sizeof"):
+                names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    if not os.path.exists(gpr.LIB_PATH):
+        gpr.build()
+    return ctypes.CDLL(gpr.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "gpr_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(built_lib):
+    missing = [n for n in declared_functions() if not hasattr(built_lib, n)]
+    assert not missing, missing
+
+
+def test_binding_loads_and_reports_errors_without_gpu_work():
+    L = gpr.lib()
+    assert L.gpr_last_error() == b""
+    # argument validation happens on the host, before any device call
+    h = ctypes.c_void_p()
+    assert L.graph_build(None, None, 5, 0, 0, None, ctypes.byref(h)) == gpr.EINVAL
+    assert b"n = 0" in L.gpr_last_error()
+    assert L.graph_build(None, None, 5, 10, 0, None, ctypes.byref(h)) == gpr.EINVAL
+    assert L.pagerank(None, 0.85, 10, 0, 0, None, None, None) == gpr.EINVAL

@@ -1,0 +1,192 @@
+"""GPU PageRank against the FP64 CPU oracle at the same iteration count.
+
+Tolerance: L1 <= 1e-5 for FP32 rank storage and <= 1e-3 for BF16 storage
+(FP32 accumulation in both).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_1606_07550_gb300 as gpr
+from gen import workloads
+
+from gpu_util import coo_for, l1, max_rel, random_coo_with_dups
+
+pytestmark = pytest.mark.gpu
+
+TOL = {gpr.FP32: 1e-5, gpr.BF16: 1e-3}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def gpu_pr(torch, g, iters, d=0.85, dt=gpr.FP32, stats=False):
+    out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    st = gpr.pagerank(g, out, damping=d, iters=iters, dtype=dt, stats=stats)
+    x = out.cpu().numpy()
+    return (x, st) if stats else x
+
+
+def check(torch, n, src, dst, iters, dt=gpr.FP32, d=0.85, buckets=None):
+    if buckets is not None:
+        os.environ["GPR_BUCKETS"] = buckets
+    try:
+        g = gpr.graph_build(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
+    finally:
+        os.environ.pop("GPR_BUCKETS", None)
+    ref = oracle.pagerank(oracle.build_csc(n, src, dst), d, iters)
+    x, st = gpu_pr(torch, g, iters, d, dt, stats=True)
+    err = l1(x, ref)
+    assert err <= TOL[dt], (err, max_rel(x, ref))
+    assert abs(st.mass - 1.0) <= 1e-5
+    g.free()
+    return err
+
+
+def test_er_10k_fp32_and_bf16(torch):
+    spec = workloads.ER_10K
+    src, dst = coo_for(spec)
+    check(torch, spec.n, src, dst, spec.iters, gpr.FP32)
+    check(torch, spec.n, src, dst, spec.iters, gpr.BF16)
+
+
+@pytest.mark.parametrize("buckets", [None, "*:1", "*:4", "*:8", "*:32", "*:0", "0:1,3:2,9:16,100:32,*:0"])
+def test_each_bucket_kernel_alone(torch, buckets):
+    # power-law graph with hubs, dangling nodes and isolated nodes
+    src, dst = gen.rmat_coo(30_000, 600_000, seed=31)
+    check(torch, 30_000, src, dst, 30, buckets=buckets)
+
+
+def test_split_rows(torch):
+    # rows longer than one chunk are split and finished by the fold kernel
+    os.environ["GPR_CHUNK_EDGES"] = "1024"
+    try:
+        src, dst = gen.rmat_coo(20_000, 800_000, seed=32)
+        check(torch, 20_000, src, dst, 20, buckets="16:8,*:0")
+    finally:
+        os.environ.pop("GPR_CHUNK_EDGES", None)
+
+
+@pytest.mark.parametrize("n,m_raw,seed", [(1, 5, 0), (2, 1, 1), (257, 3000, 2), (4099, 40_000, 3),
+                                          (100_003, 1_000_000, 4)])
+def test_random_graphs(torch, n, m_raw, seed):
+    rng = np.random.default_rng(seed)
+    src, dst = random_coo_with_dups(rng, n, m_raw)
+    for dt in (gpr.FP32, gpr.BF16):
+        check(torch, n, src, dst, 25, dt)
+
+
+def test_closed_forms_on_gpu(torch):
+    N = 1000
+    cyc = np.arange(N, dtype=np.int32)
+    g = gpr.graph_build(torch.from_numpy(cyc).cuda(), torch.from_numpy((cyc + 1) % N).cuda(), N)
+    x = gpu_pr(torch, g, 50)
+    assert np.abs(x - 1.0 / N).max() < 1e-9
+    # out-star: hub 0 -> leaves, fixed point x_hub = 1 / (N + d)
+    leaves = np.arange(1, N, dtype=np.int32)
+    g = gpr.graph_build(torch.from_numpy(np.zeros_like(leaves)).cuda(), torch.from_numpy(leaves).cuda(), N)
+    x = gpu_pr(torch, g, 200)
+    assert abs(x[0] - 1.0 / (N + 0.85)) < 1e-7
+    # no edges at all: uniform
+    z = torch.zeros(0, dtype=torch.int32, device="cuda")
+    g = gpr.graph_build(z, z, 77)
+    x = gpu_pr(torch, g, 10)
+    assert np.abs(x - 1.0 / 77).max() < 1e-9
+
+
+def test_zero_iterations_and_damping_values(torch):
+    src, dst = gen.rmat_coo(5000, 60_000, seed=5)
+    g = gpr.graph_build(src, dst, 5000)
+    x = gpu_pr(torch, g, 0)
+    assert np.abs(x - 1.0 / 5000).max() < 1e-12
+    ref_g = oracle.build_csc(5000, src, dst)
+    for d in (0.5, 0.99):
+        x = gpu_pr(torch, g, 40, d=d)
+        assert l1(x, oracle.pagerank(ref_g, d, 40)) <= 1e-5
+
+
+def test_stats_match_oracle(torch):
+    src, dst = gen.rmat_coo(20_000, 200_000, seed=6)
+    g = gpr.graph_build(src, dst, 20_000)
+    ref_g = oracle.build_csc(20_000, src, dst)
+    xr, resid, _ = oracle.pagerank(ref_g, 0.85, 12, with_resid=True)
+    x, st = gpu_pr(torch, g, 12, stats=True)
+    assert st.iters_run == 12
+    assert abs(st.residual_l1 - resid[-1]) <= 1e-6
+    assert abs(st.mass - 1.0) <= 1e-6
+    assert abs(st.dangling - xr[ref_g.outdeg == 0].sum()) <= 1e-5
+
+
+def test_deterministic(torch):
+    src, dst = gen.rmat_coo(40_000, 900_000, seed=7)
+    g = gpr.graph_build(src, dst, 40_000)
+    a = gpu_pr(torch, g, 30)
+    b = gpu_pr(torch, g, 30)
+    g2 = gpr.graph_build(src, dst, 40_000)
+    c = gpu_pr(torch, g2, 30)
+    assert (a == b).all() and (a == c).all()
+
+
+def test_host_output_and_streams(torch):
+    src, dst = gen.rmat_coo(8000, 90_000, seed=8)
+    g = gpr.graph_build(src, dst, 8000)
+    out = np.empty(8000, np.float32)
+    s = torch.cuda.Stream()
+    gpr.pagerank(g, out, iters=20, stream=s)
+    ref = oracle.pagerank(oracle.build_csc(8000, src, dst), 0.85, 20)
+    assert l1(out, ref) <= 1e-5
+
+
+def test_rejects_bad_arguments(torch):
+    g = gpr.graph_build(np.array([0], np.int32), np.array([1], np.int32), 2)
+    out = torch.empty(2, device="cuda")
+    for kw in ({"damping": 0.0}, {"damping": 1.0}, {"iters": -1}, {"dtype": 7}):
+        with pytest.raises(gpr.GprError) as ei:
+            gpr.pagerank(g, out, **kw)
+        assert ei.value.status == gpr.EINVAL
+
+
+@pytest.mark.slow
+def test_rmat_lj_full_oracle(torch):
+    """LiveJournal-shaped graph (4.8M ids, 69M raw edges), 100 iterations,
+    full-vector comparison against the oracle."""
+    spec = workloads.RMAT_LJ
+    src, dst = coo_for(spec)
+    err = check(torch, spec.n, src, dst, spec.iters)
+    print(f"rmat-lj L1 = {err:.3e}")
+
+
+@pytest.mark.slow
+def test_rmat25_properties_at_full_size(torch):
+    """Billion-edge graph: properties that hold at any size, in the benchmark's
+    launch configuration: unit mass, the lower bound (1-d)/N on every entry,
+    and one exact FP64 step on the GPU's own CSC carrying x_99 to within
+    FP32 rounding of x_100."""
+    spec = workloads.RMAT_25
+    n, m_raw = spec.n, spec.m
+    s_d = torch.empty(m_raw, dtype=torch.int32, device="cuda")
+    d_d = torch.empty(m_raw, dtype=torch.int32, device="cuda")
+    perm = torch.from_numpy(gen.permutation(n, spec.seed)).cuda()
+    gen.rmat_coo_dev(n, m_raw, spec.seed, s_d.data_ptr(), d_d.data_ptr(), perm.data_ptr())
+    g = gpr.graph_build(s_d, d_d, n)
+    del s_d, d_d, perm
+    torch.cuda.empty_cache()
+    x99 = gpu_pr(torch, g, 99).astype(np.float64)
+    x100, st = gpu_pr(torch, g, 100, stats=True)
+    assert abs(x100.astype(np.float64).sum() - 1.0) <= 1e-5
+    assert x100.min() >= (1 - 0.85) / n * (1 - 1e-5)
+    cp, ri, od = g.export()
+    s = x99.sum()
+    dang = x99[od == 0].sum()
+    contrib = np.where(od > 0, x99 / np.maximum(od, 1), 0.0) / s
+    starts = np.minimum(cp[:-1].astype(np.int64), max(len(ri) - 1, 0))
+    pulled = np.add.reduceat(contrib[ri], starts) if len(ri) else np.zeros(n)
+    pulled[np.diff(cp) == 0] = 0.0
+    step = (1 - 0.85) / n + 0.85 * (pulled + dang / s / n)
+    assert l1(x100, step) <= 1e-5
