@@ -42,8 +42,10 @@ typedef enum {
   GPR_ENOTFOUND = 7  /* unknown ticket or graph id */
 } gpr_status;
 
-/* Storage type of rank vectors.  Accumulation is always FP32; the per-step
- * mass, dangling-mass and residual reductions are FP64. */
+/* Storage type of the gathered contribution vector c = x / outdeg (the
+ * bytes the pull step reads once per edge).  The rank vector x itself is
+ * always FP32; accumulation is always FP32; the per-step mass,
+ * dangling-mass and residual reductions are FP64. */
 typedef enum { GPR_FP32 = 0, GPR_BF16 = 1 } gpr_dtype;
 
 /* Pointer-space flags */
@@ -108,7 +110,7 @@ gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, 
  *   x_{k+1}[v] = (1 - d)/N + d (sum_{u -> v} x_k[u] / outdeg(u) + D_k / N)
  * with each step applied to x_k / sum(x_k) (FP64 mass normalisation).
  *   damping : d in (0, 1).   iters : >= 0.
- *   dt      : storage of the rank vectors (GPR_FP32 or GPR_BF16).
+ *   dt      : storage of the contribution vector (GPR_FP32 or GPR_BF16).
  *   x_out   : n floats (FP32 even for BF16 storage), indexed by node id;
  *             device memory, or host memory if flags has GPR_PTR_HOST.
  *   st      : optional; filled if non-NULL (this synchronises `stream`).

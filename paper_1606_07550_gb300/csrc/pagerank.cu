@@ -31,7 +31,8 @@ struct StepParams {
   double n;
 };
 
-// ---- rank storage: FP32 or BF16 (accumulation always FP32) -------------
+// ---- storage of the gathered contributions c = x / outdeg: FP32 or BF16.
+// The rank vector x itself and all accumulation stay FP32. --------------
 template <typename T>
 __device__ __forceinline__ float ld_rank(const T* p, int64_t i);
 template <>
@@ -92,14 +93,15 @@ __device__ __forceinline__ void block_partials3(float a, float b, float c, doubl
 
 // Finish one row: store x' and c', accumulate mass, dangling mass, residual.
 template <typename T>
-__device__ __forceinline__ void finish_row(int64_t r, float y, float A, float B, const T* __restrict__ x_in,
-                                           const float* __restrict__ inv_deg, T* __restrict__ x_out,
+__device__ __forceinline__ void finish_row(int64_t r, float y, float A, float B, const float* __restrict__ x_in,
+                                           const float* __restrict__ inv_deg, float* __restrict__ x_out,
                                            T* __restrict__ c_out, float& mass, float& dang, float& res) {
   const float idg = inv_deg[r];
-  const float xs = store_rank(x_out, r, fmaf(A, y, B));
+  const float xs = fmaf(A, y, B);
+  x_out[r] = xs;
   store_rank(c_out, r, xs * idg);
   mass += xs;
-  res += fabsf(xs - ld_rank(x_in, r));
+  res += fabsf(xs - x_in[r]);
   if (idg == 0.0f) dang += xs;
 }
 
@@ -107,8 +109,8 @@ __device__ __forceinline__ void finish_row(int64_t r, float y, float A, float B,
 template <int G, typename T>
 __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ col_ptr,
                                                    const int32_t* __restrict__ row_idx, const T* __restrict__ c_in,
-                                                   const T* __restrict__ x_in, const float* __restrict__ inv_deg,
-                                                   T* __restrict__ x_out, T* __restrict__ c_out, int32_t r0,
+                                                   const float* __restrict__ x_in, const float* __restrict__ inv_deg,
+                                                   float* __restrict__ x_out, T* __restrict__ c_out, int32_t r0,
                                                    int32_t r1, const StepParams* __restrict__ prm,
                                                    double* __restrict__ partials) {
   const float A = prm->coefA, B = prm->coefB;
@@ -153,8 +155,8 @@ __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ c
 // finished here; a piece of a split row leaves its sum in chunk_sum.
 template <typename T>
 __global__ void __launch_bounds__(256) chunks_kernel(
-    const int32_t* __restrict__ row_idx, const T* __restrict__ c_in, const T* __restrict__ x_in,
-    const float* __restrict__ inv_deg, T* __restrict__ x_out, T* __restrict__ c_out,
+    const int32_t* __restrict__ row_idx, const T* __restrict__ c_in, const float* __restrict__ x_in,
+    const float* __restrict__ inv_deg, float* __restrict__ x_out, T* __restrict__ c_out,
     const int32_t* __restrict__ chunk_row, const int32_t* __restrict__ chunk_begin,
     const int32_t* __restrict__ chunk_end, const int32_t* __restrict__ chunk_whole, int32_t nchunks,
     float* __restrict__ chunk_sum, const StepParams* __restrict__ prm, double* __restrict__ partials) {
@@ -193,13 +195,14 @@ __global__ void __launch_bounds__(256) chunks_kernel(
 
 // x_0 = 1/N, c_0 = x_0 * inv_outdeg.
 template <typename T>
-__global__ void init_kernel(T* __restrict__ x, T* __restrict__ c, const float* __restrict__ inv_deg, int32_t n,
+__global__ void init_kernel(float* __restrict__ x, T* __restrict__ c, const float* __restrict__ inv_deg, int32_t n,
                             double* __restrict__ partials) {
   float mass = 0.f, dang = 0.f;
   const float x0 = 1.0f / (float)n;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const float idg = inv_deg[v];
-    const float xs = store_rank(x, v, x0);
+    const float xs = x0;
+    x[v] = xs;
     store_rank(c, v, xs * idg);
     mass += xs;
     if (idg == 0.0f) dang += xs;
@@ -212,8 +215,8 @@ __global__ void init_kernel(T* __restrict__ x, T* __restrict__ c, const float* _
 // coefficients.
 template <typename T>
 __global__ void __launch_bounds__(1024) fold_kernel(
-    const T* __restrict__ x_in, const float* __restrict__ inv_deg, T* __restrict__ x_out, T* __restrict__ c_out,
-    const int32_t* __restrict__ split_row, const int32_t* __restrict__ split_cbeg,
+    const float* __restrict__ x_in, const float* __restrict__ inv_deg, float* __restrict__ x_out,
+    T* __restrict__ c_out, const int32_t* __restrict__ split_row, const int32_t* __restrict__ split_cbeg,
     const int32_t* __restrict__ split_cend, int32_t nsplit, const float* __restrict__ chunk_sum,
     const double* __restrict__ partials, int32_t npartials, StepParams* __restrict__ prm,
     double* __restrict__ log_row) {
@@ -260,11 +263,10 @@ __global__ void __launch_bounds__(1024) fold_kernel(
   }
 }
 
-template <typename T>
-__global__ void output_kernel(const T* __restrict__ x, const int32_t* __restrict__ old2new, int32_t n,
+__global__ void output_kernel(const float* __restrict__ x, const int32_t* __restrict__ old2new, int32_t n,
                               float* __restrict__ out) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    out[v] = ld_rank(x, old2new[v]);
+    out[v] = x[old2new[v]];
 }
 
 // ---- host side -------------------------------------------------------------
@@ -276,8 +278,8 @@ struct LaunchShape {
 
 struct PagerankWork {
   int device = 0;
-  void* x[2] = {nullptr, nullptr};  // n * 4 bytes each (holds FP32 or BF16)
-  void* c[2] = {nullptr, nullptr};
+  void* x[2] = {nullptr, nullptr};  // n floats each: the rank vector, always FP32
+  void* c[2] = {nullptr, nullptr};  // n * 4 bytes each: contributions x / outdeg, FP32 or BF16
   float* out_tmp = nullptr;         // n floats, for host-pointer output
   double* partials = nullptr;
   int32_t npartials = 0;
@@ -344,8 +346,8 @@ static int grid_for_bucket(const Bucket& b, int32_t nchunks) {
 }
 
 template <typename T>
-static void launch_rows(const Bucket& b, int grid, cudaStream_t s, const Plan& P, const T* c_in, const T* x_in,
-                        T* x_out, T* c_out, const StepParams* prm, double* part) {
+static void launch_rows(const Bucket& b, int grid, cudaStream_t s, const Plan& P, const T* c_in, const float* x_in,
+                        float* x_out, T* c_out, const StepParams* prm, double* part) {
 #define GPR_ROWS(GL)                                                                                       \
   rows_kernel<GL, T><<<grid, 256, 0, s>>>(P.col_ptr, P.row_idx, c_in, x_in, P.inv_deg, x_out, c_out, b.row_begin, \
                                           b.row_end, prm, part)
@@ -364,7 +366,7 @@ static void launch_rows(const Bucket& b, int grid, cudaStream_t s, const Plan& P
 template <typename T>
 static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, cudaStream_t s) {
   const Plan& P = g->plan;
-  T* x[2] = {(T*)w->x[0], (T*)w->x[1]};
+  float* x[2] = {(float*)w->x[0], (float*)w->x[1]};
   T* c[2] = {(T*)w->c[0], (T*)w->c[1]};
   init_kernel<T><<<w->init_shape.grid, 256, 0, s>>>(x[0], c[0], P.inv_deg, g->n, w->partials);
   fold_kernel<T><<<1, 1024, 0, s>>>(x[0], P.inv_deg, x[0], c[0], P.split_row, P.split_cbeg, P.split_cend, 0,
@@ -477,10 +479,7 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
       dst = w->out_tmp;
     }
     const int og = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, num_sms() * 8));
-    if (dt == GPR_BF16)
-      output_kernel<__nv_bfloat16><<<og, 256, 0, s>>>((const __nv_bfloat16*)xf, g->plan.old2new, g->n, dst);
-    else
-      output_kernel<float><<<og, 256, 0, s>>>((const float*)xf, g->plan.old2new, g->n, dst);
+    output_kernel<<<og, 256, 0, s>>>((const float*)xf, g->plan.old2new, g->n, dst);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
     if (flags & GPR_PTR_HOST) {

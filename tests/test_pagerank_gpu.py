@@ -44,7 +44,8 @@ def check(torch, n, src, dst, iters, dt=gpr.FP32, d=0.85, buckets=None):
     x, st = gpu_pr(torch, g, iters, d, dt, stats=True)
     err = l1(x, ref)
     assert err <= TOL[dt], (err, max_rel(x, ref))
-    assert abs(st.mass - 1.0) <= 1e-5
+    # BF16 rounding of the gathered contributions moves the mass by up to ~2^-9 d
+    assert abs(st.mass - 1.0) <= TOL[dt]
     g.free()
     return err
 
