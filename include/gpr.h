@@ -119,6 +119,35 @@ gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, 
 gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags,
                     float* x_out, gpr_stats* st, void* stream);
 
+/* ---- batched personalised PageRank ---------------------------------------
+ * Personalised PageRank (section 4 Table "snap_methods"; section 4,
+ * "Fast Random Walk Algorithms": scores from the point of view of a given
+ * node), one column per seed s, teleport vector e_s, dangling mass returned
+ * to the seed:
+ *   x_0 = e_s;  x_{k+1}[v] = (1 - d) e_s[v] + d (sum_{u->v} x_k[u]/outdeg(u) + D_k e_s[v])
+ * A column stops after max_iters steps, or, if tol > 0, after the first step
+ * k with d/(1-d) * ||x_k - x_{k-1}||_1 <= tol (an a-posteriori bound on the
+ * L1 distance to the fixed point).  One call runs every column of every job
+ * in one persistent launch; a column's result does not depend on the other
+ * columns or jobs in the call. */
+typedef struct {
+  const gpr_graph* graph;
+  int32_t num_seeds;     /* K >= 1 columns */
+  const int32_t* seeds;  /* host: K node ids in [0, n) (repeats allowed) */
+  const float* damping;  /* host: K values in (0, 1) */
+  float* x_out;          /* device: n x K FP32, node-major: x_out[v * K + k] */
+  int32_t* iters_out;    /* host, optional: steps each column ran */
+  double* residual_out;  /* host, optional: last ||x_k - x_{k-1}||_1 per column */
+} gpr_ppr_job;
+
+/* jobs: host array of num_jobs >= 0 jobs (graphs may repeat).  max_iters in
+ * [0, 2^20]; tol >= 0 (0: run exactly max_iters steps).  dt: storage of the
+ * gathered contributions (the rank state and accumulation stay FP32).
+ * Synchronises `stream`.  Errors: GPR_EINVAL for a bad argument (nothing
+ * launched), GPR_ENOMEM, GPR_ECUDA. */
+gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
+                     void* stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* gpr_last_error(void);
 

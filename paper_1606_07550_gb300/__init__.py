@@ -71,6 +71,12 @@ class GraphInfo(ctypes.Structure):
                 ("max_out_degree", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
+class PprJob(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("num_seeds", ctypes.c_int32), ("seeds", ctypes.c_void_p),
+                ("damping", ctypes.c_void_p), ("x_out", ctypes.c_void_p), ("iters_out", ctypes.c_void_p),
+                ("residual_out", ctypes.c_void_p)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
                 ("dangling", ctypes.c_double)]
@@ -95,7 +101,10 @@ def lib():
         L.graph_export.argtypes = [_VP, _VP, _VP, _VP]
         L.pagerank.argtypes = [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int, ctypes.c_int, _VP,
                                ctypes.POINTER(Stats), _VP]
-        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank"):
+        L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                ctypes.c_int, _VP]
+        L.gpr_kernel_launches.restype = ctypes.c_int64
+        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "ppr_batch"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -196,3 +205,30 @@ def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int =
     _check(lib().pagerank(g.handle, damping, iters, dtype, PTR_HOST if host else PTR_DEVICE, po,
                           ctypes.byref(st) if st is not None else None, _stream_ptr(stream)))
     return st
+
+
+def ppr_batch(requests, max_iters: int = 50, tol: float = 0.0, dtype: int = FP32, stream=None):
+    """Personalised PageRank for many (graph, seeds) requests in one launch.
+
+    requests: list of (graph, seeds, damping, out) with seeds an int sequence,
+    damping a float or a per-seed sequence, out a CUDA float32 tensor of shape
+    (n, len(seeds)) (node-major).  Returns [(iters, residual)] numpy arrays
+    per request."""
+    n_req = len(requests)
+    arr = (PprJob * max(n_req, 1))()
+    keep = []
+    results = []
+    for i, (g, seeds, damping, out) in enumerate(requests):
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+        k = len(seeds)
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(damping, dtype=np.float32), (k,)))
+        it = np.zeros(k, np.int32)
+        res = np.zeros(k, np.float64)
+        if not out.is_cuda or not out.is_contiguous() or out.numel() != g.n * k:
+            raise ValueError("out must be a contiguous CUDA tensor of n x len(seeds) floats")
+        keep += [seeds, d, it, res]
+        arr[i] = PprJob(g.handle, k, seeds.ctypes.data, d.ctypes.data, out.data_ptr(), it.ctypes.data,
+                        res.ctypes.data)
+        results.append((it, res))
+    _check(lib().ppr_batch(arr, n_req, max_iters, tol, dtype, _stream_ptr(stream)))
+    return results

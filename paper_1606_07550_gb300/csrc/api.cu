@@ -9,6 +9,8 @@ gpr_status build_graph(const int32_t* src, const int32_t* dst, int64_t m_raw, in
                        gpr_graph** out);
 gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
                         gpr_stats* st, cudaStream_t s);
+gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
+                         cudaStream_t s);
 
 void graph_free_device(gpr_graph* g, cudaStream_t s) {
   if (!g) return;
@@ -25,9 +27,9 @@ void graph_free_device(gpr_graph* g, cudaStream_t s) {
 
 static int64_t graph_bytes(const gpr_graph* g) {
   const int64_t n = g->n, m = g->m;
-  // canonical CSC + relabelled CSC + permutations + inverse degrees
-  return (n + 1) * 4 + m * 4 + n * 4 + (n + 1) * 4 + m * 4 + 2 * n * 4 + n * 4 +
-         (int64_t)g->plan.nchunks * 16 + (int64_t)g->plan.nsplit * 12;
+  // CSC (relabelled ids) + out-degrees + permutations + inverse degrees + row lists + chunks
+  return (n + 1) * 4 + m * 4 + n * 4 + 2 * n * 4 + n * 4 + n * 4 + (int64_t)g->plan.nchunks * 16 +
+         (int64_t)g->plan.nsplit * 12;
 }
 }  // namespace gpr
 
@@ -106,16 +108,7 @@ gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, 
     set_error("graph_export: NULL graph");
     return GPR_EINVAL;
   }
-  cudaError_t e = cudaSuccess;
-  if (col_ptr && e == cudaSuccess) e = cudaMemcpy(col_ptr, g->col_ptr, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost);
-  if (row_idx && g->m > 0 && e == cudaSuccess)
-    e = cudaMemcpy(row_idx, g->row_idx, (size_t)g->m * 4, cudaMemcpyDeviceToHost);
-  if (outdeg && e == cudaSuccess) e = cudaMemcpy(outdeg, g->outdeg, (size_t)g->n * 4, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) {
-    set_error("graph_export: %s", cudaGetErrorString(e));
-    return GPR_ECUDA;
-  }
-  return GPR_OK;
+  return export_graph(g, col_ptr, row_idx, outdeg);
 }
 
 gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
@@ -142,6 +135,41 @@ gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype
     return GPR_EINVAL;
   }
   return run_pagerank(const_cast<gpr_graph*>(g), damping, iters, dt, flags, x_out, st, (cudaStream_t)stream);
+}
+
+gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
+                     void* stream) {
+  clear_error();
+  if (num_jobs < 0 || (num_jobs > 0 && !jobs)) {
+    set_error("ppr_batch: bad job array");
+    return GPR_EINVAL;
+  }
+  if (max_iters < 0 || max_iters > (1 << 20) || !(tol >= 0.0)) {
+    set_error("ppr_batch: max_iters %d or tol %g out of range", (int)max_iters, tol);
+    return GPR_EINVAL;
+  }
+  if (dt != GPR_FP32 && dt != GPR_BF16) {
+    set_error("ppr_batch: unknown dtype %d", (int)dt);
+    return GPR_EINVAL;
+  }
+  for (int32_t j = 0; j < num_jobs; ++j) {
+    const gpr_ppr_job& q = jobs[j];
+    if (!q.graph || q.num_seeds < 1 || !q.seeds || !q.damping || !q.x_out) {
+      set_error("ppr_batch: job %d: missing graph, seeds, damping or output, or num_seeds < 1", (int)j);
+      return GPR_EINVAL;
+    }
+    for (int32_t k = 0; k < q.num_seeds; ++k) {
+      if (q.seeds[k] < 0 || q.seeds[k] >= q.graph->n) {
+        set_error("ppr_batch: job %d: seed %d outside [0, %d)", (int)j, (int)q.seeds[k], (int)q.graph->n);
+        return GPR_EINVAL;
+      }
+      if (!(q.damping[k] > 0.f && q.damping[k] < 1.f)) {
+        set_error("ppr_batch: job %d: damping %g outside (0, 1)", (int)j, (double)q.damping[k]);
+        return GPR_EINVAL;
+      }
+    }
+  }
+  return run_ppr_batch(jobs, num_jobs, max_iters, tol, dt, (cudaStream_t)stream);
 }
 
 }  // extern "C"

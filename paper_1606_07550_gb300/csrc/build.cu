@@ -115,7 +115,7 @@ __global__ void digit_starts_kernel(const uint32_t* __restrict__ hist, uint32_t*
 // held warp-striped (item j of warp w is tile position w*512 + j*32 + lane),
 // so (warp, item, lane) order is input order and the per-warp match-based
 // ranking keeps the sort stable.
-__global__ void __launch_bounds__(kThreads) onesweep_kernel(
+__global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(
     const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
     const uint32_t* __restrict__ dstart, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
     uint32_t epoch, int* __restrict__ derr) {
@@ -251,36 +251,92 @@ uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cud
   }
 }
 
+// ------------------------------------------------- relabelling (pi) --
+// Raw out-degree counts (duplicates included) of the COO stream, and the
+// id check: an id outside [0, n) raises DERR_BAD_ID.
+__global__ void degree_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                              int32_t n, int32_t* __restrict__ odeg, int* __restrict__ derr) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = __ldcs(src + i), v = __ldcs(dst + i);
+    if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+      bad = true;
+    } else if (u != v) {
+      atomicAdd(odeg + u, 1);
+    }
+  }
+  if (bad) atomicOr(derr, DERR_BAD_ID);
+}
+
+__global__ void max_kernel(const int32_t* __restrict__ a, int32_t n, int32_t* __restrict__ out) {
+  int32_t mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    mx = max(mx, a[i]);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+// Node order key: descending raw out-degree, then ascending id.
+__global__ void node_order_keys_kernel(const int32_t* __restrict__ odeg, int32_t n, int b, int32_t maxdeg,
+                                       uint64_t* __restrict__ keys) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    keys[v] = ((uint64_t)(uint32_t)(maxdeg - odeg[v]) << b) | (uint64_t)v;
+}
+
+__global__ void perm_from_sorted_kernel(const uint64_t* __restrict__ sorted, int32_t n, uint64_t id_mask,
+                                        int32_t* __restrict__ new2old, int32_t* __restrict__ old2new) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = (int32_t)(sorted[p] & id_mask);
+    new2old[p] = v;
+    old2new[v] = (int32_t)p;
+  }
+}
+
 // -------------------------------------------------------------- packing --
-// key = dst << b | src; a self-loop or an id outside [0, n) becomes the
-// sentinel (the latter also raises DERR_BAD_ID).  Counts the digit
+// key = map(dst) << b | map(src) (map = identity if null); a self-loop or an
+// id outside [0, n) becomes the sentinel, which sorts last.  Counts the digit
 // histograms of all radix passes on the way.
-__global__ void pack_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                            int64_t m, int32_t n, int b, int passes, uint64_t* __restrict__ keys,
-                            uint32_t* __restrict__ hist, int* __restrict__ derr) {
+__global__ void pack_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                            int32_t n, int b, const int32_t* __restrict__ map, int passes,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ hist) {
   extern __shared__ uint32_t sh[];
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) sh[i] = 0;
   __syncthreads();
-  bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = __ldcs(src + i), v = __ldcs(dst + i);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t u = __ldcs(src + i), v = __ldcs(dst + i);
     uint64_t key;
-    if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
-      bad = true;
-      key = kSentinel;
-    } else if (u == v) {
+    if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n || u == v) {
       key = kSentinel;
     } else {
+      if (map) {
+        u = map[u];
+        v = map[v];
+      }
       key = ((uint64_t)(uint32_t)v << b) | (uint32_t)u;
     }
     keys[i] = key;
     for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((key >> (8 * p)) & 255)], 1u);
   }
-  if (bad) atomicOr(derr, DERR_BAD_ID);
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Keys of the edges of a CSC under a node map: key = map(row) << b | map(src).
+__global__ void csc_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                                int32_t n, int64_t m, int b, const int32_t* __restrict__ map,
+                                uint64_t* __restrict__ keys) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = n;  // row p: col_ptr[p] <= e < col_ptr[p + 1]
+    while (hi - lo > 1) {
+      const int32_t mid = lo + (hi - lo) / 2;
+      if ((int64_t)col_ptr[mid] <= e)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    keys[e] = ((uint64_t)(uint32_t)map[lo] << b) | (uint32_t)map[row_idx[e]];
+  }
 }
 
 // ------------------------------------------------------------- dedupe ----
@@ -321,11 +377,13 @@ __device__ __forceinline__ uint64_t next_key(const uint64_t (&k)[kItems], int j,
 
 // Sorted keys -> CSC.  Item j of warp w is tile position w*512 + j*32 + lane
 // (input order), so the ballot counts give each kept key its output index.
+// Keeps the first of each run of equal keys and drops sentinels; writes
+// row_idx, the row starts (gaps of empty rows filled) and out-degrees.
 __global__ void __launch_bounds__(kThreads) dedupe_kernel(
     const uint64_t* __restrict__ keys, int64_t m_raw, int b, int32_t n, int32_t* __restrict__ row_idx,
-    int32_t* __restrict__ edge_dst, int32_t* __restrict__ col_ptr, int32_t* __restrict__ outdeg,
-    uint64_t* __restrict__ status, uint32_t* __restrict__ tile_ctr, int64_t* __restrict__ m_out,
-    Gap* __restrict__ gaps, uint32_t* __restrict__ ngaps, int* __restrict__ derr) {
+    int32_t* __restrict__ col_ptr, int32_t* __restrict__ outdeg, uint64_t* __restrict__ status,
+    uint32_t* __restrict__ tile_ctr, int64_t* __restrict__ m_out, Gap* __restrict__ gaps,
+    uint32_t* __restrict__ ngaps, int* __restrict__ derr) {
   __shared__ uint32_t s_wsum[kWarps];
   __shared__ uint64_t s_excl;
   __shared__ uint32_t s_tile;
@@ -343,7 +401,6 @@ __global__ void __launch_bounds__(kThreads) dedupe_kernel(
     int64_t i = base + j * 32;
     k[j] = i < m_raw ? __ldcs(keys + i) : kSentinel;
   }
-  // keep flags in input order
   uint32_t ballot[kItems];
   uint32_t wtotal = 0;
 #pragma unroll
@@ -385,7 +442,6 @@ __global__ void __launch_bounds__(kThreads) dedupe_kernel(
       if (keep) {
         const int32_t u = (int32_t)(k[j] & src_mask);
         row_idx[my_o] = u;
-        edge_dst[my_o] = v;
         atomicAdd(&outdeg[u], 1);
         // rows (pv, v] start at my_o; the previous key is valid because
         // sentinels sort last
@@ -417,8 +473,13 @@ static int id_bits_for(int32_t n) {
   while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
   return b;
 }
+static int bits_for(uint32_t v) {
+  int b = 0;
+  while (b < 32 && (v >> b) != 0) ++b;
+  return b;
+}
 
-struct BuildTemps {
+struct Temps {
   cudaStream_t s;
   std::vector<void*> ptrs;
   void* get(size_t bytes) {
@@ -432,8 +493,44 @@ struct BuildTemps {
   }
 };
 
+static int grid_for(int64_t items, int per_sm = 8) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((items + kThreads - 1) / kThreads, (int64_t)num_sms() * per_sm));
+}
+
+// Sorted unique-or-not keys (length m_keys) -> CSC arrays; returns m.
+static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b, int32_t n, uint32_t* hist,
+                           int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg, int* derr, Temps& tmp,
+                           cudaStream_t s) {
+  GPR_CUDA(cudaMemsetAsync(col_ptr, 0, ((size_t)n + 1) * 4, s));
+  GPR_CUDA(cudaMemsetAsync(outdeg, 0, (size_t)n * 4, s));
+  if (m_keys == 0) return 0;
+  uint64_t* sorted = radix_sort_u64(keys, alt, m_keys, 2 * b, s, derr, hist);
+  const int64_t tiles = (m_keys + kTile - 1) / kTile;
+  uint64_t* status = (uint64_t*)tmp.get((size_t)tiles * 8);
+  uint32_t* ctr = (uint32_t*)tmp.get(8);
+  const int64_t gap_cap = (int64_t)n / kGapInline + 4;
+  Gap* gaps = (Gap*)tmp.get((size_t)gap_cap * sizeof(Gap));
+  uint32_t* ngaps = (uint32_t*)tmp.get(8);
+  int64_t* m_dev = (int64_t*)tmp.get(8);
+  GPR_CUDA(cudaMemsetAsync(status, 0, (size_t)tiles * 8, s));
+  GPR_CUDA(cudaMemsetAsync(ctr, 0, 8, s));
+  GPR_CUDA(cudaMemsetAsync(ngaps, 0, 8, s));
+  GPR_CUDA(cudaMemsetAsync(m_dev, 0, 8, s));
+  dedupe_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(sorted, m_keys, b, n, row_idx, col_ptr, outdeg, status, ctr,
+                                                     m_dev, gaps, ngaps, derr);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(1);
+  gap_fill_kernel<<<num_sms() * 2, kThreads, 0, s>>>(col_ptr, gaps, ngaps);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(1);
+  int64_t m = 0;
+  GPR_CUDA(cudaMemcpyAsync(&m, m_dev, sizeof m, cudaMemcpyDeviceToHost, s));
+  GPR_CUDA(cudaStreamSynchronize(s));
+  return m;
+}
+
 void graph_free_device(gpr_graph* g, cudaStream_t s);
-void plan_build_from(gpr_graph* g, const int32_t* edge_dst, cudaStream_t s, int* derr);
+void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
 
 gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_raw, int32_t n, int flags,
                        cudaStream_t s, gpr_graph** out) {
@@ -442,13 +539,11 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
   g->m_raw = m_raw;
   g->id_bits = id_bits_for(n);
   g->device = device_ordinal();
-  BuildTemps tmp{s, {}};
+  Temps tmp{s, {}};
+  const int b = g->id_bits;
   try {
     int* derr = (int*)tmp.get(sizeof(int) * 2);
-    int64_t* m_dev = (int64_t*)tmp.get(sizeof(int64_t));
     GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
-    GPR_CUDA(cudaMemsetAsync(m_dev, 0, sizeof(int64_t), s));
-
     const int32_t* src = src_in;
     const int32_t* dst = dst_in;
     if ((flags & GPR_PTR_HOST) && m_raw > 0) {
@@ -459,62 +554,77 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       src = s_dev;
       dst = d_dev;
     }
-
+    // 1. relabelling pi: nodes by descending raw out-degree (ties: ascending id)
+    int32_t* odeg = (int32_t*)tmp.get((size_t)n * 4);
+    int32_t* maxd = (int32_t*)tmp.get(8);
+    GPR_CUDA(cudaMemsetAsync(odeg, 0, (size_t)n * 4, s));
+    GPR_CUDA(cudaMemsetAsync(maxd, 0, 8, s));
+    if (m_raw > 0) {
+      degree_kernel<<<grid_for(m_raw), kThreads, 0, s>>>(src, dst, m_raw, n, odeg, derr);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+    }
+    max_kernel<<<grid_for(n), kThreads, 0, s>>>(odeg, n, maxd);
+    GPR_CUDA(cudaGetLastError());
+    count_launches(1);
+    int32_t hmax = 0;
+    int herr = 0;
+    GPR_CUDA(cudaMemcpyAsync(&hmax, maxd, 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    if (herr & DERR_BAD_ID) throw StatusFail{GPR_EINVAL, "graph_build: an edge id is outside [0, n)"};
+    {
+      uint64_t* nk = (uint64_t*)tmp.get((size_t)n * 8);
+      uint64_t* na = (uint64_t*)tmp.get((size_t)n * 8);
+      node_order_keys_kernel<<<grid_for(n), kThreads, 0, s>>>(odeg, n, b, hmax, nk);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      uint64_t* ns = radix_sort_u64(nk, na, n, b + bits_for((uint32_t)hmax), s, derr, nullptr);
+      g->plan.new2old = (int32_t*)dalloc((size_t)n * 4, s);
+      g->plan.old2new = (int32_t*)dalloc((size_t)n * 4, s);
+      perm_from_sorted_kernel<<<grid_for(n), kThreads, 0, s>>>(ns, n, (1ull << b) - 1, g->plan.new2old,
+                                                               g->plan.old2new);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+    }
+    // 2. keys (pi(dst), pi(src)), sort, de-duplicate: the CSC in relabelled ids
     g->col_ptr = (int32_t*)dalloc(((size_t)n + 1) * 4, s);
     g->outdeg = (int32_t*)dalloc((size_t)n * 4, s);
-    GPR_CUDA(cudaMemsetAsync(g->col_ptr, 0, ((size_t)n + 1) * 4, s));
-    GPR_CUDA(cudaMemsetAsync(g->outdeg, 0, (size_t)n * 4, s));
+    int64_t m = 0;
     int32_t* row_idx_full = nullptr;
-    int32_t* edge_dst = nullptr;
     if (m_raw > 0) {
-      const int bits = 2 * g->id_bits;
-      const int passes = (bits + 7) / 8;
+      const int passes = (2 * b + 7) / 8;
       uint64_t* keys = (uint64_t*)tmp.get((size_t)m_raw * 8);
       uint64_t* alt = (uint64_t*)tmp.get((size_t)m_raw * 8);
       uint32_t* hist = (uint32_t*)tmp.get(passes * 256 * 4);
       GPR_CUDA(cudaMemsetAsync(hist, 0, passes * 256 * 4, s));
-      const int grid = (int)std::min<int64_t>((m_raw + kThreads - 1) / kThreads, (int64_t)num_sms() * 8);
-      pack_kernel<<<grid, kThreads, passes * 256 * 4, s>>>(src, dst, m_raw, n, g->id_bits, passes, keys, hist,
-                                                           derr);
+      pack_kernel<<<grid_for(m_raw), kThreads, passes * 256 * 4, s>>>(src, dst, m_raw, n, b, g->plan.old2new,
+                                                                      passes, keys, hist);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
-      uint64_t* sorted = radix_sort_u64(keys, alt, m_raw, bits, s, derr, hist);
-
-      const int64_t tiles = (m_raw + kTile - 1) / kTile;
-      uint64_t* status = (uint64_t*)tmp.get((size_t)tiles * 8);
-      uint32_t* ctr = (uint32_t*)tmp.get(8);
-      const int64_t gap_cap = (int64_t)n / kGapInline + 4;
-      Gap* gaps = (Gap*)tmp.get((size_t)gap_cap * sizeof(Gap));
-      uint32_t* ngaps = (uint32_t*)tmp.get(8);
-      GPR_CUDA(cudaMemsetAsync(status, 0, (size_t)tiles * 8, s));
-      GPR_CUDA(cudaMemsetAsync(ctr, 0, 8, s));
-      GPR_CUDA(cudaMemsetAsync(ngaps, 0, 8, s));
       row_idx_full = (int32_t*)tmp.get((size_t)m_raw * 4);
-      edge_dst = (int32_t*)tmp.get((size_t)m_raw * 4);
-      dedupe_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(sorted, m_raw, g->id_bits, n, row_idx_full, edge_dst,
-                                                         g->col_ptr, g->outdeg, status, ctr, m_dev, gaps, ngaps,
-                                                         derr);
-      GPR_CUDA(cudaGetLastError());
-      count_launches(1);
-      gap_fill_kernel<<<num_sms() * 2, kThreads, 0, s>>>(g->col_ptr, gaps, ngaps);
-      GPR_CUDA(cudaGetLastError());
-      count_launches(1);
+      m = keys_to_csc(keys, alt, m_raw, b, n, hist, g->col_ptr, row_idx_full, g->outdeg, derr, tmp, s);
+    } else {
+      GPR_CUDA(cudaMemsetAsync(g->col_ptr, 0, ((size_t)n + 1) * 4, s));
+      GPR_CUDA(cudaMemsetAsync(g->outdeg, 0, (size_t)n * 4, s));
     }
-    int64_t m = 0;
-    int herr = 0;
-    GPR_CUDA(cudaMemcpyAsync(&m, m_dev, sizeof m, cudaMemcpyDeviceToHost, s));
-    GPR_CUDA(cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s));
-    GPR_CUDA(cudaStreamSynchronize(s));
-    if (herr & DERR_BAD_ID) throw StatusFail{GPR_EINVAL, "graph_build: an edge id is outside [0, n)"};
-    if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_build: a device-side wait timed out"};
     g->m = m;
     g->row_idx = (int32_t*)dalloc((size_t)std::max<int64_t>(m, 1) * 4, s);
     if (m > 0)
       GPR_CUDA(cudaMemcpyAsync(g->row_idx, row_idx_full, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
-    plan_build_from(g, edge_dst, s, derr);
-    GPR_CUDA(cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s));
     tmp.release();
+    // 3. execution layout (degree buckets, chunks, inverse degrees)
+    int* derr2 = (int*)dalloc(8, s);
+    GPR_CUDA(cudaMemsetAsync(derr2, 0, 8, s));
+    try {
+      plan_build(g, s, derr2);
+    } catch (...) {
+      dfree(derr2, s);
+      throw;
+    }
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr2, 4, cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
+    dfree(derr2, s);
     if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_build: a device-side wait timed out"};
     *out = g;
     return GPR_OK;
@@ -532,6 +642,55 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     cudaStreamSynchronize(s);
     delete g;
     set_error("graph_build: %s failed: %s", f.what, cudaGetErrorString(f.err));
+    return GPR_ECUDA;
+  }
+}
+
+// The CSC in the caller's ids: the relabelled edges mapped back through
+// new2old, sorted, and laid out by keys_to_csc (no duplicates remain).
+gpr_status export_graph(const gpr_graph* g, int32_t* col_ptr_h, int32_t* row_idx_h, int32_t* outdeg_h) {
+  cudaStream_t s = nullptr;
+  Temps tmp{s, {}};
+  try {
+    const int32_t n = g->n;
+    const int64_t m = g->m;
+    const int b = g->id_bits;
+    int* derr = (int*)tmp.get(8);
+    GPR_CUDA(cudaMemsetAsync(derr, 0, 8, s));
+    int32_t* cp = (int32_t*)tmp.get(((size_t)n + 1) * 4);
+    int32_t* ri = (int32_t*)tmp.get((size_t)std::max<int64_t>(m, 1) * 4);
+    int32_t* od = (int32_t*)tmp.get((size_t)n * 4);
+    if (m > 0) {
+      uint64_t* keys = (uint64_t*)tmp.get((size_t)m * 8);
+      uint64_t* alt = (uint64_t*)tmp.get((size_t)m * 8);
+      csc_keys_kernel<<<grid_for(m), kThreads, 0, s>>>(g->col_ptr, g->row_idx, n, m, b, g->plan.new2old, keys);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      const int64_t m2 = keys_to_csc(keys, alt, m, b, n, nullptr, cp, ri, od, derr, tmp, s);
+      if (m2 != m) throw StatusFail{GPR_ECUDA, "graph_export: edge count changed under relabelling"};
+    } else {
+      GPR_CUDA(cudaMemsetAsync(cp, 0, ((size_t)n + 1) * 4, s));
+      GPR_CUDA(cudaMemsetAsync(od, 0, (size_t)n * 4, s));
+    }
+    if (col_ptr_h) GPR_CUDA(cudaMemcpy(col_ptr_h, cp, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost));
+    if (row_idx_h && m > 0) GPR_CUDA(cudaMemcpy(row_idx_h, ri, (size_t)m * 4, cudaMemcpyDeviceToHost));
+    if (outdeg_h) GPR_CUDA(cudaMemcpy(outdeg_h, od, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    int herr = 0;
+    GPR_CUDA(cudaMemcpy(&herr, derr, 4, cudaMemcpyDeviceToHost));
+    tmp.release();
+    GPR_CUDA(cudaStreamSynchronize(s));
+    if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_export: a device-side wait timed out"};
+    return GPR_OK;
+  } catch (const StatusFail& f) {
+    tmp.release();
+    cudaStreamSynchronize(s);
+    set_error("%s", f.msg.c_str());
+    return f.st;
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    tmp.release();
+    cudaStreamSynchronize(s);
+    set_error("graph_export: %s failed: %s", f.what, cudaGetErrorString(f.err));
     return GPR_ECUDA;
   }
 }

@@ -64,28 +64,27 @@ uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cud
                          int* derr, uint32_t* hist = nullptr);
 
 // ---- PageRank execution layout -------------------------------------------
-// Rows of the relabelled CSC are grouped by in-degree bucket; within a
-// bucket, by descending out-degree.  Each bucket runs with a fixed number of
-// lanes per row (1..32), or, for the last bucket, in chunks of edges per
-// thread block.
+// The CSC is stored in relabelled ids (descending out-degree).  Rows are run
+// by in-degree bucket from ascending row lists; each bucket has a fixed
+// number of lanes per row (1..32), or, for the last bucket, warp-sized edge
+// chunks (plan.cu).
 constexpr int kMaxBuckets = 6;
 
 struct Bucket {
-  int32_t row_begin, row_end;
-  int lanes;  // 1, 2, 4, 8, 16, 32 lanes per row; 0 = chunked block-per-row
+  int32_t row_begin, row_end;  // range in Plan::rows
+  int lanes;                   // 1, 2, 4, 8, 16, 32 lanes per row; 0 = warp chunks
 };
 
 struct Plan {
-  int32_t* new2old = nullptr;  // n: relabelled row p holds original node new2old[p]
+  int32_t* new2old = nullptr;  // n: relabelled node p is the caller's node new2old[p]
   int32_t* old2new = nullptr;  // n
-  int32_t* col_ptr = nullptr;  // n + 1, relabelled CSC
-  int32_t* row_idx = nullptr;  // m, relabelled source ids
   float* inv_deg = nullptr;    // n, 1/outdeg (0 for dangling)
+  int32_t* rows = nullptr;     // n: rows grouped by bucket, ascending within a bucket
   int nbuckets = 0;
   Bucket bucket[kMaxBuckets];
   int32_t deg_threshold[kMaxBuckets];  // upper in-degree bound of each bucket (last: INT_MAX)
-  // chunks of the block bucket: (row, edge_begin, edge_end) and whether the
-  // chunk is the whole row (1) or a piece of a split row (0)
+  // edge chunks of the warp-chunk bucket: (row, edge_begin, edge_end) and
+  // whether the chunk is the whole row (1) or a piece of a split row (0)
   int32_t* chunk_row = nullptr;
   int32_t* chunk_begin = nullptr;
   int32_t* chunk_end = nullptr;
@@ -110,6 +109,8 @@ struct gpr_graph {
   int32_t n_dangling = 0;
   int32_t max_in = 0, max_out = 0;
   int device = 0;
+  // the CSC in relabelled ids (plan.new2old / plan.old2new): in-adjacency of
+  // row p is row_idx[col_ptr[p] .. col_ptr[p+1]), ascending
   int32_t* col_ptr = nullptr;  // n + 1
   int32_t* row_idx = nullptr;  // m
   int32_t* outdeg = nullptr;   // n
@@ -121,6 +122,7 @@ struct gpr_graph {
 
 namespace gpr {
 void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
+gpr_status export_graph(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg);
 void plan_free(Plan& p, cudaStream_t s);
 void pagerank_work_free(PagerankWork* w);
 

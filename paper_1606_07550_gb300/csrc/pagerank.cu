@@ -9,15 +9,18 @@
 // with coefA = d / S and coefB = (1 - d)/N + d D / (N S), where S = sum(x)
 // and D = the dangling mass of x, both FP64.  This is the step
 //   x'[v] = (1 - d)/N + d (sum_{u->v} x[u]/outdeg(u) + D/N)
-// applied to x / S (mass normalisation).  Each kernel also forms per-block
-// FP64 partials of S', D' and ||x' - x||_1 from FP32 per-thread and per-warp
-// sums; one single-block kernel folds the partials in a fixed order (so
-// repeated runs are bitwise identical) and writes the next coefficients.
+// applied to x / S (mass normalisation).  Every kernel also leaves per-block
+// partials of S', D' and ||x' - x||_1 (FP32 per thread and per warp, FP64
+// across warps); the last block of the step's final kernel folds all of them
+// in a fixed order, so repeated runs are bitwise identical, and writes the
+// next step's coefficients.
 //
-// Rows are processed by in-degree bucket: 1, 4, 8 or 32 lanes per row, and
-// rows above the last lane bucket in chunks of edges per thread block (rows
-// longer than a chunk are split and finished by the fold kernel).  The whole
-// iteration loop is one CUDA graph.
+// Rows run by in-degree bucket from ascending row lists: 1, 4, 8 or 32 lanes
+// per row, and rows above the last lane bucket as warp-sized edge chunks
+// (128-bit index loads, 16 gathers in flight per lane).  A row longer than
+// one chunk is finished from its chunk sums, in chunk order, by the finish
+// kernel.  The bucket kernels of a step are independent and run as parallel
+// branches of one CUDA graph that holds the whole iteration loop.
 #include <algorithm>
 #include <cstring>
 
@@ -44,17 +47,14 @@ __device__ __forceinline__ float ld_rank<__nv_bfloat16>(const __nv_bfloat16* p, 
   return __bfloat162float(__ldg(p + i));
 }
 template <typename T>
-__device__ __forceinline__ float store_rank(T* p, int64_t i, float v);  // returns the stored value
+__device__ __forceinline__ void store_rank(T* p, int64_t i, float v);
 template <>
-__device__ __forceinline__ float store_rank<float>(float* p, int64_t i, float v) {
+__device__ __forceinline__ void store_rank<float>(float* p, int64_t i, float v) {
   p[i] = v;
-  return v;
 }
 template <>
-__device__ __forceinline__ float store_rank<__nv_bfloat16>(__nv_bfloat16* p, int64_t i, float v) {
-  const __nv_bfloat16 b = __float2bfloat16_rn(v);
-  p[i] = b;
-  return __bfloat162float(b);
+__device__ __forceinline__ void store_rank<__nv_bfloat16>(__nv_bfloat16* p, int64_t i, float v) {
+  p[i] = __float2bfloat16_rn(v);
 }
 
 // ---- reductions ----------------------------------------------------------
@@ -105,14 +105,45 @@ __device__ __forceinline__ void finish_row(int64_t r, float y, float A, float B,
   if (idg == 0.0f) dang += xs;
 }
 
-// G lanes per row, G in {1, 2, 4, 8, 16, 32}; warps stride over row groups.
+// Warp-cooperative sum of c over edges [e0, e1): 128-bit index loads on the
+// 16-byte-aligned body, up to 16 gathers in flight per lane.  Every lane
+// returns its own partial; the caller reduces.
+template <typename T>
+__device__ __forceinline__ float warp_gather(const int32_t* __restrict__ row_idx, const T* __restrict__ c_in,
+                                             int32_t e0, int32_t e1, int lane) {
+  float y = 0.f;
+  const int32_t h = min(e1, (e0 + 3) & ~3);
+  if (e0 + lane < h) y += ld_rank(c_in, __ldcs(row_idx + e0 + lane));
+  const int32_t body_end = h + ((e1 - h) & ~3);
+  int32_t e = h + 4 * lane;
+  for (; e + 3 * 128 < body_end; e += 4 * 128) {
+    const int4 q0 = __ldcs(reinterpret_cast<const int4*>(row_idx + e));
+    const int4 q1 = __ldcs(reinterpret_cast<const int4*>(row_idx + e + 128));
+    const int4 q2 = __ldcs(reinterpret_cast<const int4*>(row_idx + e + 256));
+    const int4 q3 = __ldcs(reinterpret_cast<const int4*>(row_idx + e + 384));
+    const float a0 = ld_rank(c_in, q0.x), a1 = ld_rank(c_in, q0.y), a2 = ld_rank(c_in, q0.z), a3 = ld_rank(c_in, q0.w);
+    const float b0 = ld_rank(c_in, q1.x), b1 = ld_rank(c_in, q1.y), b2 = ld_rank(c_in, q1.z), b3 = ld_rank(c_in, q1.w);
+    const float c0 = ld_rank(c_in, q2.x), c1 = ld_rank(c_in, q2.y), c2 = ld_rank(c_in, q2.z), c3 = ld_rank(c_in, q2.w);
+    const float d0 = ld_rank(c_in, q3.x), d1 = ld_rank(c_in, q3.y), d2 = ld_rank(c_in, q3.z), d3 = ld_rank(c_in, q3.w);
+    y += ((a0 + a1) + (a2 + a3)) + ((b0 + b1) + (b2 + b3)) + ((c0 + c1) + (c2 + c3)) + ((d0 + d1) + (d2 + d3));
+  }
+  for (; e < body_end; e += 128) {
+    const int4 q = __ldcs(reinterpret_cast<const int4*>(row_idx + e));
+    const float a0 = ld_rank(c_in, q.x), a1 = ld_rank(c_in, q.y), a2 = ld_rank(c_in, q.z), a3 = ld_rank(c_in, q.w);
+    y += (a0 + a1) + (a2 + a3);
+  }
+  if (body_end + lane < e1) y += ld_rank(c_in, __ldcs(row_idx + body_end + lane));
+  return y;
+}
+
+// G lanes per row (G in {1, 2, 4, 8, 16, 32}) over rows[i0, i1).
 template <int G, typename T>
 __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ col_ptr,
-                                                   const int32_t* __restrict__ row_idx, const T* __restrict__ c_in,
+                                                   const int32_t* __restrict__ row_idx, const int32_t* __restrict__ rows,
+                                                   int32_t i0, int32_t i1, const T* __restrict__ c_in,
                                                    const float* __restrict__ x_in, const float* __restrict__ inv_deg,
-                                                   float* __restrict__ x_out, T* __restrict__ c_out, int32_t r0,
-                                                   int32_t r1, const StepParams* __restrict__ prm,
-                                                   double* __restrict__ partials) {
+                                                   float* __restrict__ x_out, T* __restrict__ c_out,
+                                                   const StepParams* __restrict__ prm, double* __restrict__ partials) {
   const float A = prm->coefA, B = prm->coefB;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
@@ -120,28 +151,20 @@ __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ c
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   float mass = 0.f, dang = 0.f, res = 0.f;
-  for (int64_t wr = r0 + warp * kRowsPerWarp; wr < r1; wr += nwarps * kRowsPerWarp) {
-    const int64_t r = wr + lane / G;
-    const bool active = r < r1;
-    int32_t e0 = 0, e1 = 0;
+  for (int64_t wi = i0 + warp * kRowsPerWarp; wi < i1; wi += nwarps * kRowsPerWarp) {
+    const int64_t i = wi + lane / G;
+    const bool active = i < i1;
+    int32_t r = 0, e0 = 0, e1 = 0;
     if (active) {
+      r = rows[i];
       e0 = col_ptr[r];
       e1 = col_ptr[r + 1];
     }
-    float y = 0.f;
+    float y;
     if constexpr (G == 32) {
-      // 128-bit index loads on the 16-byte-aligned body of the row
-      const int32_t h = min(e1, (e0 + 3) & ~3);
-      if (e0 + lane < h) y += ld_rank(c_in, __ldcs(row_idx + e0 + lane));
-      const int32_t body_end = h + ((e1 - h) & ~3);
-      for (int32_t e = h + 4 * lane; e < body_end; e += 128) {
-        const int4 q = __ldcs(reinterpret_cast<const int4*>(row_idx + e));
-        const float a0 = ld_rank(c_in, q.x), a1 = ld_rank(c_in, q.y);
-        const float a2 = ld_rank(c_in, q.z), a3 = ld_rank(c_in, q.w);
-        y += (a0 + a1) + (a2 + a3);
-      }
-      if (body_end + lane < e1) y += ld_rank(c_in, __ldcs(row_idx + body_end + lane));
+      y = warp_gather(row_idx, c_in, e0, e1, lane);
     } else {
+      y = 0.f;
       for (int32_t e = e0 + sub; e < e1; e += G) y += ld_rank(c_in, __ldcs(row_idx + e));
     }
 #pragma unroll
@@ -151,44 +174,29 @@ __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ c
   block_partials3(mass, dang, res, partials + 3 * (int64_t)blockIdx.x);
 }
 
-// One chunk of edges per block iteration.  A chunk that is a whole row is
-// finished here; a piece of a split row leaves its sum in chunk_sum.
+// One edge chunk per warp.  A chunk that is a whole row is finished here; a
+// piece of a split row leaves its sum in chunk_sum.
 template <typename T>
-__global__ void __launch_bounds__(256) chunks_kernel(
+__global__ void __launch_bounds__(256) wchunks_kernel(
     const int32_t* __restrict__ row_idx, const T* __restrict__ c_in, const float* __restrict__ x_in,
     const float* __restrict__ inv_deg, float* __restrict__ x_out, T* __restrict__ c_out,
     const int32_t* __restrict__ chunk_row, const int32_t* __restrict__ chunk_begin,
     const int32_t* __restrict__ chunk_end, const int32_t* __restrict__ chunk_whole, int32_t nchunks,
     float* __restrict__ chunk_sum, const StepParams* __restrict__ prm, double* __restrict__ partials) {
-  __shared__ float s_w[8];
   const float A = prm->coefA, B = prm->coefB;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   float mass = 0.f, dang = 0.f, res = 0.f;
-  for (int32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+  for (int64_t ch = warp; ch < nchunks; ch += nwarps) {
     const int32_t e0 = chunk_begin[ch], e1 = chunk_end[ch];
-    float y = 0.f;
-    const int32_t h = min(e1, (e0 + 3) & ~3);
-    if (e0 + t < h) y += ld_rank(c_in, __ldcs(row_idx + e0 + t));
-    const int32_t body_end = h + ((e1 - h) & ~3);
-    for (int32_t e = h + 4 * t; e < body_end; e += 4 * 256) {
-      const int4 q = __ldcs(reinterpret_cast<const int4*>(row_idx + e));
-      const float a0 = ld_rank(c_in, q.x), a1 = ld_rank(c_in, q.y);
-      const float a2 = ld_rank(c_in, q.z), a3 = ld_rank(c_in, q.w);
-      y += (a0 + a1) + (a2 + a3);
-    }
-    if (body_end + t < e1) y += ld_rank(c_in, __ldcs(row_idx + body_end + t));
-    y = warp_sum(y);
-    if (lane == 0) s_w[w] = y;
-    __syncthreads();
-    if (t == 0) {
-      float tot = 0.f;
-      for (int i = 0; i < 8; ++i) tot += s_w[i];
+    const float y = warp_sum(warp_gather(row_idx, c_in, e0, e1, lane));
+    if (lane == 0) {
       if (chunk_whole[ch])
-        finish_row(chunk_row[ch], tot, A, B, x_in, inv_deg, x_out, c_out, mass, dang, res);
+        finish_row(chunk_row[ch], y, A, B, x_in, inv_deg, x_out, c_out, mass, dang, res);
       else
-        chunk_sum[ch] = tot;
+        chunk_sum[ch] = y;
     }
-    __syncthreads();
   }
   block_partials3(mass, dang, res, partials + 3 * (int64_t)blockIdx.x);
 }
@@ -201,39 +209,47 @@ __global__ void init_kernel(float* __restrict__ x, T* __restrict__ c, const floa
   const float x0 = 1.0f / (float)n;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const float idg = inv_deg[v];
-    const float xs = x0;
-    x[v] = xs;
-    store_rank(c, v, xs * idg);
-    mass += xs;
-    if (idg == 0.0f) dang += xs;
+    x[v] = x0;
+    store_rank(c, v, x0 * idg);
+    mass += x0;
+    if (idg == 0.0f) dang += x0;
   }
   block_partials3(mass, dang, 0.f, partials + 3 * (int64_t)blockIdx.x);
 }
 
-// Single block: finish split rows, fold all block partials in a fixed order,
-// log (mass, dangling, residual) for step `it` and write the next
-// coefficients.
+// Finishes the split rows (grid-stride, chunk sums added in chunk order),
+// then the last block to arrive folds all `npartials` block partials of the
+// step (this kernel's own are the last gridDim.x of them) in index order,
+// logs (mass, dangling, residual) and writes the next coefficients.
 template <typename T>
-__global__ void __launch_bounds__(1024) fold_kernel(
+__global__ void __launch_bounds__(256) finish_kernel(
     const float* __restrict__ x_in, const float* __restrict__ inv_deg, float* __restrict__ x_out,
     T* __restrict__ c_out, const int32_t* __restrict__ split_row, const int32_t* __restrict__ split_cbeg,
     const int32_t* __restrict__ split_cend, int32_t nsplit, const float* __restrict__ chunk_sum,
-    const double* __restrict__ partials, int32_t npartials, StepParams* __restrict__ prm,
-    double* __restrict__ log_row) {
-  __shared__ double s[3][32];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    double* __restrict__ partials, int32_t npartials, StepParams* __restrict__ prm, double* __restrict__ log_row,
+    unsigned int* __restrict__ arrive) {
+  __shared__ bool s_last;
   const float A = prm->coefA, B = prm->coefB;
   float fm = 0.f, fd = 0.f, fr = 0.f;
-  for (int32_t i = t; i < nsplit; i += blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsplit; i += (int64_t)gridDim.x * blockDim.x) {
     float y = 0.f;
     for (int32_t c = split_cbeg[i]; c < split_cend[i]; ++c) y += chunk_sum[c];
     finish_row(split_row[i], y, A, B, x_in, inv_deg, x_out, c_out, fm, fd, fr);
   }
-  double a = fm, b = fd, c = fr;
-  for (int32_t i = t; i < npartials; i += blockDim.x) {
-    a += partials[3 * (int64_t)i];
-    b += partials[3 * (int64_t)i + 1];
-    c += partials[3 * (int64_t)i + 2];
+  block_partials3(fm, fd, fr, partials + 3 * (int64_t)(npartials - gridDim.x + blockIdx.x));
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(arrive, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  __shared__ double s[3][8];
+  double a = 0, b = 0, c = 0;
+  for (int32_t i = threadIdx.x; i < npartials; i += blockDim.x) {
+    a += __ldcg(partials + 3 * (int64_t)i);
+    b += __ldcg(partials + 3 * (int64_t)i + 1);
+    c += __ldcg(partials + 3 * (int64_t)i + 2);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -241,13 +257,14 @@ __global__ void __launch_bounds__(1024) fold_kernel(
     b += __shfl_xor_sync(0xffffffffu, b, o);
     c += __shfl_xor_sync(0xffffffffu, c, o);
   }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     s[0][w] = a;
     s[1][w] = b;
     s[2][w] = c;
   }
   __syncthreads();
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     double mass = 0, dang = 0, res = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       mass += s[0][i];
@@ -260,6 +277,7 @@ __global__ void __launch_bounds__(1024) fold_kernel(
     const double d = prm->d, n = prm->n;
     prm->coefA = (float)(d / mass);
     prm->coefB = (float)((1.0 - d) / n + d * dang / (n * mass));
+    *arrive = 0;  // ready for the next step
   }
 }
 
@@ -278,18 +296,23 @@ struct LaunchShape {
 
 struct PagerankWork {
   int device = 0;
-  void* x[2] = {nullptr, nullptr};  // n floats each: the rank vector, always FP32
-  void* c[2] = {nullptr, nullptr};  // n * 4 bytes each: contributions x / outdeg, FP32 or BF16
-  float* out_tmp = nullptr;         // n floats, for host-pointer output
+  float* x[2] = {nullptr, nullptr};  // n floats each: the rank vector, always FP32
+  void* c[2] = {nullptr, nullptr};   // n * 4 bytes each: contributions x / outdeg, FP32 or BF16
+  float* out_tmp = nullptr;          // n floats, for host-pointer output
   double* partials = nullptr;
-  int32_t npartials = 0;
+  int32_t npartials = 0;  // per step: bucket kernels' blocks + finish blocks
   float* chunk_sum = nullptr;
   StepParams* prm = nullptr;
+  unsigned int* arrive = nullptr;
   double* log = nullptr;  // (iters + 1) x 3
   int32_t log_cap = 0;
   LaunchShape shape[kMaxBuckets];
-  LaunchShape init_shape;
+  int finish_grid = 1;
+  int init_grid = 1;
   cudaStream_t cap = nullptr;
+  cudaStream_t side[kMaxBuckets] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kMaxBuckets] = {};
   cudaGraphExec_t exec = nullptr;
   int32_t exec_iters = -1;
   int exec_dt = -1;
@@ -308,7 +331,13 @@ void pagerank_work_free(PagerankWork* w) {
   dfree(w->partials, s);
   dfree(w->chunk_sum, s);
   dfree(w->prm, s);
+  dfree(w->arrive, s);
   dfree(w->log, s);
+  if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+  for (int i = 0; i < kMaxBuckets; ++i) {
+    if (w->ev_join[i]) cudaEventDestroy(w->ev_join[i]);
+    if (w->side[i]) cudaStreamDestroy(w->side[i]);
+  }
   if (s) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
@@ -316,41 +345,37 @@ void pagerank_work_free(PagerankWork* w) {
   delete w;
 }
 
-template <int G, typename T>
-static int rows_grid(int64_t rows) {
+template <typename K>
+static int resident_grid(K kernel, int64_t blocks_needed) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_kernel<G, T>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
   per_sm = std::max(per_sm, 1);
-  const int64_t warps = (rows + (32 / G) - 1) / (32 / G);
-  const int64_t blocks = (warps + 7) / 8;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms() * per_sm));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, (int64_t)num_sms() * per_sm));
 }
 
 template <typename T>
 static int grid_for_bucket(const Bucket& b, int32_t nchunks) {
   const int64_t rows = b.row_end - b.row_begin;
+  auto blocks = [&](int G) { return (rows * G + 255) / 256; };
   switch (b.lanes) {
-    case 1: return rows_grid<1, T>(rows);
-    case 2: return rows_grid<2, T>(rows);
-    case 4: return rows_grid<4, T>(rows);
-    case 8: return rows_grid<8, T>(rows);
-    case 16: return rows_grid<16, T>(rows);
-    case 32: return rows_grid<32, T>(rows);
-    default: {
-      int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chunks_kernel<T>, 256, 0);
-      per_sm = std::max(per_sm, 1);
-      return (int)std::max<int64_t>(1, std::min<int64_t>(nchunks, (int64_t)num_sms() * per_sm));
-    }
+    case 1: return resident_grid(rows_kernel<1, T>, blocks(1));
+    case 2: return resident_grid(rows_kernel<2, T>, blocks(2));
+    case 4: return resident_grid(rows_kernel<4, T>, blocks(4));
+    case 8: return resident_grid(rows_kernel<8, T>, blocks(8));
+    case 16: return resident_grid(rows_kernel<16, T>, blocks(16));
+    case 32: return resident_grid(rows_kernel<32, T>, blocks(32));
+    default: return resident_grid(wchunks_kernel<T>, ((int64_t)nchunks + 7) / 8);
   }
 }
 
 template <typename T>
-static void launch_rows(const Bucket& b, int grid, cudaStream_t s, const Plan& P, const T* c_in, const float* x_in,
-                        float* x_out, T* c_out, const StepParams* prm, double* part) {
-#define GPR_ROWS(GL)                                                                                       \
-  rows_kernel<GL, T><<<grid, 256, 0, s>>>(P.col_ptr, P.row_idx, c_in, x_in, P.inv_deg, x_out, c_out, b.row_begin, \
-                                          b.row_end, prm, part)
+static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_graph* g, const T* c_in,
+                          const float* x_in, float* x_out, T* c_out, float* chunk_sum, const StepParams* prm,
+                          double* part) {
+  const Plan& P = g->plan;
+#define GPR_ROWS(GL)                                                                                        \
+  rows_kernel<GL, T><<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, P.rows, b.row_begin, b.row_end, c_in, x_in, \
+                                          P.inv_deg, x_out, c_out, prm, part)
   switch (b.lanes) {
     case 1: GPR_ROWS(1); break;
     case 2: GPR_ROWS(2); break;
@@ -358,35 +383,39 @@ static void launch_rows(const Bucket& b, int grid, cudaStream_t s, const Plan& P
     case 8: GPR_ROWS(8); break;
     case 16: GPR_ROWS(16); break;
     case 32: GPR_ROWS(32); break;
-    default: break;
+    default:
+      wchunks_kernel<T><<<grid, 256, 0, s>>>(g->row_idx, c_in, x_in, P.inv_deg, x_out, c_out, P.chunk_row,
+                                             P.chunk_begin, P.chunk_end, P.chunk_whole, P.nchunks, chunk_sum, prm,
+                                             part);
+      break;
   }
 #undef GPR_ROWS
 }
 
+// Records init + `iters` steps on w->cap (which is capturing).  The bucket
+// kernels of a step fork onto side streams and join before the finish kernel.
 template <typename T>
-static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, cudaStream_t s) {
+static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters) {
   const Plan& P = g->plan;
-  float* x[2] = {(float*)w->x[0], (float*)w->x[1]};
+  cudaStream_t s = w->cap;
+  float* x[2] = {w->x[0], w->x[1]};
   T* c[2] = {(T*)w->c[0], (T*)w->c[1]};
-  init_kernel<T><<<w->init_shape.grid, 256, 0, s>>>(x[0], c[0], P.inv_deg, g->n, w->partials);
-  fold_kernel<T><<<1, 1024, 0, s>>>(x[0], P.inv_deg, x[0], c[0], P.split_row, P.split_cbeg, P.split_cend, 0,
-                                   w->chunk_sum, w->partials, w->init_shape.grid, w->prm, w->log);
+  init_kernel<T><<<w->init_grid, 256, 0, s>>>(x[0], c[0], P.inv_deg, g->n, w->partials);
+  finish_kernel<T><<<1, 256, 0, s>>>(x[0], P.inv_deg, x[0], c[0], P.split_row, P.split_cbeg, P.split_cend, 0,
+                                    w->chunk_sum, w->partials, w->init_grid + 1, w->prm, w->log, w->arrive);
   for (int32_t it = 0; it < iters; ++it) {
     const int a = it & 1, b = a ^ 1;
+    GPR_CUDA(cudaEventRecord(w->ev_fork, s));
     for (int bi = 0; bi < P.nbuckets; ++bi) {
-      const Bucket& bk = P.bucket[bi];
-      double* part = w->partials + 3 * (int64_t)w->shape[bi].partial_off;
-      if (bk.lanes == 0) {
-        chunks_kernel<T><<<w->shape[bi].grid, 256, 0, s>>>(P.row_idx, c[a], x[a], P.inv_deg, x[b], c[b],
-                                                           P.chunk_row, P.chunk_begin, P.chunk_end, P.chunk_whole,
-                                                           P.nchunks, w->chunk_sum, w->prm, part);
-      } else {
-        launch_rows<T>(bk, w->shape[bi].grid, s, P, c[a], x[a], x[b], c[b], w->prm, part);
-      }
+      GPR_CUDA(cudaStreamWaitEvent(w->side[bi], w->ev_fork, 0));
+      launch_bucket<T>(P.bucket[bi], w->shape[bi].grid, w->side[bi], g, c[a], x[a], x[b], c[b], w->chunk_sum, w->prm,
+                       w->partials + 3 * (int64_t)w->shape[bi].partial_off);
+      GPR_CUDA(cudaEventRecord(w->ev_join[bi], w->side[bi]));
+      GPR_CUDA(cudaStreamWaitEvent(s, w->ev_join[bi], 0));
     }
-    fold_kernel<T><<<1, 1024, 0, s>>>(x[a], P.inv_deg, x[b], c[b], P.split_row, P.split_cbeg, P.split_cend,
-                                     P.nsplit, w->chunk_sum, w->partials, w->npartials, w->prm,
-                                     w->log + 3 * (int64_t)(it + 1));
+    finish_kernel<T><<<w->finish_grid, 256, 0, s>>>(x[a], P.inv_deg, x[b], c[b], P.split_row, P.split_cbeg,
+                                                    P.split_cend, P.nsplit, w->chunk_sum, w->partials, w->npartials,
+                                                    w->prm, w->log + 3 * (int64_t)(it + 1), w->arrive);
   }
 }
 
@@ -395,29 +424,35 @@ static PagerankWork* work_make(gpr_graph* g, cudaStream_t s) {
   w->device = g->device;
   try {
     GPR_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+    for (int i = 0; i < kMaxBuckets; ++i) {
+      GPR_CUDA(cudaStreamCreateWithFlags(&w->side[i], cudaStreamNonBlocking));
+      GPR_CUDA(cudaEventCreateWithFlags(&w->ev_join[i], cudaEventDisableTiming));
+    }
+    GPR_CUDA(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
     const size_t vb = (size_t)g->n * 4;
     for (int i = 0; i < 2; ++i) {
-      w->x[i] = dalloc(vb, s);
+      w->x[i] = (float*)dalloc(vb, s);
       w->c[i] = dalloc(vb, s);
     }
     const Plan& P = g->plan;
     int off = 0;
     for (int bi = 0; bi < P.nbuckets; ++bi) {
-      // grid sizes of both storage types agree (same kernels' occupancy up to
-      // register use); take the FP32 ones and the max with BF16
-      int g32 = grid_for_bucket<float>(P.bucket[bi], P.nchunks);
-      int g16 = grid_for_bucket<__nv_bfloat16>(P.bucket[bi], P.nchunks);
+      const int g32 = grid_for_bucket<float>(P.bucket[bi], P.nchunks);
+      const int g16 = grid_for_bucket<__nv_bfloat16>(P.bucket[bi], P.nchunks);
       w->shape[bi].grid = std::max(g32, g16);
       w->shape[bi].partial_off = off;
       off += w->shape[bi].grid;
     }
-    w->npartials = off;
-    w->init_shape.grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, num_sms() * 4));
-    const int32_t np = std::max(w->npartials, w->init_shape.grid);
+    w->finish_grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)P.nsplit + 255) / 256, num_sms() * 2));
+    w->npartials = off + w->finish_grid;
+    w->init_grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, num_sms() * 4));
+    const int32_t np = std::max(w->npartials, w->init_grid + 1);
     w->partials = (double*)dalloc((size_t)np * 3 * sizeof(double), s);
     GPR_CUDA(cudaMemsetAsync(w->partials, 0, (size_t)np * 3 * sizeof(double), s));
     w->chunk_sum = (float*)dalloc((size_t)std::max(P.nchunks, 1) * 4, s);
     w->prm = (StepParams*)dalloc(sizeof(StepParams), s);
+    w->arrive = (unsigned int*)dalloc(16, s);
+    GPR_CUDA(cudaMemsetAsync(w->arrive, 0, 16, s));
     return w;
   } catch (...) {
     pagerank_work_free(w);
@@ -454,10 +489,17 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
       GPR_CUDA(cudaStreamSynchronize(s));
       cudaGraph_t graph = nullptr;
       GPR_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
-      if (dt == GPR_BF16)
-        record_iterations<__nv_bfloat16>(g, w, iters, w->cap);
-      else
-        record_iterations<float>(g, w, iters, w->cap);
+      try {
+        if (dt == GPR_BF16)
+          record_iterations<__nv_bfloat16>(g, w, iters);
+        else
+          record_iterations<float>(g, w, iters);
+      } catch (...) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(w->cap, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        throw;
+      }
       cudaError_t e = cudaStreamEndCapture(w->cap, &graph);
       if (e != cudaSuccess) throw CudaFail{e, "cudaStreamEndCapture"};
       e = cudaGraphInstantiate(&w->exec, graph, 0);
@@ -472,14 +514,14 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
     }
     GPR_CUDA(cudaGraphLaunch(w->exec, s));
     count_launches(w->exec_kernels);
-    const void* xf = w->x[iters & 1];
+    const float* xf = w->x[iters & 1];
     float* dst = (flags & GPR_PTR_HOST) ? nullptr : x_out;
     if (!dst) {
       if (!w->out_tmp) w->out_tmp = (float*)dalloc((size_t)g->n * 4, s);
       dst = w->out_tmp;
     }
     const int og = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, num_sms() * 8));
-    output_kernel<<<og, 256, 0, s>>>((const float*)xf, g->plan.old2new, g->n, dst);
+    output_kernel<<<og, 256, 0, s>>>(xf, g->plan.old2new, g->n, dst);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
     if (flags & GPR_PTR_HOST) {

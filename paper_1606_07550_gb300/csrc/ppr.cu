@@ -1,0 +1,532 @@
+// Batched personalised PageRank (section 4 Table "snap_methods" and section
+// 4.3, "Fast Random Walk Algorithms": personalised PageRank scores from the
+// point of view of a given node).
+//
+// One column per seed s with teleport vector e_s, the dangling mass of each
+// column returned to its own seed:
+//   x_0 = e_s,  x_{k+1}[v] = (1 - d) e_s[v] + d (sum_{u->v} x_k[u]/outdeg(u) + D_k e_s[v])
+// A job is one graph with up to 64 columns, stored node-major (row p holds
+// the 64 columns of node p): the pull step gathers whole 256-byte rows
+// (128 bytes with BF16 contributions), one warp per row, two columns per
+// lane.  Rows longer than one warp's fair share are handled by the whole
+// block with a fixed-order combine.
+//
+// Each job runs on one thread-block cluster for all of its steps.  The
+// cluster's blocks split the rows by edge count; after each step they meet at
+// the hardware cluster barrier, then every block folds the per-column FP64
+// partials of all blocks (read through distributed shared memory) in rank
+// order, so every block holds identical D, residual and stop decisions.
+// Clusters pull jobs from a global queue (largest first) until it is empty:
+// one persistent launch covers the whole batch.
+//
+// Per-column arithmetic does not depend on the other columns of a job or on
+// the batch around it: a column gives the same bits alone or in any mix.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <climits>
+#include <numeric>
+#include <vector>
+
+#include "gpr_internal.cuh"
+#include "ppr_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gpr {
+
+constexpr int kPprThreads = 512;
+constexpr int kPprWarps = kPprThreads / 32;
+
+__device__ __forceinline__ float2 ld_pair(const float* p) { return __ldcg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ float2 ld_pair(const __nv_bfloat16* p) {
+  const unsigned int u = __ldcg(reinterpret_cast<const unsigned int*>(p));
+  __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u);
+  return __bfloat1622float2(b);
+}
+__device__ __forceinline__ void st_pair(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void st_pair(__nv_bfloat16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+template <typename T>
+__device__ __forceinline__ void st_one(T* p, float a);
+template <>
+__device__ __forceinline__ void st_one<float>(float* p, float a) {
+  *p = a;
+}
+template <>
+__device__ __forceinline__ void st_one<__nv_bfloat16>(__nv_bfloat16* p, float a) {
+  *p = __float2bfloat16_rn(a);
+}
+
+// Sum of the contribution rows of the sources of edges [e0, e1), two columns
+// per lane.  Warp-cooperative: all lanes call it with the same range; each
+// group of 32 indices is loaded once, coalesced, and broadcast by shuffles.
+template <typename T>
+__device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx, const T* __restrict__ C,
+                                             int32_t e0, int32_t e1, int lane) {
+  float ax = 0.f, ay = 0.f;
+  for (int32_t e = e0; e < e1; e += 32) {
+    const int32_t idx = (e + lane < e1) ? __ldcs(row_idx + e + lane) : 0;
+    const int cnt = min(32, e1 - e);
+    int j = 0;
+    for (; j + 4 <= cnt; j += 4) {
+      const int32_t u0 = __shfl_sync(0xffffffffu, idx, j), u1 = __shfl_sync(0xffffffffu, idx, j + 1);
+      const int32_t u2 = __shfl_sync(0xffffffffu, idx, j + 2), u3 = __shfl_sync(0xffffffffu, idx, j + 3);
+      const float2 v0 = ld_pair(C + (int64_t)u0 * kPprCols + 2 * lane);
+      const float2 v1 = ld_pair(C + (int64_t)u1 * kPprCols + 2 * lane);
+      const float2 v2 = ld_pair(C + (int64_t)u2 * kPprCols + 2 * lane);
+      const float2 v3 = ld_pair(C + (int64_t)u3 * kPprCols + 2 * lane);
+      ax += (v0.x + v1.x) + (v2.x + v3.x);
+      ay += (v0.y + v1.y) + (v2.y + v3.y);
+    }
+    for (; j < cnt; ++j) {
+      const int32_t u = __shfl_sync(0xffffffffu, idx, j);
+      const float2 v = ld_pair(C + (int64_t)u * kPprCols + 2 * lane);
+      ax += v.x;
+      ay += v.y;
+    }
+  }
+  return make_float2(ax, ay);
+}
+
+struct ColRegs {
+  float a0, a1;    // d of the two columns
+  float b0, b1;    // seed coefficient (1 - d) + d D
+  int32_t s0, s1;  // relabelled seed rows
+  bool l0, l1;     // live
+};
+
+template <typename T>
+__device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, const ColRegs& c, float* __restrict__ X,
+                                               T* __restrict__ Cout, const float* __restrict__ inv_deg, int lane,
+                                               float (&acc)[2][3]) {
+  const float inv = inv_deg[p];
+  float* xp = X + (int64_t)p * kPprCols + 2 * lane;
+  const float2 xo = *reinterpret_cast<const float2*>(xp);
+  const float n0 = c.l0 ? fmaf(c.a0, y.x, p == c.s0 ? c.b0 : 0.f) : xo.x;
+  const float n1 = c.l1 ? fmaf(c.a1, y.y, p == c.s1 ? c.b1 : 0.f) : xo.y;
+  *reinterpret_cast<float2*>(xp) = make_float2(n0, n1);
+  st_pair(Cout + (int64_t)p * kPprCols + 2 * lane, n0 * inv, n1 * inv);
+  acc[0][0] += n0;
+  acc[1][0] += n1;
+  if (inv == 0.f) {
+    acc[0][1] += n0;
+    acc[1][1] += n1;
+  }
+  acc[0][2] += fabsf(n0 - xo.x);
+  acc[1][2] += fabsf(n1 - xo.y);
+}
+
+__device__ __forceinline__ int32_t lower_bound_i32(const int32_t* a, int32_t n, int64_t key) {
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int32_t mid = lo + (hi - lo) / 2;
+    if ((int64_t)a[mid] < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict__ jobs,
+                                                            const int32_t* __restrict__ order, int32_t njobs,
+                                                            uint32_t* __restrict__ queue, char* __restrict__ ws,
+                                                            int64_t ws_stride, int32_t cluster_size) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank();
+  const int64_t cid = blockIdx.x / cluster_size;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  __shared__ int s_job;
+  __shared__ float s_wpart[kPprWarps][3][kPprCols];
+  __shared__ double s_part[2][3][kPprCols];
+  __shared__ float s_heavy[kPprWarps][kPprCols];
+  __shared__ int32_t s_seed[kPprCols];
+  __shared__ float s_d[kPprCols], s_tol[kPprCols];
+  __shared__ double s_D[kPprCols], s_res[kPprCols];
+  __shared__ int32_t s_status[kPprCols], s_iters[kPprCols], s_maxit[kPprCols], s_newdone[kPprCols];
+
+  for (;;) {
+    if (crank == 0 && tid == 0) s_job = (int)atomicAdd(queue, 1u);
+    cl.sync();
+    const int jq = *cl.map_shared_rank(&s_job, 0);
+    cl.sync();
+    if (jq >= njobs) break;
+    PprJob* J = &jobs[order[jq]];
+    const int32_t n = J->n;
+    const int32_t* __restrict__ col_ptr = J->col_ptr;
+    const int32_t* __restrict__ row_idx = J->row_idx;
+    const float* __restrict__ inv_deg = J->inv_deg;
+    const bool own_state = J->X != nullptr;
+    float* X;
+    T* Cb[2];
+    if (own_state) {
+      X = J->X;
+      Cb[0] = (T*)J->C0;
+      Cb[1] = (T*)J->C1;
+    } else {
+      char* base = ws + cid * ws_stride;
+      X = (float*)base;
+      Cb[0] = (T*)(base + (int64_t)J->n_cap * kPprCols * 4);
+      Cb[1] = Cb[0] + (int64_t)J->n_cap * kPprCols;
+    }
+    int parity = J->parity;
+
+    // this block's rows: split by edge count
+    const int64_t m = col_ptr[n];
+    auto split = [&](int r) -> int32_t {
+      if (r <= 0) return 0;
+      if (r >= cluster_size) return n;
+      return lower_bound_i32(col_ptr, n + 1, (m * r + cluster_size - 1) / cluster_size);
+    };
+    const int32_t r0 = min(split(crank), n), r1 = max(r0, min(split(crank + 1), n));
+    // long rows of this block: the part of the (ascending) long-row list in [r0, r1)
+    const int32_t h0 = lower_bound_i32(J->heavy_rows, J->n_heavy, r0);
+    const int32_t h1 = lower_bound_i32(J->heavy_rows, J->n_heavy, r1);
+    const int32_t heavy_deg = J->heavy_deg;
+
+    // column records
+    if (tid < kPprCols) {
+      const PprCol cr = J->cols[tid];
+      s_status[tid] = cr.status;
+      s_newdone[tid] = 0;
+      if (cr.status == kColFresh) {
+        s_seed[tid] = J->old2new[cr.seed];
+        s_D[tid] = inv_deg[s_seed[tid]] == 0.f ? 1.0 : 0.0;
+        s_iters[tid] = 0;
+        s_res[tid] = 0.0;
+      } else {
+        s_seed[tid] = cr.status == kColEmpty ? -1 : J->old2new[cr.seed];
+        s_D[tid] = cr.dangling;
+        s_iters[tid] = cr.iters;
+        s_res[tid] = cr.residual;
+      }
+      s_d[tid] = cr.damping;
+      s_tol[tid] = cr.tol;
+      s_maxit[tid] = cr.max_iters;
+    }
+    __syncthreads();
+    // fresh columns start at e_seed in X and in the current contribution buffer
+    {
+      T* Cc = Cb[parity];
+      if (!own_state) {
+        for (int64_t i = (int64_t)r0 * kPprCols + tid; i < (int64_t)r1 * kPprCols; i += kPprThreads) {
+          X[i] = 0.f;
+          st_one(Cc + i, 0.f);
+        }
+      } else {
+        for (int k = 0; k < kPprCols; ++k) {
+          if (s_status[k] != kColFresh) continue;
+          for (int32_t p = r0 + tid; p < r1; p += kPprThreads) {
+            X[(int64_t)p * kPprCols + k] = 0.f;
+            st_one(Cc + (int64_t)p * kPprCols + k, 0.f);
+          }
+        }
+      }
+      __syncthreads();
+      if (tid < kPprCols && s_status[tid] == kColFresh) {
+        const int32_t s = s_seed[tid];
+        if (s >= r0 && s < r1) {
+          X[(int64_t)s * kPprCols + tid] = 1.f;
+          st_one(Cc + (int64_t)s * kPprCols + tid, inv_deg[s]);
+        }
+      }
+      __syncthreads();
+      if (tid < kPprCols && s_status[tid] == kColFresh) s_status[tid] = kColRunning;
+      // a column with no steps to run is finished as it stands
+      if (tid < kPprCols && s_status[tid] == kColRunning && s_iters[tid] >= s_maxit[tid]) {
+        s_status[tid] = kColDone;
+        s_newdone[tid] = 1;
+      }
+    }
+    cl.sync();
+
+    for (int32_t it = 0; it < J->iters; ++it) {
+      // any live column left?
+      const int live_any = __syncthreads_or(tid < kPprCols && s_status[tid] == kColRunning);
+      if (!live_any) break;
+      const T* __restrict__ Cin = Cb[parity];
+      T* __restrict__ Cout = Cb[parity ^ 1];
+      ColRegs c;
+      {
+        const int k0 = 2 * lane, k1 = 2 * lane + 1;
+        c.l0 = s_status[k0] == kColRunning;
+        c.l1 = s_status[k1] == kColRunning;
+        c.a0 = s_d[k0];
+        c.a1 = s_d[k1];
+        c.b0 = (float)((1.0 - (double)s_d[k0]) + (double)s_d[k0] * s_D[k0]);
+        c.b1 = (float)((1.0 - (double)s_d[k1]) + (double)s_d[k1] * s_D[k1]);
+        c.s0 = s_seed[k0];
+        c.s1 = s_seed[k1];
+      }
+      float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      // light rows: one warp per row, round-robin
+      for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
+        const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+        if (e1 - e0 > heavy_deg) continue;
+        const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
+        finish_ppr_row(p, y, c, X, Cout, inv_deg, lane, acc);
+      }
+      // long rows: the whole block, fixed-order combine
+      for (int32_t hi = h0; hi < h1; ++hi) {
+        const int32_t p = J->heavy_rows[hi];
+        const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+        const int32_t per = (((e1 - e0) + kPprWarps - 1) / kPprWarps + 31) & ~31;
+        const int32_t a = min(e1, e0 + warp * per), b = min(e1, a + per);
+        const float2 y = gather_row(row_idx, Cin, a, b, lane);
+        s_heavy[warp][2 * lane] = y.x;
+        s_heavy[warp][2 * lane + 1] = y.y;
+        __syncthreads();
+        if (warp == 0) {
+          float yx = 0.f, yy = 0.f;
+          for (int w = 0; w < kPprWarps; ++w) {
+            yx += s_heavy[w][2 * lane];
+            yy += s_heavy[w][2 * lane + 1];
+          }
+          finish_ppr_row(p, make_float2(yx, yy), c, X, Cout, inv_deg, lane, acc);
+        }
+        __syncthreads();
+      }
+      // per-column partials: FP32 per warp, FP64 across warps and blocks
+      for (int v = 0; v < 3; ++v) {
+        s_wpart[warp][v][2 * lane] = acc[0][v];
+        s_wpart[warp][v][2 * lane + 1] = acc[1][v];
+      }
+      __syncthreads();
+      if (tid < 3 * kPprCols) {
+        const int v = tid / kPprCols, k = tid % kPprCols;
+        double sum = 0.0;
+        for (int w = 0; w < kPprWarps; ++w) sum += (double)s_wpart[w][v][k];
+        s_part[it & 1][v][k] = sum;
+      }
+      cl.sync();
+      if (tid < kPprCols && s_status[tid] == kColRunning) {
+        double tot[3] = {0.0, 0.0, 0.0};
+        for (int r = 0; r < cluster_size; ++r) {
+          const double* pp = cl.map_shared_rank(&s_part[it & 1][0][0], r);
+          tot[0] += pp[tid];
+          tot[1] += pp[kPprCols + tid];
+          tot[2] += pp[2 * kPprCols + tid];
+        }
+        s_D[tid] = tot[1];
+        s_res[tid] = tot[2];
+        const int32_t k_it = s_iters[tid] + 1;
+        s_iters[tid] = k_it;
+        const double d = s_d[tid];
+        const bool converged = s_tol[tid] > 0.f && (d / (1.0 - d)) * tot[2] <= (double)s_tol[tid];
+        if (converged || k_it >= s_maxit[tid]) {
+          s_status[tid] = kColDone;
+          s_newdone[tid] = 1;
+        }
+      }
+      parity ^= 1;
+      __syncthreads();
+    }
+
+    // columns that finished in this launch: write them out by node id
+    {
+      const int32_t v0 = (int32_t)((int64_t)n * crank / cluster_size);
+      const int32_t v1 = (int32_t)((int64_t)n * (crank + 1) / cluster_size);
+      for (int k = 0; k < kPprCols; ++k) {
+        if (!s_newdone[k]) continue;
+        float* out = J->cols[k].out;
+        const int32_t ldo = J->cols[k].ldo;
+        for (int32_t v = v0 + tid; v < v1; v += kPprThreads)
+          out[(int64_t)v * ldo] = X[(int64_t)J->old2new[v] * kPprCols + k];
+      }
+    }
+    if (crank == 0) {
+      if (tid < kPprCols) {
+        PprCol* cr = &J->cols[tid];
+        cr->status = s_status[tid];
+        cr->iters = s_iters[tid];
+        cr->dangling = s_D[tid];
+        cr->residual = s_res[tid];
+      }
+      if (tid == 0) J->parity = parity;
+    }
+    cl.sync();  // the workspace and s_job are reused by the next job
+  }
+}
+
+// ---- host side ----------------------------------------------------------------
+
+static int g_cluster_size = 8;
+
+int ppr_cluster_size() { return g_cluster_size; }
+
+template <typename T>
+static int max_clusters_for(int cluster) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster * 64, 1, 1);
+  cfg.blockDim = dim3(kPprThreads, 1, 1);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int num = 0;
+  if (cudaOccupancyMaxActiveClusters(&num, ppr_kernel<T>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return num;
+}
+
+int ppr_max_clusters(gpr_dtype dt) {
+  return dt == GPR_BF16 ? max_clusters_for<__nv_bfloat16>(g_cluster_size) : max_clusters_for<float>(g_cluster_size);
+}
+
+void ppr_launch(PprJob* jobs_dev, const int32_t* order_dev, int32_t njobs, uint32_t* queue_dev, char* ws,
+                int64_t ws_stride, int clusters, gpr_dtype dt, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * g_cluster_size), 1, 1);
+  cfg.blockDim = dim3(kPprThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = g_cluster_size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (dt == GPR_BF16)
+    e = cudaLaunchKernelEx(&cfg, ppr_kernel<__nv_bfloat16>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
+                           g_cluster_size);
+  else
+    e = cudaLaunchKernelEx(&cfg, ppr_kernel<float>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
+                           g_cluster_size);
+  if (e != cudaSuccess) throw CudaFail{e, "cudaLaunchKernelEx(ppr_kernel)"};
+  count_launches(1);
+}
+
+gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
+                         cudaStream_t s) {
+  std::vector<void*> tmp;
+  auto T = [&](size_t bytes) {
+    void* p = dalloc(bytes, s);
+    tmp.push_back(p);
+    return p;
+  };
+  try {
+    // one device job per 64 columns
+    std::vector<PprJob> dj;
+    std::vector<std::vector<PprCol>> cols;
+    std::vector<std::pair<int32_t, int32_t>> src;  // (request, first column)
+    int32_t n_cap = 1;
+    for (int32_t j = 0; j < num_jobs; ++j) {
+      const gpr_graph* g = jobs[j].graph;
+      for (int32_t k0 = 0; k0 < jobs[j].num_seeds; k0 += kPprCols) {
+        PprJob J{};
+        J.inv_deg = g->plan.inv_deg;
+        J.old2new = g->plan.old2new;
+        J.n = g->n;
+        J.col_ptr = g->col_ptr;
+        J.row_idx = g->row_idx;
+        J.heavy_rows = g->plan.rows;
+        J.n_heavy = 0;
+        J.heavy_deg = INT_MAX;
+        for (int b = 0; b < g->plan.nbuckets; ++b)
+          if (g->plan.bucket[b].lanes == 0) {
+            J.heavy_rows = g->plan.rows + g->plan.bucket[b].row_begin;
+            J.n_heavy = g->plan.bucket[b].row_end - g->plan.bucket[b].row_begin;
+            J.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : 0;
+          }
+        J.iters = max_iters;
+        J.n_cap = 0;  // set below
+        std::vector<PprCol> cc(kPprCols);
+        for (int k = 0; k < kPprCols; ++k) {
+          PprCol c{};
+          const int32_t kk = k0 + k;
+          if (kk < jobs[j].num_seeds) {
+            c.status = kColFresh;
+            c.seed = jobs[j].seeds[kk];
+            c.damping = jobs[j].damping[kk];
+            c.tol = (float)tol;
+            c.max_iters = max_iters;
+            c.out = jobs[j].x_out + kk;
+            c.ldo = jobs[j].num_seeds;
+          } else {
+            c.status = kColEmpty;
+            c.seed = 0;
+            c.damping = 0.5f;
+          }
+          cc[k] = c;
+        }
+        dj.push_back(J);
+        cols.push_back(cc);
+        src.emplace_back(j, k0);
+        n_cap = std::max(n_cap, g->n);
+      }
+    }
+    const int32_t nj = (int32_t)dj.size();
+    if (nj == 0) return GPR_OK;
+    // largest work first
+    std::vector<int32_t> order(nj);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<int64_t> work(nj);
+    for (int32_t i = 0; i < nj; ++i) {
+      const gpr_graph* g = jobs[src[i].first].graph;
+      work[i] = g->m + g->n;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+
+    PprCol* cols_dev = (PprCol*)T((size_t)nj * kPprCols * sizeof(PprCol));
+    std::vector<PprCol> flat((size_t)nj * kPprCols);
+    for (int32_t i = 0; i < nj; ++i)
+      std::copy(cols[i].begin(), cols[i].end(), flat.begin() + (size_t)i * kPprCols);
+    GPR_CUDA(cudaMemcpyAsync(cols_dev, flat.data(), flat.size() * sizeof(PprCol), cudaMemcpyHostToDevice, s));
+    for (int32_t i = 0; i < nj; ++i) {
+      dj[i].cols = cols_dev + (size_t)i * kPprCols;
+      dj[i].n_cap = n_cap;
+    }
+    PprJob* jobs_dev = (PprJob*)T((size_t)nj * sizeof(PprJob));
+    int32_t* order_dev = (int32_t*)T((size_t)nj * 4);
+    uint32_t* queue = (uint32_t*)T(16);
+    GPR_CUDA(cudaMemcpyAsync(jobs_dev, dj.data(), (size_t)nj * sizeof(PprJob), cudaMemcpyHostToDevice, s));
+    GPR_CUDA(cudaMemcpyAsync(order_dev, order.data(), (size_t)nj * 4, cudaMemcpyHostToDevice, s));
+    GPR_CUDA(cudaMemsetAsync(queue, 0, 16, s));
+    int clusters = ppr_max_clusters(dt);
+    if (clusters <= 0) throw StatusFail{GPR_ECUDA, "no thread-block cluster of the PPR kernel fits on this GPU"};
+    clusters = std::min(clusters, nj);
+    const size_t tsz = dt == GPR_BF16 ? 2 : 4;
+    const int64_t stride = (((int64_t)n_cap * kPprCols * (4 + 2 * tsz)) + 255) & ~(int64_t)255;
+    char* ws = (char*)T((size_t)stride * clusters);
+    ppr_launch(jobs_dev, order_dev, nj, queue, ws, stride, clusters, dt, s);
+    // per-column results back to the caller
+    GPR_CUDA(cudaMemcpyAsync(flat.data(), cols_dev, flat.size() * sizeof(PprCol), cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    for (int32_t i = 0; i < nj; ++i) {
+      const gpr_ppr_job& rq = jobs[src[i].first];
+      for (int k = 0; k < kPprCols; ++k) {
+        const int32_t kk = src[i].second + k;
+        if (kk >= rq.num_seeds) break;
+        const PprCol& c = flat[(size_t)i * kPprCols + k];
+        if (rq.iters_out) rq.iters_out[kk] = c.iters;
+        if (rq.residual_out) rq.residual_out[kk] = c.residual;
+      }
+    }
+    for (void* p : tmp) dfree(p, s);
+    return GPR_OK;
+  } catch (const StatusFail& f) {
+    for (void* p : tmp) dfree(p, s);
+    set_error("ppr_batch: %s", f.msg.c_str());
+    return f.st;
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    for (void* p : tmp) dfree(p, s);
+    set_error("ppr_batch: %s failed: %s", f.what, cudaGetErrorString(f.err));
+    return GPR_ECUDA;
+  }
+}
+
+}  // namespace gpr
