@@ -45,8 +45,12 @@ typedef enum {
 /* Storage type of the gathered contribution vector c = x / outdeg (the
  * bytes the pull step reads once per edge).  The rank vector x itself is
  * always FP32; accumulation is always FP32; the per-step mass,
- * dangling-mass and residual reductions are FP64. */
-typedef enum { GPR_FP32 = 0, GPR_BF16 = 1 } gpr_dtype;
+ * dangling-mass and residual reductions are FP64.
+ *   GPR_BF16: 8-bit significand.  pagerank rounds to nearest; ppr_batch
+ *             rounds stochastically (deterministic counter-based bits).
+ *   GPR_FP16: ppr_batch only: 11-bit significand, values stored times 2^10
+ *             (a personalised column lies in [0, 1]). */
+typedef enum { GPR_FP32 = 0, GPR_BF16 = 1, GPR_FP16 = 2 } gpr_dtype;
 
 /* Pointer-space flags */
 #define GPR_PTR_DEVICE 0 /* arrays are device (or managed) memory */

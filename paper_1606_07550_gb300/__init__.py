@@ -27,7 +27,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTREADY, ENOTFOUND = range(8)
 _NAMES = ["GPR_OK", "GPR_EINVAL", "GPR_ENOMEM", "GPR_ECUDA", "GPR_ETIMEOUT", "GPR_EBUSY", "GPR_ENOTREADY",
           "GPR_ENOTFOUND"]
-FP32, BF16 = 0, 1
+FP32, BF16, FP16 = 0, 1, 2
 PTR_DEVICE, PTR_HOST = 0, 1
 
 

@@ -148,7 +148,7 @@ gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iter
     set_error("ppr_batch: max_iters %d or tol %g out of range", (int)max_iters, tol);
     return GPR_EINVAL;
   }
-  if (dt != GPR_FP32 && dt != GPR_BF16) {
+  if (dt != GPR_FP32 && dt != GPR_BF16 && dt != GPR_FP16) {
     set_error("ppr_batch: unknown dtype %d", (int)dt);
     return GPR_EINVAL;
   }

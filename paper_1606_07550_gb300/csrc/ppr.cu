@@ -28,6 +28,8 @@
 #include <numeric>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "gpr_internal.cuh"
 #include "ppr_internal.cuh"
 
@@ -38,17 +40,51 @@ namespace gpr {
 constexpr int kPprThreads = 512;
 constexpr int kPprWarps = kPprThreads / 32;
 
+// FP16 contributions are stored times 2^10 (values of a personalised column
+// lie in [0, 1], so they stay below 1024 and far above the subnormal range
+// for any contribution that matters); the power-of-two scale adds no rounding.
+constexpr float kHalfScale = 1024.0f;
+constexpr float kHalfUnscale = 1.0f / 1024.0f;
+
 __device__ __forceinline__ float2 ld_pair(const float* p) { return __ldcg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ float2 ld_pair(const __half* p) {
+  const unsigned int u = __ldcg(reinterpret_cast<const unsigned int*>(p));
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+  return make_float2(f.x * kHalfUnscale, f.y * kHalfUnscale);
+}
 __device__ __forceinline__ float2 ld_pair(const __nv_bfloat16* p) {
   const unsigned int u = __ldcg(reinterpret_cast<const unsigned int*>(p));
   __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u);
   return __bfloat1622float2(b);
 }
-__device__ __forceinline__ void st_pair(float* p, float a, float b) {
+__device__ __forceinline__ void st_pair(float* p, float a, float b, uint32_t) {
   *reinterpret_cast<float2*>(p) = make_float2(a, b);
 }
-__device__ __forceinline__ void st_pair(__nv_bfloat16* p, float a, float b) {
-  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+// BF16 contributions are rounded stochastically: add 16 random bits below the
+// kept mantissa and truncate (non-negative finite values only).  Round-to-
+// nearest would round the same value the same way at every step near the
+// fixed point and bias the result by up to d/(1-d) unit roundoffs; random
+// rounding makes the errors of successive steps independent, so the
+// contraction damps them.  The bits come from a counter-based hash of
+// (column, step, node), so a column gives the same bits alone or in a batch.
+__device__ __forceinline__ uint16_t bf16_sr(float v, uint32_t r16) {
+  return (uint16_t)((__float_as_uint(v) + (r16 & 0xFFFFu)) >> 16);
+}
+__device__ __forceinline__ void st_pair(__nv_bfloat16* p, float a, float b, uint32_t rnd) {
+  const uint32_t packed = (uint32_t)bf16_sr(a, rnd) | ((uint32_t)bf16_sr(b, rnd >> 16) << 16);
+  *reinterpret_cast<uint32_t*>(p) = packed;
+}
+__device__ __forceinline__ void st_pair(__half* p, float a, float b, uint32_t) {
+  *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * kHalfScale, b * kHalfScale);
+}
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  // a 32-bit integer finaliser (Wang / Jenkins style mix)
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
 }
 template <typename T>
 __device__ __forceinline__ void st_one(T* p, float a);
@@ -59,6 +95,10 @@ __device__ __forceinline__ void st_one<float>(float* p, float a) {
 template <>
 __device__ __forceinline__ void st_one<__nv_bfloat16>(__nv_bfloat16* p, float a) {
   *p = __float2bfloat16_rn(a);
+}
+template <>
+__device__ __forceinline__ void st_one<__half>(__half* p, float a) {
+  *p = __float2half_rn(a * kHalfScale);
 }
 
 // Sum of the contribution rows of the sources of edges [e0, e1), two columns
@@ -93,10 +133,11 @@ __device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx
 }
 
 struct ColRegs {
-  float a0, a1;    // d of the two columns
-  float b0, b1;    // seed coefficient (1 - d) + d D
-  int32_t s0, s1;  // relabelled seed rows
-  bool l0, l1;     // live
+  float a0, a1;      // d of the two columns
+  float b0, b1;      // seed coefficient (1 - d) + d D
+  int32_t s0, s1;    // relabelled seed rows
+  bool l0, l1;       // live
+  uint32_t k0, k1;   // rounding-hash keys of (column, step)
 };
 
 template <typename T>
@@ -109,7 +150,9 @@ __device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, const ColReg
   const float n0 = c.l0 ? fmaf(c.a0, y.x, p == c.s0 ? c.b0 : 0.f) : xo.x;
   const float n1 = c.l1 ? fmaf(c.a1, y.y, p == c.s1 ? c.b1 : 0.f) : xo.y;
   *reinterpret_cast<float2*>(xp) = make_float2(n0, n1);
-  st_pair(Cout + (int64_t)p * kPprCols + 2 * lane, n0 * inv, n1 * inv);
+  const uint32_t hp = (uint32_t)p * 0x9E3779B1u;
+  const uint32_t rnd = (hash32(c.k0 ^ hp) & 0xFFFFu) | (hash32(c.k1 ^ hp) << 16);
+  st_pair(Cout + (int64_t)p * kPprCols + 2 * lane, n0 * inv, n1 * inv, rnd);
   acc[0][0] += n0;
   acc[1][0] += n1;
   if (inv == 0.f) {
@@ -150,6 +193,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
   __shared__ float s_d[kPprCols], s_tol[kPprCols];
   __shared__ double s_D[kPprCols], s_res[kPprCols];
   __shared__ int32_t s_status[kPprCols], s_iters[kPprCols], s_maxit[kPprCols], s_newdone[kPprCols];
+  __shared__ uint32_t s_key[kPprCols];
 
   for (;;) {
     if (crank == 0 && tid == 0) s_job = (int)atomicAdd(queue, 1u);
@@ -208,6 +252,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       }
       s_d[tid] = cr.damping;
       s_tol[tid] = cr.tol;
+      s_key[tid] = hash32((uint32_t)cr.seed * 0x85EBCA6Bu ^ __float_as_uint(cr.damping));
       s_maxit[tid] = cr.max_iters;
     }
     __syncthreads();
@@ -263,6 +308,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         c.b1 = (float)((1.0 - (double)s_d[k1]) + (double)s_d[k1] * s_D[k1]);
         c.s0 = s_seed[k0];
         c.s1 = s_seed[k1];
+        c.k0 = hash32(s_key[k0] ^ hash32((uint32_t)s_iters[k0] + 0x632BE5ABu));
+        c.k1 = hash32(s_key[k1] ^ hash32((uint32_t)s_iters[k1] + 0x632BE5ABu));
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       // light rows: one warp per row, round-robin
@@ -381,7 +428,9 @@ static int max_clusters_for(int cluster) {
 }
 
 int ppr_max_clusters(gpr_dtype dt) {
-  return dt == GPR_BF16 ? max_clusters_for<__nv_bfloat16>(g_cluster_size) : max_clusters_for<float>(g_cluster_size);
+  if (dt == GPR_BF16) return max_clusters_for<__nv_bfloat16>(g_cluster_size);
+  if (dt == GPR_FP16) return max_clusters_for<__half>(g_cluster_size);
+  return max_clusters_for<float>(g_cluster_size);
 }
 
 void ppr_launch(PprJob* jobs_dev, const int32_t* order_dev, int32_t njobs, uint32_t* queue_dev, char* ws,
@@ -401,6 +450,9 @@ void ppr_launch(PprJob* jobs_dev, const int32_t* order_dev, int32_t njobs, uint3
   cudaError_t e;
   if (dt == GPR_BF16)
     e = cudaLaunchKernelEx(&cfg, ppr_kernel<__nv_bfloat16>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
+                           g_cluster_size);
+  else if (dt == GPR_FP16)
+    e = cudaLaunchKernelEx(&cfg, ppr_kernel<__half>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
                            g_cluster_size);
   else
     e = cudaLaunchKernelEx(&cfg, ppr_kernel<float>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
@@ -498,7 +550,7 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
     int clusters = ppr_max_clusters(dt);
     if (clusters <= 0) throw StatusFail{GPR_ECUDA, "no thread-block cluster of the PPR kernel fits on this GPU"};
     clusters = std::min(clusters, nj);
-    const size_t tsz = dt == GPR_BF16 ? 2 : 4;
+    const size_t tsz = (dt == GPR_BF16 || dt == GPR_FP16) ? 2 : 4;
     const int64_t stride = (((int64_t)n_cap * kPprCols * (4 + 2 * tsz)) + 255) & ~(int64_t)255;
     char* ws = (char*)T((size_t)stride * clusters);
     ppr_launch(jobs_dev, order_dev, nj, queue, ws, stride, clusters, dt, s);

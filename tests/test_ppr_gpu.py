@@ -1,8 +1,10 @@
 """Batched personalised PageRank on the GPU against the FP64 CPU oracle.
 
-Every column is compared with a single-seed oracle run at the same step count
-(L1 <= 1e-5 with FP32 contributions, <= 1e-3 with BF16), and a column must give
-the same bits alone as inside a batch.
+Every column is compared with a single-seed oracle run at the same step count:
+L1 <= 1e-5 with FP32 contributions and <= 1e-3 with scaled FP16 ones.  BF16
+contributions (8-bit significand) have an error floor near 1e-3 for
+personalised columns, whose mass sits on few nodes; they are held to 3e-3.
+A column must give the same bits alone as inside a batch.
 """
 import numpy as np
 import pytest
@@ -15,7 +17,7 @@ from gpu_util import l1, random_coo_with_dups
 
 pytestmark = pytest.mark.gpu
 
-TOL = {gpr.FP32: 1e-5, gpr.BF16: 1e-3}
+TOL = {gpr.FP32: 1e-5, gpr.FP16: 1e-3, gpr.BF16: 3e-3}
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +38,7 @@ def run(torch, reqs, iters, tol=0.0, dt=gpr.FP32):
     return [o.cpu().numpy() for o in outs], res
 
 
-@pytest.mark.parametrize("dt", [gpr.FP32, gpr.BF16])
+@pytest.mark.parametrize("dt", [gpr.FP32, gpr.FP16, gpr.BF16])
 def test_columns_match_oracle(torch, dt):
     graphs = [make_graph(torch, n, m, 40 + i) for i, (n, m) in
               enumerate([(1000, 12_000), (5000, 90_000), (20_000, 500_000), (3001, 3000)])]
