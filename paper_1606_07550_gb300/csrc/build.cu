@@ -15,6 +15,7 @@
 //            offsets (row starts plus gap fill) and out-degrees in one pass
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <atomic>
@@ -65,8 +66,28 @@ static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+// The library allocates with the device's default stream-ordered pool.  The
+// pool is told to keep freed memory mapped (a setting of this process only),
+// so that repeated builds reuse it instead of mapping it again; set
+// GPR_POOL_RELEASE=1 to return freed memory to the system at each sync.
+static void keep_pool_memory() {
+  static bool done[64] = {false};
+  const int d = device_ordinal();
+  if (d < 0 || d >= 64 || done[d]) return;
+  done[d] = true;
+  const char* env = getenv("GPR_POOL_RELEASE");
+  if (env && atoi(env) != 0) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+}
+
 void* dalloc(size_t bytes, cudaStream_t s) {
   void* p = nullptr;
+  keep_pool_memory();
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMallocAsync(&p, bytes, s);
   if (e != cudaSuccess) {
