@@ -55,6 +55,10 @@ int device_ordinal();
 void count_launches(int64_t k);
 int64_t launches_so_far();
 
+// Entries of the contribution vector that one block can hold in shared
+// memory (FP32), a multiple of 8.
+int32_t hot_capacity();
+
 // ---- radix sort of 64-bit keys (onesweep-style, build.cu) -----------------
 // Sorts keys[0..n) ascending on the low `bits` bits (stable LSD, 8-bit
 // digits), using `alt` (n entries) as the second buffer.  Returns the buffer
@@ -83,15 +87,24 @@ struct Plan {
   int nbuckets = 0;
   Bucket bucket[kMaxBuckets];
   int32_t deg_threshold[kMaxBuckets];  // upper in-degree bound of each bucket (last: INT_MAX)
-  // edge chunks of the warp-chunk bucket: (row, edge_begin, edge_end) and
-  // whether the chunk is the whole row (1) or a piece of a split row (0)
+  // Hot/cold split: sources below hot_H (the most-read contributions) are
+  // gathered by a pass that keeps c[0, hot_H) in shared memory.  Rows are
+  // sorted, so the hot sources of row p are the prefix [col_ptr[p], split[p]).
+  int32_t hot_H = 0;
+  int32_t* split = nullptr;  // n
+  // edge chunks of the long-row bucket: (row, edge_begin, edge_end); chunks
+  // [0, n_hot_chunks) cover hot prefixes, the rest cold suffixes.  Every long
+  // row is finished from its chunk sums: hot chunks [hbeg, hend), cold chunks
+  // [cbeg, cend).
   int32_t* chunk_row = nullptr;
   int32_t* chunk_begin = nullptr;
   int32_t* chunk_end = nullptr;
-  int32_t* chunk_whole = nullptr;
   int32_t nchunks = 0;
-  int32_t* split_row = nullptr;   // rows split over several chunks
-  int32_t* split_cbeg = nullptr;  // their chunk ranges [cbeg, cend) in the chunk list
+  int32_t n_hot_chunks = 0;
+  int32_t* split_row = nullptr;  // the long rows
+  int32_t* split_hbeg = nullptr;
+  int32_t* split_hend = nullptr;
+  int32_t* split_cbeg = nullptr;
   int32_t* split_cend = nullptr;
   int32_t nsplit = 0;
   int32_t chunk_edges = 0;

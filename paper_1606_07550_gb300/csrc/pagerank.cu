@@ -137,10 +137,13 @@ __device__ __forceinline__ float warp_gather(const int32_t* __restrict__ row_idx
 }
 
 // G lanes per row (G in {1, 2, 4, 8, 16, 32}) over rows[i0, i1).
+// Cold pass: the part of each row from split[r] on (from col_ptr[r] when
+// split is null), plus the hot-pass sum y_hot[r] (when not null).
 template <int G, typename T>
 __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ col_ptr,
                                                    const int32_t* __restrict__ row_idx, const int32_t* __restrict__ rows,
-                                                   int32_t i0, int32_t i1, const T* __restrict__ c_in,
+                                                   int32_t i0, int32_t i1, const int32_t* __restrict__ split,
+                                                   const float* __restrict__ y_hot, const T* __restrict__ c_in,
                                                    const float* __restrict__ x_in, const float* __restrict__ inv_deg,
                                                    float* __restrict__ x_out, T* __restrict__ c_out,
                                                    const StepParams* __restrict__ prm, double* __restrict__ partials) {
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ c
     int32_t r = 0, e0 = 0, e1 = 0;
     if (active) {
       r = rows[i];
-      e0 = col_ptr[r];
+      e0 = split ? split[r] : col_ptr[r];
       e1 = col_ptr[r + 1];
     }
     float y;
@@ -169,36 +172,116 @@ __global__ void __launch_bounds__(256) rows_kernel(const int32_t* __restrict__ c
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-    if (active && sub == 0) finish_row(r, y, A, B, x_in, inv_deg, x_out, c_out, mass, dang, res);
+    if (active && sub == 0) {
+      if (y_hot) y += y_hot[r];
+      finish_row(r, y, A, B, x_in, inv_deg, x_out, c_out, mass, dang, res);
+    }
   }
   block_partials3(mass, dang, res, partials + 3 * (int64_t)blockIdx.x);
 }
 
-// One edge chunk per warp.  A chunk that is a whole row is finished here; a
-// piece of a split row leaves its sum in chunk_sum.
+// Cold pass over long rows: one edge chunk per warp, chunks [c0, c1); each
+// leaves its sum in chunk_sum (the finish kernel completes the rows).
 template <typename T>
-__global__ void __launch_bounds__(256) wchunks_kernel(
-    const int32_t* __restrict__ row_idx, const T* __restrict__ c_in, const float* __restrict__ x_in,
-    const float* __restrict__ inv_deg, float* __restrict__ x_out, T* __restrict__ c_out,
-    const int32_t* __restrict__ chunk_row, const int32_t* __restrict__ chunk_begin,
-    const int32_t* __restrict__ chunk_end, const int32_t* __restrict__ chunk_whole, int32_t nchunks,
-    float* __restrict__ chunk_sum, const StepParams* __restrict__ prm, double* __restrict__ partials) {
-  const float A = prm->coefA, B = prm->coefB;
+__global__ void __launch_bounds__(256) wchunks_kernel(const int32_t* __restrict__ row_idx, const T* __restrict__ c_in,
+                                                      const int32_t* __restrict__ chunk_begin,
+                                                      const int32_t* __restrict__ chunk_end, int32_t c0, int32_t c1,
+                                                      float* __restrict__ chunk_sum) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float mass = 0.f, dang = 0.f, res = 0.f;
-  for (int64_t ch = warp; ch < nchunks; ch += nwarps) {
-    const int32_t e0 = chunk_begin[ch], e1 = chunk_end[ch];
-    const float y = warp_sum(warp_gather(row_idx, c_in, e0, e1, lane));
-    if (lane == 0) {
-      if (chunk_whole[ch])
-        finish_row(chunk_row[ch], y, A, B, x_in, inv_deg, x_out, c_out, mass, dang, res);
-      else
-        chunk_sum[ch] = y;
+  for (int64_t ch = c0 + warp; ch < c1; ch += nwarps) {
+    const float y = warp_sum(warp_gather(row_idx, c_in, chunk_begin[ch], chunk_end[ch], lane));
+    if (lane == 0) chunk_sum[ch] = y;
+  }
+}
+
+// Hot pass.  Each block copies c[0, H) into shared memory, then sums, over
+// the hot prefix [col_ptr[r], split[r]) of every row, contributions read from
+// that copy only: rows of the lane buckets into y_hot[r], hot chunks of the
+// long rows into chunk_sum.  Same lane layout per bucket as the cold pass.
+struct HotLayout {
+  int nb;
+  int lanes[kMaxBuckets];
+  int32_t begin[kMaxBuckets], end[kMaxBuckets];
+};
+
+template <typename T>
+__device__ __forceinline__ float sm_f(const T* s, int32_t u);
+template <>
+__device__ __forceinline__ float sm_f<float>(const float* s, int32_t u) {
+  return s[u];
+}
+template <>
+__device__ __forceinline__ float sm_f<__nv_bfloat16>(const __nv_bfloat16* s, int32_t u) {
+  return __bfloat162float(s[u]);
+}
+
+template <int G, typename T>
+__device__ __forceinline__ void hot_rows(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                                         const int32_t* __restrict__ rows, int32_t i0, int32_t i1,
+                                         const int32_t* __restrict__ split, const T* s_c, float* __restrict__ y_hot) {
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (G - 1);
+  constexpr int kRowsPerWarp = 32 / G;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wi = i0 + warp * kRowsPerWarp; wi < i1; wi += nwarps * kRowsPerWarp) {
+    const int64_t i = wi + lane / G;
+    const bool active = i < i1;
+    int32_t r = 0, e0 = 0, e1 = 0;
+    if (active) {
+      r = rows[i];
+      e0 = col_ptr[r];
+      e1 = split[r];
+    }
+    float y = 0.f;
+    for (int32_t e = e0 + sub; e < e1; e += G) y += sm_f(s_c, __ldcs(row_idx + e));
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (active && sub == 0) y_hot[r] = y;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) hot_kernel(const int32_t* __restrict__ col_ptr,
+                                                      const int32_t* __restrict__ row_idx,
+                                                      const int32_t* __restrict__ rows, HotLayout lay,
+                                                      const int32_t* __restrict__ split, const T* __restrict__ c_in,
+                                                      int32_t H, const int32_t* __restrict__ chunk_begin,
+                                                      const int32_t* __restrict__ chunk_end, int32_t n_hot_chunks,
+                                                      float* __restrict__ y_hot, float* __restrict__ chunk_sum) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_c = reinterpret_cast<T*>(smem_raw);
+  {
+    const int4* src = reinterpret_cast<const int4*>(c_in);
+    int4* dst = reinterpret_cast<int4*>(s_c);
+    const int32_t nvec = (int32_t)((int64_t)H * sizeof(T) / 16);  // H is a multiple of 8
+    for (int32_t i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  for (int k = 0; k < lay.nb; ++k) {
+    const int32_t i0 = lay.begin[k], i1 = lay.end[k];
+    switch (lay.lanes[k]) {
+      case 1: hot_rows<1, T>(col_ptr, row_idx, rows, i0, i1, split, s_c, y_hot); break;
+      case 2: hot_rows<2, T>(col_ptr, row_idx, rows, i0, i1, split, s_c, y_hot); break;
+      case 4: hot_rows<4, T>(col_ptr, row_idx, rows, i0, i1, split, s_c, y_hot); break;
+      case 8: hot_rows<8, T>(col_ptr, row_idx, rows, i0, i1, split, s_c, y_hot); break;
+      case 16: hot_rows<16, T>(col_ptr, row_idx, rows, i0, i1, split, s_c, y_hot); break;
+      case 32: hot_rows<32, T>(col_ptr, row_idx, rows, i0, i1, split, s_c, y_hot); break;
+      default: break;
     }
   }
-  block_partials3(mass, dang, res, partials + 3 * (int64_t)blockIdx.x);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t ch = warp; ch < n_hot_chunks; ch += nwarps) {
+    const int32_t e0 = chunk_begin[ch], e1 = chunk_end[ch];
+    float y = 0.f;
+    for (int32_t e = e0 + lane; e < e1; e += 32) y += sm_f(s_c, __ldcs(row_idx + e));
+    y = warp_sum(y);
+    if (lane == 0) chunk_sum[ch] = y;
+  }
 }
 
 // x_0 = 1/N, c_0 = x_0 * inv_outdeg.
@@ -217,14 +300,15 @@ __global__ void init_kernel(float* __restrict__ x, T* __restrict__ c, const floa
   block_partials3(mass, dang, 0.f, partials + 3 * (int64_t)blockIdx.x);
 }
 
-// Finishes the split rows (grid-stride, chunk sums added in chunk order),
+// Finishes the long rows (grid-stride; hot then cold chunk sums, in order),
 // then the last block to arrive folds all `npartials` block partials of the
 // step (this kernel's own are the last gridDim.x of them) in index order,
 // logs (mass, dangling, residual) and writes the next coefficients.
 template <typename T>
 __global__ void __launch_bounds__(256) finish_kernel(
     const float* __restrict__ x_in, const float* __restrict__ inv_deg, float* __restrict__ x_out,
-    T* __restrict__ c_out, const int32_t* __restrict__ split_row, const int32_t* __restrict__ split_cbeg,
+    T* __restrict__ c_out, const int32_t* __restrict__ split_row, const int32_t* __restrict__ split_hbeg,
+    const int32_t* __restrict__ split_hend, const int32_t* __restrict__ split_cbeg,
     const int32_t* __restrict__ split_cend, int32_t nsplit, const float* __restrict__ chunk_sum,
     double* __restrict__ partials, int32_t npartials, StepParams* __restrict__ prm, double* __restrict__ log_row,
     unsigned int* __restrict__ arrive) {
@@ -233,6 +317,7 @@ __global__ void __launch_bounds__(256) finish_kernel(
   float fm = 0.f, fd = 0.f, fr = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsplit; i += (int64_t)gridDim.x * blockDim.x) {
     float y = 0.f;
+    for (int32_t c = split_hbeg[i]; c < split_hend[i]; ++c) y += chunk_sum[c];
     for (int32_t c = split_cbeg[i]; c < split_cend[i]; ++c) y += chunk_sum[c];
     finish_row(split_row[i], y, A, B, x_in, inv_deg, x_out, c_out, fm, fd, fr);
   }
@@ -299,8 +384,11 @@ struct PagerankWork {
   float* x[2] = {nullptr, nullptr};  // n floats each: the rank vector, always FP32
   void* c[2] = {nullptr, nullptr};   // n * 4 bytes each: contributions x / outdeg, FP32 or BF16
   float* out_tmp = nullptr;          // n floats, for host-pointer output
+  float* y_hot = nullptr;            // n floats: hot-pass row sums
+  int hot_grid = 0;                  // 0: no hot pass
+  size_t hot_smem32 = 0, hot_smem16 = 0;
   double* partials = nullptr;
-  int32_t npartials = 0;  // per step: bucket kernels' blocks + finish blocks
+  int32_t npartials = 0;  // per step: lane-bucket kernels' blocks + finish blocks
   float* chunk_sum = nullptr;
   StepParams* prm = nullptr;
   unsigned int* arrive = nullptr;
@@ -328,6 +416,7 @@ void pagerank_work_free(PagerankWork* w) {
     dfree(w->c[i], s);
   }
   dfree(w->out_tmp, s);
+  dfree(w->y_hot, s);
   dfree(w->partials, s);
   dfree(w->chunk_sum, s);
   dfree(w->prm, s);
@@ -343,6 +432,21 @@ void pagerank_work_free(PagerankWork* w) {
     cudaStreamDestroy(s);
   }
   delete w;
+}
+
+int32_t hot_capacity() {
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device_ordinal());
+  const int64_t bytes = optin > 4096 ? (int64_t)optin - 4096 : 0;  // leave room for static shared memory
+  return (int32_t)((bytes / 4) & ~(int64_t)7);
+}
+
+template <typename T>
+static int hot_grid_for(size_t smem) {
+  cudaFuncSetAttribute(hot_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot_kernel<T>, 1024, smem);
+  return num_sms() * std::max(per_sm, 1);
 }
 
 template <typename K>
@@ -369,13 +473,17 @@ static int grid_for_bucket(const Bucket& b, int32_t nchunks) {
 }
 
 template <typename T>
-static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_graph* g, const T* c_in,
-                          const float* x_in, float* x_out, T* c_out, float* chunk_sum, const StepParams* prm,
-                          double* part) {
+static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_graph* g, const float* y_hot,
+                          const T* c_in, const float* x_in, float* x_out, T* c_out, float* chunk_sum,
+                          const StepParams* prm, double* part) {
   const Plan& P = g->plan;
-#define GPR_ROWS(GL)                                                                                        \
-  rows_kernel<GL, T><<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, P.rows, b.row_begin, b.row_end, c_in, x_in, \
-                                          P.inv_deg, x_out, c_out, prm, part)
+  // only warp-per-row rows are split; narrower buckets read their whole rows
+  const bool split_rows = P.hot_H > 0 && b.lanes == 32;
+  const int32_t* split = split_rows ? P.split : nullptr;
+  if (!split_rows) y_hot = nullptr;
+#define GPR_ROWS(GL)                                                                                            \
+  rows_kernel<GL, T><<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, P.rows, b.row_begin, b.row_end, split, y_hot, \
+                                          c_in, x_in, P.inv_deg, x_out, c_out, prm, part)
   switch (b.lanes) {
     case 1: GPR_ROWS(1); break;
     case 2: GPR_ROWS(2); break;
@@ -384,38 +492,53 @@ static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_g
     case 16: GPR_ROWS(16); break;
     case 32: GPR_ROWS(32); break;
     default:
-      wchunks_kernel<T><<<grid, 256, 0, s>>>(g->row_idx, c_in, x_in, P.inv_deg, x_out, c_out, P.chunk_row,
-                                             P.chunk_begin, P.chunk_end, P.chunk_whole, P.nchunks, chunk_sum, prm,
-                                             part);
+      wchunks_kernel<T><<<grid, 256, 0, s>>>(g->row_idx, c_in, P.chunk_begin, P.chunk_end, P.n_hot_chunks,
+                                             P.nchunks, chunk_sum);
       break;
   }
 #undef GPR_ROWS
 }
 
-// Records init + `iters` steps on w->cap (which is capturing).  The bucket
-// kernels of a step fork onto side streams and join before the finish kernel.
+// Records init + `iters` steps on w->cap (which is capturing).  A step is the
+// hot pass, then the cold-pass bucket kernels forked onto side streams, joined
+// before the finish kernel.
 template <typename T>
 static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters) {
   const Plan& P = g->plan;
   cudaStream_t s = w->cap;
   float* x[2] = {w->x[0], w->x[1]};
   T* c[2] = {(T*)w->c[0], (T*)w->c[1]};
+  const bool hot = w->hot_grid > 0;
+  const size_t hot_smem = sizeof(T) == 2 ? w->hot_smem16 : w->hot_smem32;
+  HotLayout hl{};
+  hl.nb = P.nbuckets;
+  for (int k = 0; k < P.nbuckets; ++k) {
+    hl.lanes[k] = P.bucket[k].lanes == 32 ? 32 : 0;  // the hot pass takes warp-per-row rows and long rows only
+    hl.begin[k] = P.bucket[k].row_begin;
+    hl.end[k] = P.bucket[k].row_end;
+  }
   init_kernel<T><<<w->init_grid, 256, 0, s>>>(x[0], c[0], P.inv_deg, g->n, w->partials);
-  finish_kernel<T><<<1, 256, 0, s>>>(x[0], P.inv_deg, x[0], c[0], P.split_row, P.split_cbeg, P.split_cend, 0,
-                                    w->chunk_sum, w->partials, w->init_grid + 1, w->prm, w->log, w->arrive);
+  finish_kernel<T><<<1, 256, 0, s>>>(x[0], P.inv_deg, x[0], c[0], P.split_row, P.split_hbeg, P.split_hend,
+                                    P.split_cbeg, P.split_cend, 0, w->chunk_sum, w->partials, w->init_grid + 1,
+                                    w->prm, w->log, w->arrive);
   for (int32_t it = 0; it < iters; ++it) {
     const int a = it & 1, b = a ^ 1;
+    if (hot)
+      hot_kernel<T><<<w->hot_grid, 1024, hot_smem, s>>>(g->col_ptr, g->row_idx, P.rows, hl, P.split, c[a], P.hot_H,
+                                                        P.chunk_begin, P.chunk_end, P.n_hot_chunks, w->y_hot,
+                                                        w->chunk_sum);
     GPR_CUDA(cudaEventRecord(w->ev_fork, s));
     for (int bi = 0; bi < P.nbuckets; ++bi) {
       GPR_CUDA(cudaStreamWaitEvent(w->side[bi], w->ev_fork, 0));
-      launch_bucket<T>(P.bucket[bi], w->shape[bi].grid, w->side[bi], g, c[a], x[a], x[b], c[b], w->chunk_sum, w->prm,
-                       w->partials + 3 * (int64_t)w->shape[bi].partial_off);
+      launch_bucket<T>(P.bucket[bi], w->shape[bi].grid, w->side[bi], g, hot ? w->y_hot : nullptr, c[a], x[a], x[b],
+                       c[b], w->chunk_sum, w->prm, w->partials + 3 * (int64_t)w->shape[bi].partial_off);
       GPR_CUDA(cudaEventRecord(w->ev_join[bi], w->side[bi]));
       GPR_CUDA(cudaStreamWaitEvent(s, w->ev_join[bi], 0));
     }
-    finish_kernel<T><<<w->finish_grid, 256, 0, s>>>(x[a], P.inv_deg, x[b], c[b], P.split_row, P.split_cbeg,
-                                                    P.split_cend, P.nsplit, w->chunk_sum, w->partials, w->npartials,
-                                                    w->prm, w->log + 3 * (int64_t)(it + 1), w->arrive);
+    finish_kernel<T><<<w->finish_grid, 256, 0, s>>>(x[a], P.inv_deg, x[b], c[b], P.split_row, P.split_hbeg,
+                                                    P.split_hend, P.split_cbeg, P.split_cend, P.nsplit, w->chunk_sum,
+                                                    w->partials, w->npartials, w->prm,
+                                                    w->log + 3 * (int64_t)(it + 1), w->arrive);
   }
 }
 
@@ -435,13 +558,20 @@ static PagerankWork* work_make(gpr_graph* g, cudaStream_t s) {
       w->c[i] = dalloc(vb, s);
     }
     const Plan& P = g->plan;
+    const int32_t n_cold_chunks = P.nchunks - P.n_hot_chunks;
     int off = 0;
     for (int bi = 0; bi < P.nbuckets; ++bi) {
-      const int g32 = grid_for_bucket<float>(P.bucket[bi], P.nchunks);
-      const int g16 = grid_for_bucket<__nv_bfloat16>(P.bucket[bi], P.nchunks);
+      const int g32 = grid_for_bucket<float>(P.bucket[bi], n_cold_chunks);
+      const int g16 = grid_for_bucket<__nv_bfloat16>(P.bucket[bi], n_cold_chunks);
       w->shape[bi].grid = std::max(g32, g16);
       w->shape[bi].partial_off = off;
-      off += w->shape[bi].grid;
+      if (P.bucket[bi].lanes != 0) off += w->shape[bi].grid;  // the chunk kernel finishes no rows
+    }
+    if (P.hot_H > 0) {
+      w->hot_smem32 = (size_t)P.hot_H * 4;
+      w->hot_smem16 = (size_t)P.hot_H * 2;
+      w->hot_grid = std::max(hot_grid_for<float>(w->hot_smem32), hot_grid_for<__nv_bfloat16>(w->hot_smem16));
+      w->y_hot = (float*)dalloc((size_t)g->n * 4, s);
     }
     w->finish_grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)P.nsplit + 255) / 256, num_sms() * 2));
     w->npartials = off + w->finish_grid;
@@ -510,7 +640,7 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
       }
       w->exec_iters = iters;
       w->exec_dt = (int)dt;
-      w->exec_kernels = 2 + (int64_t)iters * (g->plan.nbuckets + 1);
+      w->exec_kernels = 2 + (int64_t)iters * (g->plan.nbuckets + 1 + (w->hot_grid > 0 ? 1 : 0));
     }
     GPR_CUDA(cudaGraphLaunch(w->exec, s));
     count_launches(w->exec_kernels);

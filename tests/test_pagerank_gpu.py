@@ -33,13 +33,16 @@ def gpu_pr(torch, g, iters, d=0.85, dt=gpr.FP32, stats=False):
     return (x, st) if stats else x
 
 
-def check(torch, n, src, dst, iters, dt=gpr.FP32, d=0.85, buckets=None):
+def check(torch, n, src, dst, iters, dt=gpr.FP32, d=0.85, buckets=None, hot=None):
     if buckets is not None:
         os.environ["GPR_BUCKETS"] = buckets
+    if hot is not None:
+        os.environ["GPR_HOT"] = hot
     try:
         g = gpr.graph_build(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
     finally:
         os.environ.pop("GPR_BUCKETS", None)
+        os.environ.pop("GPR_HOT", None)
     ref = oracle.pagerank(oracle.build_csc(n, src, dst), d, iters)
     x, st = gpu_pr(torch, g, iters, d, dt, stats=True)
     err = l1(x, ref)
@@ -57,11 +60,15 @@ def test_er_10k_fp32_and_bf16(torch):
     check(torch, spec.n, src, dst, spec.iters, gpr.BF16)
 
 
+@pytest.mark.parametrize("hot", [None, "100000", "256"])
 @pytest.mark.parametrize("buckets", [None, "*:1", "*:4", "*:8", "*:32", "*:0", "0:1,3:2,9:16,100:32,*:0"])
-def test_each_bucket_kernel_alone(torch, buckets):
-    # power-law graph with hubs, dangling nodes and isolated nodes
+def test_each_bucket_kernel_alone(torch, buckets, hot):
+    # power-law graph with hubs, dangling nodes and isolated nodes; hot=None
+    # runs without the shared-memory hot pass, "100000" puts every source in
+    # it, "256" splits the rows between the two passes
     src, dst = gen.rmat_coo(30_000, 600_000, seed=31)
-    check(torch, 30_000, src, dst, 30, buckets=buckets)
+    for dt in (gpr.FP32, gpr.BF16):
+        check(torch, 30_000, src, dst, 30, dt=dt, buckets=buckets, hot=hot)
 
 
 def test_split_rows(torch):
@@ -70,6 +77,7 @@ def test_split_rows(torch):
     try:
         src, dst = gen.rmat_coo(20_000, 800_000, seed=32)
         check(torch, 20_000, src, dst, 20, buckets="16:8,*:0")
+        check(torch, 20_000, src, dst, 20, buckets="16:8,*:0", hot="1000")
     finally:
         os.environ.pop("GPR_CHUNK_EDGES", None)
 
