@@ -152,6 +152,69 @@ typedef struct {
 gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
                      void* stream);
 
+/* ---- serving: continuous batching of personalised-PageRank requests ------
+ * A server keeps a pool of graphs resident on the device and answers
+ * personalised-PageRank requests (the same operation as ppr_batch) that
+ * arrive at any time.  A scheduler thread admits queued requests first come,
+ * first served while the device-memory budget allows, packs their columns
+ * into per-graph batches of 64 columns, and runs a few steps of every active
+ * batch per launch; columns that finish free their place, and requests that
+ * arrived meanwhile join the running batches at the next launch.  A
+ * request's result does not depend on the requests it ran with. */
+typedef struct gpr_server gpr_server;
+
+typedef struct {
+  int64_t budget_bytes;    /* device memory for the pool + batch state + results */
+  int32_t max_queue;       /* queued (not yet admitted) requests before GPR_EBUSY; <= 0: 65536 */
+  int32_t steps_per_tick;  /* steps per launch; <= 0: 8 */
+  int32_t fail_alloc_at;   /* test hook: the k-th batch allocation fails as if out of memory (0: off) */
+} gpr_server_config;
+
+typedef struct {
+  int32_t graph_id;      /* index into the pool */
+  int32_t num_seeds;     /* 1..64 */
+  const int32_t* seeds;  /* host: node ids in [0, n); copied by serve_submit */
+  float damping;         /* in (0, 1) */
+  double tol;            /* >= 0; 0: run max_iters steps */
+  int32_t max_iters;     /* >= 0 */
+  gpr_dtype dt;          /* storage of the gathered contributions */
+} gpr_request;
+
+typedef struct {
+  gpr_status status;    /* GPR_OK, or why the request failed (GPR_ENOMEM, GPR_ECUDA) */
+  int32_t n;            /* nodes of the graph */
+  int32_t num_seeds;
+  int32_t iters_max;    /* steps run by the slowest column */
+  double latency_ms;    /* submit to completion */
+  const float* x;       /* device: n x num_seeds FP32, node-major; owned by the
+                           server until serve_release */
+} gpr_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed, rejected_busy, rejected_nomem;
+  int64_t ticks, queued, active_columns, device_bytes_in_use;
+} gpr_server_stats;
+
+/* pool: num_graphs graphs that outlive the server.  Errors: GPR_EINVAL;
+ * GPR_ENOMEM if the pool alone exceeds the budget; GPR_ECUDA. */
+gpr_status serve_create(const gpr_graph* const* pool, int32_t num_graphs, const gpr_server_config* cfg,
+                        gpr_server** out);
+/* Non-blocking.  GPR_EINVAL for a bad request; GPR_ENOMEM if it could never
+ * fit the budget; GPR_EBUSY if the queue is full. */
+gpr_status serve_submit(gpr_server* s, const gpr_request* r, uint64_t* ticket);
+/* Waits up to timeout_us (0: just look) for the request to finish.
+ * GPR_ENOTREADY on timeout; GPR_ENOTFOUND for an unknown ticket. */
+gpr_status serve_poll(gpr_server* s, uint64_t ticket, int64_t timeout_us, gpr_result* r);
+/* Copies a finished result (n x num_seeds floats) to dst (device memory, or
+ * host memory with GPR_PTR_HOST).  Synchronous. */
+gpr_status serve_fetch(gpr_server* s, uint64_t ticket, float* dst, int flags);
+/* Frees a finished result.  GPR_ENOTREADY if it is still running. */
+gpr_status serve_release(gpr_server* s, uint64_t ticket);
+gpr_status serve_stats(gpr_server* s, gpr_server_stats* st);
+/* Stops the scheduler, cancels queued and running requests and frees all
+ * server memory (not the pool).  No serve_* call may run concurrently. */
+gpr_status serve_destroy(gpr_server* s);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* gpr_last_error(void);
 

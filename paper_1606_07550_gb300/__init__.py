@@ -77,6 +77,28 @@ class PprJob(ctypes.Structure):
                 ("residual_out", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_queue", ctypes.c_int32), ("steps_per_tick", ctypes.c_int32),
+                ("fail_alloc_at", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("graph_id", ctypes.c_int32), ("num_seeds", ctypes.c_int32), ("seeds", ctypes.c_void_p),
+                ("damping", ctypes.c_float), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("dt", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n", ctypes.c_int32), ("num_seeds", ctypes.c_int32),
+                ("iters_max", ctypes.c_int32), ("latency_ms", ctypes.c_double), ("x", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "admitted", "completed", "failed", "rejected_busy",
+                                               "rejected_nomem", "ticks", "queued", "active_columns",
+                                               "device_bytes_in_use")]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
                 ("dangling", ctypes.c_double)]
@@ -104,7 +126,17 @@ def lib():
         L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                 ctypes.c_int, _VP]
         L.gpr_kernel_launches.restype = ctypes.c_int64
-        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "ppr_batch"):
+        L.serve_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, ctypes.POINTER(ServerConfig),
+                                   ctypes.POINTER(_VP)]
+        L.serve_submit.argtypes = [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+        L.serve_poll.argtypes = [_VP, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Result)]
+        L.serve_fetch.argtypes = [_VP, ctypes.c_uint64, _VP, ctypes.c_int]
+        L.serve_release.argtypes = [_VP, ctypes.c_uint64]
+        L.serve_stats.argtypes = [_VP, ctypes.POINTER(ServerStats)]
+        L.serve_destroy.argtypes = [_VP]
+        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "ppr_batch",
+                     "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
+                     "serve_destroy"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -232,3 +264,61 @@ def ppr_batch(requests, max_iters: int = 50, tol: float = 0.0, dtype: int = FP32
         results.append((it, res))
     _check(lib().ppr_batch(arr, n_req, max_iters, tol, dtype, _stream_ptr(stream)))
     return results
+
+
+class Server:
+    """Continuous-batching personalised-PageRank server over a resident pool
+    of graphs (see serve_* in include/gpr.h)."""
+
+    def __init__(self, pool, budget_bytes: int, max_queue: int = 0, steps_per_tick: int = 0,
+                 fail_alloc_at: int = 0):
+        self.pool = list(pool)
+        arr = (_VP * len(self.pool))(*[g.handle for g in self.pool])
+        cfg = ServerConfig(budget_bytes, max_queue, steps_per_tick, fail_alloc_at)
+        h = _VP()
+        _check(lib().serve_create(arr, len(self.pool), ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h.value
+
+    def submit(self, graph_id: int, seeds, damping: float = 0.85, tol: float = 0.0, max_iters: int = 50,
+               dtype: int = FP32) -> int:
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+        req = Request(graph_id, len(seeds), seeds.ctypes.data, damping, tol, max_iters, dtype)
+        t = ctypes.c_uint64()
+        _check(lib().serve_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """The Result once finished, or None on timeout."""
+        r = Result()
+        st = lib().serve_poll(self._h, ticket, timeout_us, ctypes.byref(r))
+        if st == ENOTREADY:
+            return None
+        _check(st)
+        return r
+
+    def fetch(self, ticket: int, out):
+        """Copy a finished result into `out` (CUDA tensor or host array, n*k floats)."""
+        po, host = _ptr_and_flag(out)
+        _check(lib().serve_fetch(self._h, ticket, po, PTR_HOST if host else PTR_DEVICE))
+        return out
+
+    def release(self, ticket: int):
+        _check(lib().serve_release(self._h, ticket))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().serve_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().serve_destroy(h))
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.serve_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass

@@ -1,0 +1,599 @@
+// Continuous-batching server for personalised-PageRank requests (the
+// operation of ppr.cu; section 4 Table "snap_methods").
+//
+// A slot is one graph with 64 column places whose rank state (X) and
+// contributions (C, double-buffered) stay on the device between launches.
+// The scheduler thread loops:
+//   1. admit queued requests first come, first served: a request takes
+//      num_seeds free places of a slot of its graph and storage type (a new
+//      slot if none has room) and an n x num_seeds result buffer, if the
+//      device budget allows; otherwise it waits (no overtaking);
+//   2. launch steps_per_tick steps over every slot with live columns, one
+//      persistent launch per storage type (ppr_kernel in slot mode: new
+//      columns start at e_seed, finished ones freeze and are written to
+//      their result buffer by node id);
+//   3. read back the column records, complete requests whose columns are
+//      all finished, free their places and slots that became empty.
+// A column's arithmetic does not depend on the other columns, so a result
+// is the same whether its request ran alone or in a mix.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gpr_internal.cuh"
+#include "ppr_internal.cuh"
+
+namespace gpr {
+
+using Clock = std::chrono::steady_clock;
+
+struct Slot {
+  int graph = -1;
+  gpr_dtype dt = GPR_FP32;
+  float* X = nullptr;
+  void* C0 = nullptr;
+  void* C1 = nullptr;
+  int32_t parity = 0;
+  int64_t bytes = 0;
+  PprCol cols[kPprCols];
+  uint64_t owner[kPprCols];  // ticket holding each place (0: free)
+  int used = 0;
+};
+
+enum ReqState { kQueued, kRunning, kDone, kFailed };
+
+struct Req {
+  uint64_t ticket = 0;
+  int32_t graph = 0;
+  std::vector<int32_t> seeds;
+  float damping = 0.85f;
+  double tol = 0.0;
+  int32_t max_iters = 0;
+  gpr_dtype dt = GPR_FP32;
+  ReqState state = kQueued;
+  gpr_status status = GPR_OK;
+  float* result = nullptr;
+  int64_t result_bytes = 0;
+  int remaining = 0;
+  int32_t iters_max = 0;
+  Clock::time_point t_submit, t_done;
+};
+
+}  // namespace gpr
+
+struct gpr_server {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<const gpr_graph*> pool;
+  gpr_server_config cfg{};
+  int64_t pool_bytes = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, gpr::Req> reqs;
+  std::vector<gpr::Slot*> slots;
+  int64_t bytes_in_use = 0;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread th;
+  int alloc_attempts = 0;
+  gpr_server_stats st{};
+  // device staging for one launch
+  gpr::PprJob* d_jobs = nullptr;
+  gpr::PprCol* d_cols = nullptr;
+  int32_t* d_order = nullptr;
+  uint32_t* d_queue = nullptr;
+  int cap_jobs = 0;
+};
+
+namespace gpr {
+
+static size_t elem_bytes(gpr_dtype dt) { return dt == GPR_FP32 ? 4 : 2; }
+
+static int64_t slot_bytes(const gpr_graph* g, gpr_dtype dt) {
+  return (int64_t)g->n * kPprCols * (4 + 2 * (int64_t)elem_bytes(dt));
+}
+
+static void fill_job(PprJob& J, const gpr_graph* g) {
+  J = PprJob{};
+  J.col_ptr = g->col_ptr;
+  J.row_idx = g->row_idx;
+  J.inv_deg = g->plan.inv_deg;
+  J.old2new = g->plan.old2new;
+  J.n = g->n;
+  J.heavy_rows = g->plan.rows;
+  J.n_heavy = 0;
+  J.heavy_deg = INT_MAX;
+  for (int b = 0; b < g->plan.nbuckets; ++b)
+    if (g->plan.bucket[b].lanes == 0) {
+      J.heavy_rows = g->plan.rows + g->plan.bucket[b].row_begin;
+      J.n_heavy = g->plan.bucket[b].row_end - g->plan.bucket[b].row_begin;
+      J.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : 0;
+    }
+}
+
+static void free_slot(gpr_server* S, Slot* sl) {
+  dfree(sl->X, S->stream);
+  dfree(sl->C0, S->stream);
+  dfree(sl->C1, S->stream);
+  S->bytes_in_use -= sl->bytes;
+  delete sl;
+}
+
+// Place a queued request (lock held).  Returns false if it must wait.
+static bool try_admit(gpr_server* S, Req& r) {
+  const gpr_graph* g = S->pool[r.graph];
+  const int k = (int)r.seeds.size();
+  Slot* target = nullptr;
+  for (Slot* sl : S->slots)
+    if (sl->graph == r.graph && sl->dt == r.dt && kPprCols - sl->used >= k) {
+      target = sl;
+      break;
+    }
+  const int64_t need = (target ? 0 : slot_bytes(g, r.dt)) + (int64_t)g->n * k * 4;
+  if (S->bytes_in_use + need > S->cfg.budget_bytes) return false;
+  try {
+    if (!target) {
+      ++S->alloc_attempts;
+      if (S->cfg.fail_alloc_at > 0 && S->alloc_attempts == S->cfg.fail_alloc_at)
+        throw StatusFail{GPR_ENOMEM, "injected allocation failure"};
+      Slot* sl = new Slot();
+      sl->graph = r.graph;
+      sl->dt = r.dt;
+      sl->bytes = slot_bytes(g, r.dt);
+      try {
+        sl->X = (float*)dalloc((size_t)g->n * kPprCols * 4, S->stream);
+        sl->C0 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
+        sl->C1 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
+      } catch (...) {
+        dfree(sl->X, S->stream);
+        dfree(sl->C0, S->stream);
+        dfree(sl->C1, S->stream);
+        delete sl;
+        throw;
+      }
+      for (int c = 0; c < kPprCols; ++c) {
+        sl->cols[c] = PprCol{};
+        sl->cols[c].status = kColEmpty;
+        sl->cols[c].damping = 0.5f;
+        sl->owner[c] = 0;
+      }
+      S->slots.push_back(sl);
+      S->bytes_in_use += sl->bytes;
+      target = sl;
+    }
+    r.result = (float*)dalloc((size_t)g->n * k * 4, S->stream);
+  } catch (const StatusFail& f) {
+    r.state = kFailed;
+    r.status = f.st;
+    r.t_done = Clock::now();
+    ++S->st.failed;
+    S->cv_done.notify_all();
+    return true;  // consumed (failed), the queue moves on
+  }
+  r.result_bytes = (int64_t)g->n * k * 4;
+  S->bytes_in_use += r.result_bytes;
+  int placed = 0;
+  for (int c = 0; c < kPprCols && placed < k; ++c) {
+    if (target->owner[c]) continue;
+    PprCol& col = target->cols[c];
+    col = PprCol{};
+    col.status = kColFresh;
+    col.seed = r.seeds[placed];
+    col.damping = r.damping;
+    col.tol = (float)r.tol;
+    col.max_iters = r.max_iters;
+    col.out = r.result + placed;
+    col.ldo = k;
+    target->owner[c] = r.ticket;
+    ++placed;
+  }
+  target->used += k;
+  r.state = kRunning;
+  r.remaining = k;
+  ++S->st.admitted;
+  return true;
+}
+
+static void ensure_staging(gpr_server* S, int jobs) {
+  if (jobs <= S->cap_jobs) return;
+  dfree(S->d_jobs, S->stream);
+  dfree(S->d_cols, S->stream);
+  dfree(S->d_order, S->stream);
+  S->d_jobs = nullptr;
+  S->d_cols = nullptr;
+  S->d_order = nullptr;
+  S->cap_jobs = 0;
+  const int cap = std::max(jobs, 2 * S->cap_jobs + 16);
+  S->d_jobs = (PprJob*)dalloc((size_t)cap * sizeof(PprJob), S->stream);
+  S->d_cols = (PprCol*)dalloc((size_t)cap * kPprCols * sizeof(PprCol), S->stream);
+  S->d_order = (int32_t*)dalloc((size_t)cap * 4, S->stream);
+  S->cap_jobs = cap;
+}
+
+// One launch per storage type over the slots with live columns; then the
+// column records come back.  Runs without the lock: only the scheduler
+// thread touches slots.
+static void run_tick(gpr_server* S, const std::vector<Slot*>& live) {
+  ensure_staging(S, (int)live.size());
+  std::vector<PprJob> jobs(live.size());
+  std::vector<PprCol> cols(live.size() * kPprCols);
+  std::vector<int32_t> order(live.size());
+  for (size_t i = 0; i < live.size(); ++i) {
+    Slot* sl = live[i];
+    fill_job(jobs[i], S->pool[sl->graph]);
+    jobs[i].X = sl->X;
+    jobs[i].C0 = sl->C0;
+    jobs[i].C1 = sl->C1;
+    jobs[i].parity = sl->parity;
+    jobs[i].iters = S->cfg.steps_per_tick;
+    jobs[i].cols = S->d_cols + i * kPprCols;
+    std::copy(sl->cols, sl->cols + kPprCols, cols.begin() + i * kPprCols);
+  }
+  GPR_CUDA(cudaMemcpyAsync(S->d_jobs, jobs.data(), jobs.size() * sizeof(PprJob), cudaMemcpyHostToDevice, S->stream));
+  GPR_CUDA(cudaMemcpyAsync(S->d_cols, cols.data(), cols.size() * sizeof(PprCol), cudaMemcpyHostToDevice, S->stream));
+  for (gpr_dtype dt : {GPR_FP32, GPR_BF16, GPR_FP16}) {
+    int cnt = 0;
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i]->dt == dt) order[cnt++] = (int32_t)i;
+    if (!cnt) continue;
+    // largest graphs first
+    std::stable_sort(order.begin(), order.begin() + cnt, [&](int32_t a, int32_t b) {
+      return S->pool[live[a]->graph]->m > S->pool[live[b]->graph]->m;
+    });
+    GPR_CUDA(cudaMemcpyAsync(S->d_order, order.data(), cnt * 4, cudaMemcpyHostToDevice, S->stream));
+    GPR_CUDA(cudaMemsetAsync(S->d_queue, 0, 16, S->stream));
+    const int clusters = std::max(1, std::min(ppr_max_clusters(dt), cnt));
+    ppr_launch(S->d_jobs, S->d_order, cnt, S->d_queue, nullptr, 0, clusters, dt, S->stream);
+    // the launch reads order/queue asynchronously: finish it before reusing them
+    GPR_CUDA(cudaStreamSynchronize(S->stream));
+  }
+  GPR_CUDA(cudaMemcpyAsync(cols.data(), S->d_cols, cols.size() * sizeof(PprCol), cudaMemcpyDeviceToHost, S->stream));
+  GPR_CUDA(cudaMemcpyAsync(jobs.data(), S->d_jobs, jobs.size() * sizeof(PprJob), cudaMemcpyDeviceToHost, S->stream));
+  GPR_CUDA(cudaStreamSynchronize(S->stream));
+  for (size_t i = 0; i < live.size(); ++i) {
+    std::copy(cols.begin() + i * kPprCols, cols.begin() + (i + 1) * kPprCols, live[i]->cols);
+    live[i]->parity = jobs[i].parity;
+  }
+}
+
+static void fail_running(gpr_server* S, gpr_status st) {
+  for (Slot* sl : S->slots) {
+    for (int c = 0; c < kPprCols; ++c) {
+      if (!sl->owner[c]) continue;
+      auto it = S->reqs.find(sl->owner[c]);
+      if (it != S->reqs.end() && it->second.state == kRunning) {
+        it->second.state = kFailed;
+        it->second.status = st;
+        it->second.t_done = Clock::now();
+        ++S->st.failed;
+      }
+      sl->owner[c] = 0;
+      sl->cols[c].status = kColEmpty;
+    }
+    sl->used = 0;
+  }
+  S->cv_done.notify_all();
+}
+
+static void scheduler(gpr_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    // 1. admission, first come first served
+    while (!S->queue.empty()) {
+      auto it = S->reqs.find(S->queue.front());
+      if (it == S->reqs.end()) {
+        S->queue.pop_front();
+        continue;
+      }
+      if (!try_admit(S, it->second)) break;
+      S->queue.pop_front();
+    }
+    std::vector<Slot*> live;
+    for (Slot* sl : S->slots)
+      if (sl->used > 0) live.push_back(sl);
+    if (live.empty()) {
+      if (S->stop) break;
+      S->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    if (S->stop) break;
+    // 2. one tick on the device
+    lk.unlock();
+    bool ok = true;
+    std::string err;
+    try {
+      run_tick(S, live);
+    } catch (const CudaFail& f) {
+      cudaGetLastError();
+      ok = false;
+      err = std::string(f.what) + ": " + cudaGetErrorString(f.err);
+    } catch (const StatusFail& f) {
+      ok = false;
+      err = f.msg;
+    }
+    lk.lock();
+    ++S->st.ticks;
+    if (!ok) {
+      fail_running(S, GPR_ECUDA);
+      continue;
+    }
+    // 3. retire finished columns and requests
+    const auto now = Clock::now();
+    for (Slot* sl : live) {
+      for (int c = 0; c < kPprCols; ++c) {
+        if (!sl->owner[c] || sl->cols[c].status != kColDone) continue;
+        auto it = S->reqs.find(sl->owner[c]);
+        if (it != S->reqs.end()) {
+          Req& r = it->second;
+          r.iters_max = std::max(r.iters_max, sl->cols[c].iters);
+          if (--r.remaining == 0 && r.state == kRunning) {
+            r.state = kDone;
+            r.status = GPR_OK;
+            r.t_done = now;
+            ++S->st.completed;
+          }
+        }
+        sl->owner[c] = 0;
+        sl->cols[c] = PprCol{};
+        sl->cols[c].status = kColEmpty;
+        sl->cols[c].damping = 0.5f;
+        --sl->used;
+      }
+    }
+    for (size_t i = 0; i < S->slots.size();) {
+      if (S->slots[i]->used == 0) {
+        free_slot(S, S->slots[i]);
+        S->slots.erase(S->slots.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    S->cv_done.notify_all();
+  }
+}
+
+}  // namespace gpr
+
+using namespace gpr;
+
+extern "C" {
+
+gpr_status serve_create(const gpr_graph* const* pool, int32_t num_graphs, const gpr_server_config* cfg,
+                        gpr_server** out) {
+  clear_error();
+  if (!out || !cfg || num_graphs < 1 || !pool) {
+    set_error("serve_create: bad arguments");
+    return GPR_EINVAL;
+  }
+  *out = nullptr;
+  for (int32_t i = 0; i < num_graphs; ++i)
+    if (!pool[i]) {
+      set_error("serve_create: pool graph %d is NULL", (int)i);
+      return GPR_EINVAL;
+    }
+  gpr_server* S = new gpr_server();
+  S->device = device_ordinal();
+  S->pool.assign(pool, pool + num_graphs);
+  S->cfg = *cfg;
+  if (S->cfg.max_queue <= 0) S->cfg.max_queue = 65536;
+  if (S->cfg.steps_per_tick <= 0) S->cfg.steps_per_tick = 8;
+  std::vector<const gpr_graph*> uniq(S->pool);
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  for (const gpr_graph* g : uniq) S->pool_bytes += g->device_bytes;
+  S->bytes_in_use = S->pool_bytes;
+  if (S->pool_bytes > S->cfg.budget_bytes) {
+    set_error("serve_create: the pool alone (%lld bytes) exceeds the budget", (long long)S->pool_bytes);
+    delete S;
+    return GPR_ENOMEM;
+  }
+  try {
+    GPR_CUDA(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+    S->d_queue = (uint32_t*)dalloc(16, S->stream);
+  } catch (const StatusFail& f) {
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    set_error("serve_create: %s", f.msg.c_str());
+    return f.st;
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    set_error("serve_create: %s failed: %s", f.what, cudaGetErrorString(f.err));
+    return GPR_ECUDA;
+  }
+  S->th = std::thread(scheduler, S);
+  *out = S;
+  return GPR_OK;
+}
+
+gpr_status serve_submit(gpr_server* S, const gpr_request* r, uint64_t* ticket) {
+  clear_error();
+  if (!S || !r || !ticket) {
+    set_error("serve_submit: NULL argument");
+    return GPR_EINVAL;
+  }
+  if (r->graph_id < 0 || r->graph_id >= (int32_t)S->pool.size()) {
+    set_error("serve_submit: graph_id %d not in the pool", (int)r->graph_id);
+    return GPR_EINVAL;
+  }
+  const gpr_graph* g = S->pool[r->graph_id];
+  if (r->num_seeds < 1 || r->num_seeds > kPprCols || !r->seeds) {
+    set_error("serve_submit: num_seeds %d outside [1, %d]", (int)r->num_seeds, kPprCols);
+    return GPR_EINVAL;
+  }
+  for (int32_t k = 0; k < r->num_seeds; ++k)
+    if (r->seeds[k] < 0 || r->seeds[k] >= g->n) {
+      set_error("serve_submit: seed %d outside [0, %d)", (int)r->seeds[k], (int)g->n);
+      return GPR_EINVAL;
+    }
+  if (!(r->damping > 0.f && r->damping < 1.f) || !(r->tol >= 0.0) || r->max_iters < 0 ||
+      (r->dt != GPR_FP32 && r->dt != GPR_BF16 && r->dt != GPR_FP16)) {
+    set_error("serve_submit: damping, tol, max_iters or dtype out of range");
+    return GPR_EINVAL;
+  }
+  const int64_t alone = S->pool_bytes + slot_bytes(g, r->dt) + (int64_t)g->n * r->num_seeds * 4;
+  std::lock_guard<std::mutex> lk(S->mu);
+  ++S->st.submitted;
+  if (alone > S->cfg.budget_bytes) {
+    ++S->st.rejected_nomem;
+    set_error("serve_submit: the request needs %lld bytes with the pool; the budget is %lld", (long long)alone,
+              (long long)S->cfg.budget_bytes);
+    return GPR_ENOMEM;
+  }
+  if ((int32_t)S->queue.size() >= S->cfg.max_queue) {
+    ++S->st.rejected_busy;
+    set_error("serve_submit: queue full");
+    return GPR_EBUSY;
+  }
+  Req q;
+  q.ticket = S->next_ticket++;
+  q.graph = r->graph_id;
+  q.seeds.assign(r->seeds, r->seeds + r->num_seeds);
+  q.damping = r->damping;
+  q.tol = r->tol;
+  q.max_iters = r->max_iters;
+  q.dt = r->dt;
+  q.t_submit = Clock::now();
+  *ticket = q.ticket;
+  S->reqs.emplace(q.ticket, std::move(q));
+  S->queue.push_back(*ticket);
+  S->cv_work.notify_one();
+  return GPR_OK;
+}
+
+gpr_status serve_poll(gpr_server* S, uint64_t ticket, int64_t timeout_us, gpr_result* out) {
+  clear_error();
+  if (!S || !out) {
+    set_error("serve_poll: NULL argument");
+    return GPR_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto ready = [&]() {
+    auto it = S->reqs.find(ticket);
+    return it == S->reqs.end() || it->second.state == kDone || it->second.state == kFailed;
+  };
+  if (timeout_us > 0) S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) {
+    set_error("serve_poll: unknown ticket %llu", (unsigned long long)ticket);
+    return GPR_ENOTFOUND;
+  }
+  Req& r = it->second;
+  if (r.state != kDone && r.state != kFailed) return GPR_ENOTREADY;
+  out->status = r.status;
+  out->n = S->pool[r.graph]->n;
+  out->num_seeds = (int32_t)r.seeds.size();
+  out->iters_max = r.iters_max;
+  out->latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+  out->x = r.state == kDone ? r.result : nullptr;
+  return GPR_OK;
+}
+
+gpr_status serve_fetch(gpr_server* S, uint64_t ticket, float* dst, int flags) {
+  clear_error();
+  if (!S || !dst) {
+    set_error("serve_fetch: NULL argument");
+    return GPR_EINVAL;
+  }
+  const float* src = nullptr;
+  size_t bytes = 0;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) {
+      set_error("serve_fetch: unknown ticket");
+      return GPR_ENOTFOUND;
+    }
+    if (it->second.state != kDone) {
+      set_error("serve_fetch: request not finished");
+      return GPR_ENOTREADY;
+    }
+    src = it->second.result;
+    bytes = (size_t)it->second.result_bytes;
+  }
+  cudaError_t e = cudaMemcpy(dst, src, bytes, (flags & GPR_PTR_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) {
+    set_error("serve_fetch: %s", cudaGetErrorString(e));
+    return GPR_ECUDA;
+  }
+  return GPR_OK;
+}
+
+gpr_status serve_release(gpr_server* S, uint64_t ticket) {
+  clear_error();
+  if (!S) {
+    set_error("serve_release: NULL server");
+    return GPR_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) {
+    set_error("serve_release: unknown ticket");
+    return GPR_ENOTFOUND;
+  }
+  if (it->second.state != kDone && it->second.state != kFailed) {
+    set_error("serve_release: request still queued or running");
+    return GPR_ENOTREADY;
+  }
+  if (it->second.result) {
+    dfree(it->second.result, S->stream);
+    S->bytes_in_use -= it->second.result_bytes;
+  }
+  S->reqs.erase(it);
+  S->cv_work.notify_one();
+  return GPR_OK;
+}
+
+gpr_status serve_stats(gpr_server* S, gpr_server_stats* st) {
+  clear_error();
+  if (!S || !st) {
+    set_error("serve_stats: NULL argument");
+    return GPR_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  *st = S->st;
+  st->queued = (int64_t)S->queue.size();
+  int64_t cols = 0;
+  for (Slot* sl : S->slots) cols += sl->used;
+  st->active_columns = cols;
+  st->device_bytes_in_use = S->bytes_in_use;
+  return GPR_OK;
+}
+
+gpr_status serve_destroy(gpr_server* S) {
+  clear_error();
+  if (!S) return GPR_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv_work.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  cudaStreamSynchronize(S->stream);
+  for (Slot* sl : S->slots) free_slot(S, sl);
+  S->slots.clear();
+  for (auto& kv : S->reqs)
+    if (kv.second.result) dfree(kv.second.result, S->stream);
+  dfree(S->d_jobs, S->stream);
+  dfree(S->d_cols, S->stream);
+  dfree(S->d_order, S->stream);
+  dfree(S->d_queue, S->stream);
+  cudaError_t e = cudaStreamSynchronize(S->stream);
+  cudaStreamDestroy(S->stream);
+  delete S;
+  if (e != cudaSuccess) {
+    set_error("serve_destroy: %s", cudaGetErrorString(e));
+    return GPR_ECUDA;
+  }
+  return GPR_OK;
+}
+
+}  // extern "C"
