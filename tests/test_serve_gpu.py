@@ -87,7 +87,7 @@ def test_alone_equals_mix_and_admission_mid_flight(torch, pool):
         assert wait(srv, t).status == gpr.OK
         srv.release(t)
     st = srv.stats()
-    assert st["completed"] == 24 and st["failed"] == 0
+    assert st["completed"] == 23 and st["failed"] == 0
     srv.close()
 
 
