@@ -108,6 +108,9 @@ def test_budget_admission_and_rejections(torch, pool):
     assert ei.value.status == gpr.ENOMEM
     small.close()
     t1 = srv.submit(2, list(range(64)), max_iters=300)
+    t0 = time.time()
+    while srv.stats()["admitted"] < 1 and time.time() - t0 < 30:  # t1 leaves the queue
+        time.sleep(0.001)
     t2 = srv.submit(2, list(range(64, 128)), max_iters=10)   # waits: the budget holds one
     with pytest.raises(gpr.GprError) as ei:
         srv.submit(2, [7], max_iters=10)                      # queue (max 1) is full
