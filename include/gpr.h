@@ -215,6 +215,28 @@ gpr_status serve_stats(gpr_server* s, gpr_server_stats* st);
  * server memory (not the pool).  No serve_* call may run concurrently. */
 gpr_status serve_destroy(gpr_server* s);
 
+/* ---- allocation-free variant (no counterpart in the paper) ----------------
+ * pagerank_csc_noalloc: the iteration of `pagerank` (same update, same FP64
+ * mass normalisation, FP32 contributions) on a CSC that the caller already
+ * holds in device memory, for callers that cannot allocate device memory:
+ * hosts that run on a fixed memory plan made at start-up, allocator-free
+ * regions of a larger runtime, or code that shares the device with an
+ * allocator it does not own.  It allocates nothing: its scratch is one
+ * static device array of about 24 MiB that every GPU loading this library
+ * holds until the process exits.
+ *   col_ptr (n + 1), row_idx (m), outdeg (n): device int32 arrays of the
+ *             in-adjacency (sources of node v are row_idx[col_ptr[v] ..
+ *             col_ptr[v+1]), any order), as graph_export returns them.
+ *   n       : 1 <= n <= 2^21 (the scratch size); larger n is GPR_EINVAL.
+ *   x_out   : device, n floats, written by node id.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one scratch array: calls whose work overlaps on the
+ * GPU (on different streams, or from different threads) race.  Work is
+ * queued on `stream`; the call does not synchronise it. */
+gpr_status pagerank_csc_noalloc(const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg, int32_t n,
+                                double damping, int32_t iters, float* x_out, void* stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* gpr_last_error(void);
 

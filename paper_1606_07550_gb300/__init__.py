@@ -134,6 +134,8 @@ def lib():
         L.serve_release.argtypes = [_VP, ctypes.c_uint64]
         L.serve_stats.argtypes = [_VP, ctypes.POINTER(ServerStats)]
         L.serve_destroy.argtypes = [_VP]
+        L.pagerank_csc_noalloc.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _VP, _VP]
+        L.pagerank_csc_noalloc.restype = ctypes.c_int
         for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "ppr_batch",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
                      "serve_destroy"):
@@ -322,3 +324,14 @@ class Server:
                 self._h = None
         except Exception:
             pass
+
+
+def pagerank_csc_noalloc(col_ptr, row_idx, outdeg, n: int, out, damping: float = 0.85, iters: int = 50,
+                         stream=None):
+    """PageRank on a caller-held device CSC without any device allocation
+    (int32 CUDA tensors col_ptr, row_idx, outdeg; float32 CUDA tensor out)."""
+    for t in (col_ptr, row_idx, outdeg, out):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("pagerank_csc_noalloc takes contiguous CUDA tensors")
+    _check(lib().pagerank_csc_noalloc(col_ptr.data_ptr(), row_idx.data_ptr(), outdeg.data_ptr(), n, damping, iters,
+                                      out.data_ptr(), _stream_ptr(stream)))
