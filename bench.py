@@ -44,7 +44,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpr", "reference"], default="gpr")
-    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k"], default="rmat25")
+    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve"], default="rmat25")
+    ap.add_argument("--graphs", type=int, default=4096, help="batched: number of graphs")
+    ap.add_argument("--dtypes", default="fp32,bf16,fp16", help="batched: contribution storage types")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-warmup", type=float, default=5.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--pool", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-scale", type=int, default=19)
@@ -372,11 +378,239 @@ def run_gpr(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def build_graph_dev(torch, gpr, spec, stream=None):
+    """Device-generated R-MAT COO of `spec` -> graph (the COO is freed)."""
+    import gen
+    s = torch.empty(spec.m, dtype=torch.int32, device="cuda")
+    d = torch.empty(spec.m, dtype=torch.int32, device="cuda")
+    perm = torch.from_numpy(gen.permutation(spec.n, spec.seed)).cuda()
+    gen.rmat_coo_dev(spec.n, spec.m, spec.seed, s.data_ptr(), d.data_ptr(), perm.data_ptr(),
+                     stream=torch.cuda.current_stream().cuda_stream, abc=spec.abc)
+    return gpr.graph_build(s, d, spec.n)
+
+
+def run_batched(args, world, rank, local):
+    """Config: 4,096 R-MAT graphs (n log-uniform in [1e3, 2e5], mean out-degree
+    uniform in [4, 32]), 64 personalised-PageRank seeds each, damping 0.85,
+    50 steps, one persistent launch per storage type.  Baselines on the same
+    GPU: one solve per call (ppr_batch with one seed) and plain PageRank
+    (pagerank, one vector) per solve, each timed on a sample and expressed in
+    solves/s.  Accuracy: sampled columns against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import gen
+    import oracle
+    import paper_1606_07550_gb300 as gpr
+    from gen import workloads
+
+    torch.cuda.set_device(local)
+    specs = workloads.batched_specs(args.graphs)
+    t0 = time.perf_counter()
+    graphs = [build_graph_dev(torch, gpr, sp) for sp in specs]
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    seeds = [gen.seed_nodes(sp.n, 64, workloads.batched_seed_base(g)) for g, sp in enumerate(specs)]
+    outs = [torch.empty((sp.n, 64), dtype=torch.float32, device="cuda") for sp in specs]
+    reqs = [(g, s, 0.85, o) for g, s, o in zip(graphs, seeds, outs)]
+    iters = 50
+    n_solves = 64 * len(specs)
+    refs = []  # (graph, column, oracle x) on every 256th graph
+    for g in range(0, len(specs), 256):
+        sp = specs[g]
+        src, dst = gen.rmat_coo(sp.n, sp.m, seed=sp.seed)
+        csc = oracle.build_csc(sp.n, src, dst)
+        for k in (0, 21, 42, 63):
+            refs.append((g, k, oracle.ppr(csc, int(seeds[g][k]), 0.85, iters)[0]))
+    dts = {"fp32": gpr.FP32, "bf16": gpr.BF16, "fp16": gpr.FP16}
+    res = {}
+    stream = torch.cuda.current_stream()
+    for name in args.dtypes.split(","):
+        dt = dts[name]
+        for _ in range(max(1, args.warmup)):
+            gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        # accuracy on sampled graphs, 4 seeds each, against the FP64 oracle
+        l1s, mrs = [], []
+        for g, k, xr in refs:
+            x = outs[g][:, k].cpu().numpy()
+            l1s.append(float(np.abs(x - xr).sum()))
+            nz = xr > 0
+            mrs.append(float(np.max(np.abs(x[nz] - xr[nz]) / xr[nz])) if nz.any() else 0.0)
+        res[name] = {"ms": ms, "solves_per_s": n_solves / (ms * 1e-3), "l1_max": max(l1s),
+                     "l1_mean": statistics.mean(l1s), "max_rel_err_max": max(mrs), "sampled_columns": len(l1s)}
+    # baselines: one solve at a time, on a sample of (graph, seed) pairs
+    sample = list(range(0, len(specs), max(1, len(specs) // 64)))
+    one_out = [torch.empty((specs[g].n, 1), dtype=torch.float32, device="cuda") for g in sample]
+    for i, g in enumerate(sample[:4]):
+        gpr.ppr_batch([(graphs[g], seeds[g][:1], 0.85, one_out[i])], max_iters=iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, g in enumerate(sample):
+        gpr.ppr_batch([(graphs[g], seeds[g][:1], 0.85, one_out[i])], max_iters=iters)
+    torch.cuda.synchronize()
+    one_ppr = len(sample) / (time.perf_counter() - t0)
+    pr_out = [torch.empty(specs[g].n, dtype=torch.float32, device="cuda") for g in sample]
+    for i, g in enumerate(sample[:4]):
+        gpr.pagerank(graphs[g], pr_out[i], iters=iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, g in enumerate(sample):
+        gpr.pagerank(graphs[g], pr_out[i], iters=iters)
+    torch.cuda.synchronize()
+    one_pr = len(sample) / (time.perf_counter() - t0)
+    sum_n = sum(sp.n for sp in specs)
+    sum_m = sum(g.m for g in graphs)
+    best = res.get("fp32") or next(iter(res.values()))
+    line = {
+        "metric": "PPR solves/s (batched)", "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched-ppr-4096x64", "graphs": len(specs), "seeds_per_graph": 64, "iters": iters,
+                   "damping": 0.85, "sum_n": sum_n, "sum_m": sum_m, "sum_m_raw": sum(sp.m for sp in specs),
+                   "step": "one ppr_batch call: every column of every graph, one persistent launch"},
+        "by_dtype": res,
+        "one_at_a_time": {"ppr_single_seed_solves_per_s": one_ppr, "plain_pagerank_solves_per_s": one_pr,
+                          "sample_pairs": len(sample),
+                          "speedup_vs_single_seed": best["solves_per_s"] / one_ppr,
+                          "speedup_vs_plain_pagerank": best["solves_per_s"] / one_pr},
+        "setup_s": t_setup,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, world, rank, local):
+    """Config: a resident pool of 256 R-MAT graphs (scales 14-22, edge factor
+    16); Poisson arrivals at 2,000 requests/s, each naming a graph, 1-64 seeds,
+    damping in [0.80, 0.90] and tolerance 1e-6 or 1e-3 (BF16 contributions for
+    half of the 1e-3 requests); admission under a 40 GB device budget that
+    includes the pool.  Reports submit-to-completion p50/p99 over the requests
+    that arrived in the measured window, solves/s completed in the window (one
+    seed = one solve), rejections and the backlog.  Baseline on the same GPU:
+    the same kind of requests solved one seed per call (ppr_batch with one
+    seed), on a sample of the trace."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_1606_07550_gb300 as gpr
+    from gen import workloads
+
+    torch.cuda.set_device(local)
+    specs = workloads.serving_pool_specs(args.pool)
+    t0 = time.perf_counter()
+    graphs = [build_graph_dev(torch, gpr, sp) for sp in specs]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    t_setup = time.perf_counter() - t0
+    warm, window = args.serve_warmup, args.serve_seconds
+    trace = workloads.serving_trace([sp.n for sp in specs], rate=args.serve_rate, duration=warm + window, seed=7)
+    budget = 40 << 30
+    srv = gpr.Server(graphs, budget_bytes=budget, max_queue=1 << 20, steps_per_tick=8)
+    info = {}     # ticket -> (arrival s, seeds)
+    done = {}     # ticket -> (latency ms, status, steps, completion s)
+    rejected = {"busy": 0, "nomem": 0}
+    stop = threading.Event()
+    tstart = time.perf_counter()
+
+    def collector():
+        while True:
+            ts = srv.completed(timeout_us=20_000)
+            now = time.perf_counter() - tstart
+            for t in ts:
+                r = srv.poll(t)
+                done[t] = (r.latency_ms, r.status, r.iters_max, now)
+                srv.release(t)
+            if stop.is_set() and not ts:
+                return
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    i = 0
+    while i < len(trace):
+        now = time.perf_counter() - tstart
+        while i < len(trace) and trace[i].t_arrive <= now:
+            q = trace[i]
+            try:
+                t = srv.submit(q.graph, q.seeds, damping=q.damping, tol=q.tol, max_iters=1000,
+                               dtype=gpr.BF16 if q.bf16 else gpr.FP32)
+                info[t] = (q.t_arrive, len(q.seeds))
+            except gpr.GprError as e:
+                rejected["busy" if e.status == gpr.EBUSY else "nomem"] += 1
+            i += 1
+        if i < len(trace):
+            time.sleep(max(0.0, min(0.002, trace[i].t_arrive - (time.perf_counter() - tstart))))
+    t_submitted = time.perf_counter() - tstart
+    drain_limit = 30.0
+    while len(done) < len(info) and time.perf_counter() - tstart < t_submitted + drain_limit:
+        time.sleep(0.05)
+    stop.set()
+    th.join(timeout=10)
+    st = srv.stats()
+    srv.close()
+    in_window = [t for t, (a, _) in info.items() if warm <= a < warm + window]
+    lat = sorted(done[t][0] for t in in_window if t in done and done[t][1] == gpr.OK)
+    unfinished = sum(1 for t in in_window if t not in done)
+    solves = sum(info[t][1] for t, d in done.items() if d[1] == gpr.OK and warm <= d[3] < warm + window)
+    offered = sum(info[t][1] for t in in_window)
+
+    def pct(a, q):
+        return a[min(len(a) - 1, int(q * len(a)))] if a else None
+
+    # baseline: one seed per call, on a sample of the trace's requests
+    sample = trace[:: max(1, len(trace) // 40)][:40]
+    outs = [torch.empty((graphs[q.graph].n, 1), dtype=torch.float32, device="cuda") for q in sample]
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
+    nb = 0
+    for q, o in zip(sample, outs):
+        for sd in q.seeds:
+            gpr.ppr_batch([(graphs[q.graph], [int(sd)], q.damping, o)], max_iters=1000, tol=q.tol,
+                          dtype=gpr.BF16 if q.bf16 else gpr.FP32)
+            nb += 1
+    torch.cuda.synchronize()
+    base = nb / (time.perf_counter() - b0)
+    line = {
+        "metric": "PPR solves/s (served)", "value": solves / window, "unit": "solves/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": window * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving-pool256-poisson", "pool_graphs": len(specs),
+                   "pool_raw_edges": sum(sp.m for sp in specs), "rate_req_per_s": args.serve_rate,
+                   "warmup_s": warm, "window_s": window, "budget_bytes": budget, "steps_per_tick": 8,
+                   "max_iters": 1000},
+        "latency_ms": {"p50": pct(lat, 0.50), "p99": pct(lat, 0.99), "completed": len(lat),
+                       "arrived_in_window": len(in_window), "unfinished_after_drain": unfinished},
+        "offered_solves_per_s": offered / window,
+        "rejected": rejected,
+        "server": st,
+        "one_at_a_time_solves_per_s": base, "baseline_sample_solves": nb,
+        "speedup_vs_one_at_a_time": (solves / window) / base if base else None,
+        "setup_s": t_setup,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_gpr(args, world, rank, local)
     if world > 1:

@@ -205,6 +205,10 @@ gpr_status serve_submit(gpr_server* s, const gpr_request* r, uint64_t* ticket);
 /* Waits up to timeout_us (0: just look) for the request to finish.
  * GPR_ENOTREADY on timeout; GPR_ENOTFOUND for an unknown ticket. */
 gpr_status serve_poll(gpr_server* s, uint64_t ticket, int64_t timeout_us, gpr_result* r);
+/* Completion queue: waits up to timeout_us (0: just look) for requests to
+ * finish (successfully or not) and writes up to cap of their tickets, each
+ * reported once, to `tickets`; *count receives how many. */
+gpr_status serve_completed(gpr_server* s, uint64_t* tickets, int32_t cap, int64_t timeout_us, int32_t* count);
 /* Copies a finished result (n x num_seeds floats) to dst (device memory, or
  * host memory with GPR_PTR_HOST).  Synchronous. */
 gpr_status serve_fetch(gpr_server* s, uint64_t ticket, float* dst, int flags);

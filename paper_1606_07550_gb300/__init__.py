@@ -131,6 +131,8 @@ def lib():
         L.serve_submit.argtypes = [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
         L.serve_poll.argtypes = [_VP, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Result)]
         L.serve_fetch.argtypes = [_VP, ctypes.c_uint64, _VP, ctypes.c_int]
+        L.serve_completed.argtypes = [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int32)]
         L.serve_release.argtypes = [_VP, ctypes.c_uint64]
         L.serve_stats.argtypes = [_VP, ctypes.POINTER(ServerStats)]
         L.serve_destroy.argtypes = [_VP]
@@ -138,7 +140,7 @@ def lib():
         L.pagerank_csc_noalloc.restype = ctypes.c_int
         for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "ppr_batch",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
-                     "serve_destroy"):
+                     "serve_destroy", "serve_completed"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -297,6 +299,13 @@ class Server:
             return None
         _check(st)
         return r
+
+    def completed(self, timeout_us: int = 0, cap: int = 4096):
+        """Tickets of requests that finished since the last call."""
+        buf = (ctypes.c_uint64 * cap)()
+        cnt = ctypes.c_int32()
+        _check(lib().serve_completed(self._h, buf, cap, timeout_us, ctypes.byref(cnt)))
+        return list(buf[: cnt.value])
 
     def fetch(self, ticket: int, out):
         """Copy a finished result into `out` (CUDA tensor or host array, n*k floats)."""

@@ -75,6 +75,7 @@ struct gpr_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> queue;
+  std::deque<uint64_t> finished;  // completion queue for serve_completed
   std::unordered_map<uint64_t, gpr::Req> reqs;
   std::vector<gpr::Slot*> slots;
   int64_t bytes_in_use = 0;
@@ -173,6 +174,7 @@ static bool try_admit(gpr_server* S, Req& r) {
     r.status = f.st;
     r.t_done = Clock::now();
     ++S->st.failed;
+    S->finished.push_back(r.ticket);
     S->cv_done.notify_all();
     return true;  // consumed (failed), the queue moves on
   }
@@ -272,6 +274,7 @@ static void fail_running(gpr_server* S, gpr_status st) {
         it->second.status = st;
         it->second.t_done = Clock::now();
         ++S->st.failed;
+        S->finished.push_back(it->first);
       }
       sl->owner[c] = 0;
       sl->cols[c].status = kColEmpty;
@@ -338,6 +341,7 @@ static void scheduler(gpr_server* S) {
             r.status = GPR_OK;
             r.t_done = now;
             ++S->st.completed;
+            S->finished.push_back(r.ticket);
           }
         }
         sl->owner[c] = 0;
@@ -494,6 +498,24 @@ gpr_status serve_poll(gpr_server* S, uint64_t ticket, int64_t timeout_us, gpr_re
   out->iters_max = r.iters_max;
   out->latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
   out->x = r.state == kDone ? r.result : nullptr;
+  return GPR_OK;
+}
+
+gpr_status serve_completed(gpr_server* S, uint64_t* tickets, int32_t cap, int64_t timeout_us, int32_t* count) {
+  clear_error();
+  if (!S || !tickets || cap < 1 || !count) {
+    set_error("serve_completed: bad arguments");
+    return GPR_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (timeout_us > 0 && S->finished.empty())
+    S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&]() { return !S->finished.empty(); });
+  int32_t k = 0;
+  while (k < cap && !S->finished.empty()) {
+    tickets[k++] = S->finished.front();
+    S->finished.pop_front();
+  }
+  *count = k;
   return GPR_OK;
 }
 
