@@ -37,7 +37,7 @@ namespace cg = cooperative_groups;
 
 namespace gpr {
 
-constexpr int kPprThreads = 512;
+constexpr int kPprThreads = 1024;
 constexpr int kPprWarps = kPprThreads / 32;
 
 // FP16 contributions are stored times 2^10 (values of a personalised column
@@ -112,15 +112,15 @@ __device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx
     const int32_t idx = (e + lane < e1) ? __ldcs(row_idx + e + lane) : 0;
     const int cnt = min(32, e1 - e);
     int j = 0;
-    for (; j + 4 <= cnt; j += 4) {
-      const int32_t u0 = __shfl_sync(0xffffffffu, idx, j), u1 = __shfl_sync(0xffffffffu, idx, j + 1);
-      const int32_t u2 = __shfl_sync(0xffffffffu, idx, j + 2), u3 = __shfl_sync(0xffffffffu, idx, j + 3);
-      const float2 v0 = ld_pair(C + (int64_t)u0 * kPprCols + 2 * lane);
-      const float2 v1 = ld_pair(C + (int64_t)u1 * kPprCols + 2 * lane);
-      const float2 v2 = ld_pair(C + (int64_t)u2 * kPprCols + 2 * lane);
-      const float2 v3 = ld_pair(C + (int64_t)u3 * kPprCols + 2 * lane);
-      ax += (v0.x + v1.x) + (v2.x + v3.x);
-      ay += (v0.y + v1.y) + (v2.y + v3.y);
+    for (; j + 8 <= cnt; j += 8) {  // eight 256-byte row gathers in flight per warp
+      float2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int32_t u = __shfl_sync(0xffffffffu, idx, j + q);
+        v[q] = ld_pair(C + (int64_t)u * kPprCols + 2 * lane);
+      }
+      ax += ((v[0].x + v[1].x) + (v[2].x + v[3].x)) + ((v[4].x + v[5].x) + (v[6].x + v[7].x));
+      ay += ((v[0].y + v[1].y) + (v[2].y + v[3].y)) + ((v[4].y + v[5].y) + (v[6].y + v[7].y));
     }
     for (; j < cnt; ++j) {
       const int32_t u = __shfl_sync(0xffffffffu, idx, j);

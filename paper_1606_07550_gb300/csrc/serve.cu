@@ -8,7 +8,9 @@
 //      num_seeds free places of a slot of its graph and storage type (a new
 //      slot if none has room) and an n x num_seeds result buffer, if the
 //      device budget allows; otherwise it waits (no overtaking);
-//   2. launch steps_per_tick steps over every slot with live columns, one
+//   2. launch a few steps over every slot with live columns (about
+//      edges_per_tick / m steps for a graph of m edges, at most
+//      steps_per_tick), one
 //      persistent launch per storage type (ppr_kernel in slot mode: new
 //      columns start at e_seed, finished ones freeze and are written to
 //      their result buffer by node id);
@@ -233,7 +235,10 @@ static void run_tick(gpr_server* S, const std::vector<Slot*>& live) {
     jobs[i].C0 = sl->C0;
     jobs[i].C1 = sl->C1;
     jobs[i].parity = sl->parity;
-    jobs[i].iters = S->cfg.steps_per_tick;
+    {
+      const int64_t m = std::max<int64_t>(S->pool[sl->graph]->m, 1);
+      jobs[i].iters = (int32_t)std::max<int64_t>(1, std::min<int64_t>(S->cfg.steps_per_tick, S->cfg.edges_per_tick / m));
+    }
     jobs[i].cols = S->d_cols + i * kPprCols;
     std::copy(sl->cols, sl->cols + kPprCols, cols.begin() + i * kPprCols);
   }
@@ -387,7 +392,8 @@ gpr_status serve_create(const gpr_graph* const* pool, int32_t num_graphs, const 
   S->pool.assign(pool, pool + num_graphs);
   S->cfg = *cfg;
   if (S->cfg.max_queue <= 0) S->cfg.max_queue = 65536;
-  if (S->cfg.steps_per_tick <= 0) S->cfg.steps_per_tick = 8;
+  if (S->cfg.steps_per_tick <= 0) S->cfg.steps_per_tick = 64;
+  if (S->cfg.edges_per_tick <= 0) S->cfg.edges_per_tick = (int64_t)1 << 24;
   std::vector<const gpr_graph*> uniq(S->pool);
   std::sort(uniq.begin(), uniq.end());
   uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
