@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) dedupe_kernel(
     const uint64_t* __restrict__ keys, int64_t m_raw, int b, int32_t n, int32_t* __restrict__ row_idx,
     int32_t* __restrict__ col_ptr, int32_t* __restrict__ outdeg, uint64_t* __restrict__ status,
     uint32_t* __restrict__ tile_ctr, int64_t* __restrict__ m_out, Gap* __restrict__ gaps,
-    uint32_t* __restrict__ ngaps, int* __restrict__ derr) {
+    uint32_t* __restrict__ ngaps, int* __restrict__ derr, int withhold_tile0) {
   __shared__ uint32_t s_wsum[kWarps];
   __shared__ uint64_t s_excl;
   __shared__ uint32_t s_tile;
@@ -439,7 +439,9 @@ __global__ void __launch_bounds__(kThreads) dedupe_kernel(
     for (int ww = 0; ww < kWarps; ++ww) tot += s_wsum[ww];
     uint64_t excl = 0;
     if (tile == 0) {
-      st_relaxed_u64(status, lb_word(1, kFlagInc, tot));
+      // withhold_tile0: fault-injection hook for tests; the first tile never
+      // publishes, so every later tile's bounded wait runs out
+      if (!withhold_tile0) st_relaxed_u64(status, lb_word(1, kFlagInc, tot));
     } else {
       st_relaxed_u64(status + tile, lb_word(1, kFlagAgg, tot));
       excl = lookback(status, tile, 1, 1, derr);
@@ -537,8 +539,10 @@ static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b,
   GPR_CUDA(cudaMemsetAsync(ctr, 0, 8, s));
   GPR_CUDA(cudaMemsetAsync(ngaps, 0, 8, s));
   GPR_CUDA(cudaMemsetAsync(m_dev, 0, 8, s));
+  const char* inj = getenv("GPR_INJECT_LOOKBACK_STALL");
+  const int withhold = (inj && atoi(inj) != 0 && tiles > 1) ? 1 : 0;
   dedupe_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(sorted, m_keys, b, n, row_idx, col_ptr, outdeg, status, ctr,
-                                                     m_dev, gaps, ngaps, derr);
+                                                     m_dev, gaps, ngaps, derr, withhold);
   GPR_CUDA(cudaGetLastError());
   count_launches(1);
   gap_fill_kernel<<<num_sms() * 2, kThreads, 0, s>>>(col_ptr, gaps, ngaps);
@@ -625,6 +629,9 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       count_launches(1);
       row_idx_full = (int32_t*)tmp.get((size_t)m_raw * 4);
       m = keys_to_csc(keys, alt, m_raw, b, n, hist, g->col_ptr, row_idx_full, g->outdeg, derr, tmp, s);
+      GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
+      GPR_CUDA(cudaStreamSynchronize(s));
+      if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_build: a device-side wait timed out"};
     } else {
       GPR_CUDA(cudaMemsetAsync(g->col_ptr, 0, ((size_t)n + 1) * 4, s));
       GPR_CUDA(cudaMemsetAsync(g->outdeg, 0, (size_t)n * 4, s));
