@@ -594,7 +594,7 @@ def run_serve(args, world, rank, local):
         "config": {"workload": "serving-pool256-poisson", "pool_graphs": len(specs),
                    "pool_raw_edges": sum(sp.m for sp in specs), "rate_req_per_s": args.serve_rate,
                    "warmup_s": warm, "window_s": window, "budget_bytes": budget,
-                   "steps_per_tick": "min(64, 2^24 / m)",
+                   "steps_per_tick": 8, "edges_per_part": 1 << 20,
                    "max_iters": 1000},
         "latency_ms": {"p50": pct(lat, 0.50), "p99": pct(lat, 0.99), "completed": len(lat),
                        "arrived_in_window": len(in_window), "unfinished_after_drain": unfinished},

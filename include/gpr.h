@@ -166,10 +166,10 @@ typedef struct gpr_server gpr_server;
 typedef struct {
   int64_t budget_bytes;    /* device memory for the pool + batch state + results */
   int32_t max_queue;       /* queued (not yet admitted) requests before GPR_EBUSY; <= 0: 65536 */
-  int32_t steps_per_tick;  /* at most this many steps per batch per launch; <= 0: 64 */
-  int64_t edges_per_tick;  /* a batch on a graph of m edges runs about edges_per_tick / m steps
-                              per launch (at least 1), so launches stay short whatever the
-                              graph sizes; <= 0: 2^24 */
+  int32_t steps_per_tick;  /* steps between two admission rounds; <= 0: 8 */
+  int64_t edges_per_part;  /* a batch's rows are split into parts of about this many edges,
+                              each part one unit of work per step, so large graphs spread
+                              over every SM; <= 0: 2^20 */
   int32_t fail_alloc_at;   /* test hook: the k-th batch allocation fails as if out of memory (0: off) */
 } gpr_server_config;
 

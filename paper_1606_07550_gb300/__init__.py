@@ -79,7 +79,7 @@ class PprJob(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("max_queue", ctypes.c_int32), ("steps_per_tick", ctypes.c_int32),
-                ("edges_per_tick", ctypes.c_int64), ("fail_alloc_at", ctypes.c_int32)]
+                ("edges_per_part", ctypes.c_int64), ("fail_alloc_at", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -275,10 +275,10 @@ class Server:
     of graphs (see serve_* in include/gpr.h)."""
 
     def __init__(self, pool, budget_bytes: int, max_queue: int = 0, steps_per_tick: int = 0,
-                 edges_per_tick: int = 0, fail_alloc_at: int = 0):
+                 edges_per_part: int = 0, fail_alloc_at: int = 0):
         self.pool = list(pool)
         arr = (_VP * len(self.pool))(*[g.handle for g in self.pool])
-        cfg = ServerConfig(budget_bytes, max_queue, steps_per_tick, edges_per_tick, fail_alloc_at)
+        cfg = ServerConfig(budget_bytes, max_queue, steps_per_tick, edges_per_part, fail_alloc_at)
         h = _VP()
         _check(lib().serve_create(arr, len(self.pool), ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h.value

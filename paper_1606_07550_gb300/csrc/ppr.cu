@@ -11,7 +11,8 @@
 // lane.  Rows longer than one warp's fair share are handled by the whole
 // block with a fixed-order combine.
 //
-// Each job runs on one thread-block cluster for all of its steps.  The
+// ppr_batch: each job runs on one thread-block cluster for all of its steps,
+// in a per-cluster workspace.  The
 // cluster's blocks split the rows by edge count; after each step they meet at
 // the hardware cluster barrier, then every block folds the per-column FP64
 // partials of all blocks (read through distributed shared memory) in rank
@@ -206,20 +207,12 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
     const int32_t* __restrict__ col_ptr = J->col_ptr;
     const int32_t* __restrict__ row_idx = J->row_idx;
     const float* __restrict__ inv_deg = J->inv_deg;
-    const bool own_state = J->X != nullptr;
-    float* X;
+    char* base = ws + cid * ws_stride;
+    float* X = (float*)base;
     T* Cb[2];
-    if (own_state) {
-      X = J->X;
-      Cb[0] = (T*)J->C0;
-      Cb[1] = (T*)J->C1;
-    } else {
-      char* base = ws + cid * ws_stride;
-      X = (float*)base;
-      Cb[0] = (T*)(base + (int64_t)J->n_cap * kPprCols * 4);
-      Cb[1] = Cb[0] + (int64_t)J->n_cap * kPprCols;
-    }
-    int parity = J->parity;
+    Cb[0] = (T*)(base + (int64_t)J->n_cap * kPprCols * 4);
+    Cb[1] = Cb[0] + (int64_t)J->n_cap * kPprCols;
+    int parity = 0;
 
     // this block's rows: split by edge count
     const int64_t m = col_ptr[n];
@@ -256,22 +249,12 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       s_maxit[tid] = cr.max_iters;
     }
     __syncthreads();
-    // fresh columns start at e_seed in X and in the current contribution buffer
+    // every column starts at e_seed in X and in the current contribution buffer
     {
       T* Cc = Cb[parity];
-      if (!own_state) {
-        for (int64_t i = (int64_t)r0 * kPprCols + tid; i < (int64_t)r1 * kPprCols; i += kPprThreads) {
-          X[i] = 0.f;
-          st_one(Cc + i, 0.f);
-        }
-      } else {
-        for (int k = 0; k < kPprCols; ++k) {
-          if (s_status[k] != kColFresh) continue;
-          for (int32_t p = r0 + tid; p < r1; p += kPprThreads) {
-            X[(int64_t)p * kPprCols + k] = 0.f;
-            st_one(Cc + (int64_t)p * kPprCols + k, 0.f);
-          }
-        }
+      for (int64_t i = (int64_t)r0 * kPprCols + tid; i < (int64_t)r1 * kPprCols; i += kPprThreads) {
+        X[i] = 0.f;
+        st_one(Cc + i, 0.f);
       }
       __syncthreads();
       if (tid < kPprCols && s_status[tid] == kColFresh) {
@@ -395,9 +378,206 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         cr->dangling = s_D[tid];
         cr->residual = s_res[tid];
       }
-      if (tid == 0) J->parity = parity;
     }
     cl.sync();  // the workspace and s_job are reused by the next job
+  }
+}
+
+// ---- step-major kernel (the server) ------------------------------------------
+//
+// One launch = one step of every (slot, part) item.  Launch sequence of a
+// tick with T steps: kStepInit (fresh columns start at e_seed; state st[0]),
+// kStepRun with step = 1..T (fold the previous step's part sums in part
+// order, decide stops, then pull), kStepFinish (fold step T, write the
+// records).  Run step s reads st[(s-1)&1] and psum[(s-1)&1] and writes
+// st[s&1] and psum[s&1]; every part of a slot computes the same decisions and
+// only part 0 writes them.  A finished column is written out, by node id,
+// by every part for its own rows, at the launch that detects it.
+
+template <typename T>
+__global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc* __restrict__ slots,
+                                                                 const StepItem* __restrict__ items, int32_t nitems,
+                                                                 int mode, int32_t step) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ float s_wpart[kPprWarps][3][kPprCols];
+  __shared__ float s_heavy[kPprWarps][kPprCols];
+  __shared__ int32_t s_seed[kPprCols], s_status[kPprCols], s_iters[kPprCols], s_newdone[kPprCols];
+  __shared__ float s_d[kPprCols];
+  __shared__ double s_D[kPprCols];
+  __shared__ uint32_t s_key[kPprCols];
+  const int cur = step & 1, prev = cur ^ 1;
+  for (int32_t ii = blockIdx.x; ii < nitems; ii += gridDim.x) {
+    const StepItem item = items[ii];
+    const SlotDesc* S = slots + item.slot;
+    const int32_t r0 = S->part_rows[item.part], r1 = S->part_rows[item.part + 1];
+    const float* __restrict__ inv_deg = S->inv_deg;
+    float* X = S->X;
+
+    // ---- column state for this launch
+    if (tid < kPprCols) {
+      const PprCol cr = S->rec[tid];
+      const int32_t seed_row = cr.status == kColEmpty ? -1 : S->old2new[cr.seed];
+      s_seed[tid] = seed_row;
+      s_d[tid] = cr.damping;
+      s_key[tid] = hash32((uint32_t)cr.seed * 0x85EBCA6Bu ^ __float_as_uint(cr.damping));
+      int32_t status, iters;
+      double D, res;
+      int newdone = 0;
+      if (mode == kStepInit) {
+        status = cr.status;
+        iters = cr.iters;
+        D = cr.dangling;
+        res = cr.residual;
+        if (status == kColFresh) {
+          status = kColRunning;
+          iters = 0;
+          res = 0.0;
+          D = inv_deg[seed_row] == 0.f ? 1.0 : 0.0;
+          if (iters >= cr.max_iters) {
+            status = kColDone;
+            newdone = 1;
+          }
+        }
+      } else {
+        const ColState cs = S->st[prev][tid];
+        status = cs.status;
+        iters = cs.iters;
+        D = cs.dangling;
+        res = cs.residual;
+        const bool fold = mode == kStepFinish || step > 1;
+        if (fold && status == kColRunning) {
+          double dsum = 0.0, rsum = 0.0;
+          const double* ps = S->psum[prev];
+          for (int32_t q = 0; q < S->nparts; ++q) {
+            dsum += ps[(3 * q + 1) * kPprCols + tid];
+            rsum += ps[(3 * q + 2) * kPprCols + tid];
+          }
+          D = dsum;
+          res = rsum;
+          iters += 1;
+          const double d = cr.damping;
+          if ((cr.tol > 0.f && (d / (1.0 - d)) * rsum <= (double)cr.tol) || iters >= cr.max_iters) {
+            status = kColDone;
+            newdone = 1;
+          }
+        }
+      }
+      s_status[tid] = status;
+      s_iters[tid] = iters;
+      s_D[tid] = D;
+      s_newdone[tid] = newdone;
+      if (item.part == 0) {
+        if (mode == kStepFinish) {
+          PprCol* w = S->rec + tid;
+          w->status = status;
+          w->iters = iters;
+          w->dangling = D;
+          w->residual = res;
+        } else {
+          S->st[mode == kStepInit ? 0 : cur][tid] = ColState{status, iters, D, res};
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- fresh columns start at e_seed (X and the current contributions)
+    if (mode == kStepInit) {
+      T* Cc = (T*)S->C[S->parity];
+      for (int k = 0; k < kPprCols; ++k) {
+        if (S->rec[k].status != kColFresh) continue;
+        const int32_t sr = s_seed[k];
+        for (int32_t p = r0 + tid; p < r1; p += kPprThreads) {
+          const float v = p == sr ? 1.f : 0.f;
+          X[(int64_t)p * kPprCols + k] = v;
+          st_one(Cc + (int64_t)p * kPprCols + k, v * inv_deg[p]);
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- columns finished by now: this part's rows go out by node id
+    for (int k = 0; k < kPprCols; ++k) {
+      if (!s_newdone[k]) continue;
+      const PprCol cr = S->rec[k];
+      for (int32_t p = r0 + tid; p < r1; p += kPprThreads)
+        cr.out[(int64_t)S->new2old[p] * cr.ldo] = X[(int64_t)p * kPprCols + k];
+    }
+
+    if (mode == kStepRun) {
+      const T* __restrict__ Cin = (const T*)S->C[(S->parity + step - 1) & 1];
+      T* __restrict__ Cout = (T*)S->C[(S->parity + step) & 1];
+      const int32_t* __restrict__ col_ptr = S->col_ptr;
+      const int32_t* __restrict__ row_idx = S->row_idx;
+      ColRegs c;
+      {
+        const int k0 = 2 * lane, k1 = 2 * lane + 1;
+        c.l0 = s_status[k0] == kColRunning;
+        c.l1 = s_status[k1] == kColRunning;
+        c.a0 = s_d[k0];
+        c.a1 = s_d[k1];
+        c.b0 = (float)((1.0 - (double)s_d[k0]) + (double)s_d[k0] * s_D[k0]);
+        c.b1 = (float)((1.0 - (double)s_d[k1]) + (double)s_d[k1] * s_D[k1]);
+        c.s0 = s_seed[k0];
+        c.s1 = s_seed[k1];
+        c.k0 = hash32(s_key[k0] ^ hash32((uint32_t)s_iters[k0] + 0x632BE5ABu));
+        c.k1 = hash32(s_key[k1] ^ hash32((uint32_t)s_iters[k1] + 0x632BE5ABu));
+      }
+      float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      const int32_t heavy_deg = S->heavy_deg;
+      for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
+        const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+        if (e1 - e0 > heavy_deg) continue;
+        const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
+        finish_ppr_row(p, y, c, X, Cout, inv_deg, lane, acc);
+      }
+      const int32_t h0 = lower_bound_i32(S->heavy_rows, S->n_heavy, r0);
+      const int32_t h1 = lower_bound_i32(S->heavy_rows, S->n_heavy, r1);
+      for (int32_t hi = h0; hi < h1; ++hi) {
+        const int32_t p = S->heavy_rows[hi];
+        const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+        const int32_t per = (((e1 - e0) + kPprWarps - 1) / kPprWarps + 31) & ~31;
+        const int32_t a = min(e1, e0 + warp * per), b = min(e1, a + per);
+        const float2 y = gather_row(row_idx, Cin, a, b, lane);
+        s_heavy[warp][2 * lane] = y.x;
+        s_heavy[warp][2 * lane + 1] = y.y;
+        __syncthreads();
+        if (warp == 0) {
+          float yx = 0.f, yy = 0.f;
+          for (int w = 0; w < kPprWarps; ++w) {
+            yx += s_heavy[w][2 * lane];
+            yy += s_heavy[w][2 * lane + 1];
+          }
+          finish_ppr_row(p, make_float2(yx, yy), c, X, Cout, inv_deg, lane, acc);
+        }
+        __syncthreads();
+      }
+      for (int v = 0; v < 3; ++v) {
+        s_wpart[warp][v][2 * lane] = acc[0][v];
+        s_wpart[warp][v][2 * lane + 1] = acc[1][v];
+      }
+      __syncthreads();
+      if (tid < 3 * kPprCols) {
+        const int v = tid / kPprCols, k = tid % kPprCols;
+        double sum = 0.0;
+        for (int w = 0; w < kPprWarps; ++w) sum += (double)s_wpart[w][v][k];
+        S->psum[cur][(3 * (int64_t)item.part + v) * kPprCols + k] = sum;
+      }
+    }
+    __syncthreads();  // shared state is reused by the next item
+  }
+}
+
+__global__ void part_bounds_kernel(const int32_t* __restrict__ col_ptr, int32_t n, int64_t m, int32_t nparts,
+                                   int32_t* __restrict__ part_rows) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= nparts; i += gridDim.x * blockDim.x) {
+    if (i == 0) {
+      part_rows[i] = 0;
+    } else if (i == nparts) {
+      part_rows[i] = n;
+    } else {
+      const int64_t target = (m * i + nparts - 1) / nparts;
+      part_rows[i] = min(n, lower_bound_i32(col_ptr, n + 1, target));
+    }
   }
 }
 
@@ -425,6 +605,35 @@ static int max_clusters_for(int cluster) {
     return 0;
   }
   return num;
+}
+
+
+void ppr_part_bounds(const int32_t* col_ptr, int32_t n, int64_t m, int32_t nparts, int32_t* part_rows,
+                     cudaStream_t s) {
+  part_bounds_kernel<<<std::max(1, (nparts + 256) / 256), 256, 0, s>>>(col_ptr, n, m, nparts, part_rows);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+template <typename T>
+static int step_grid(int32_t nitems) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ppr_step_kernel<T>, kPprThreads, 0);
+  return std::max(1, std::min(nitems, num_sms() * std::max(per_sm, 1)));
+}
+
+void ppr_step_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int32_t nitems, int mode, int32_t step,
+                     gpr_dtype dt, cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (dt == GPR_BF16)
+    ppr_step_kernel<__nv_bfloat16><<<step_grid<__nv_bfloat16>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev,
+                                                                                          nitems, mode, step);
+  else if (dt == GPR_FP16)
+    ppr_step_kernel<__half><<<step_grid<__half>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev, nitems, mode, step);
+  else
+    ppr_step_kernel<float><<<step_grid<float>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev, nitems, mode, step);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 
 int ppr_max_clusters(gpr_dtype dt) {

@@ -26,7 +26,8 @@ struct PprCol {
   int32_t pad;
 };
 
-// One job: a graph and 64 column slots.
+// One ppr_batch job: a graph and 64 column places; its state lives in the
+// workspace of the cluster that runs it.
 struct PprJob {
   const int32_t* col_ptr;  // relabelled CSC (execution layout)
   const int32_t* row_idx;
@@ -36,15 +37,50 @@ struct PprJob {
   int32_t n_heavy;
   int32_t heavy_deg;
   int32_t n;
-  int32_t n_cap;        // rows of the per-cluster workspace (batch mode)
-  int32_t iters;        // steps to run in this launch at most
-  float* X;             // n x 64 FP32 state, or null: use the cluster workspace
-  void* C0;             // n x 64 contributions (FP32 or BF16), double-buffered
-  void* C1;
-  int32_t parity;       // which C buffer holds the current contributions
-  int32_t pad;
+  int32_t n_cap;        // rows of the per-cluster workspace
+  int32_t iters;        // steps to run at most
   PprCol* cols;         // 64 records
 };
+
+// ---- step-major execution for the server --------------------------------
+// A slot's rows are split into parts of about equal edge count; one launch
+// runs one step of every (slot, part) item, so a large graph is spread over
+// every SM.  The per-column sums of a step are folded, in part order, at the
+// start of the next launch; column state is double-buffered by step parity.
+struct ColState {
+  int32_t status, iters;
+  double dangling, residual;
+};
+
+struct SlotDesc {
+  const int32_t* col_ptr;
+  const int32_t* row_idx;
+  const float* inv_deg;
+  const int32_t* old2new;
+  const int32_t* new2old;
+  const int32_t* heavy_rows;
+  int32_t n_heavy, heavy_deg;
+  int32_t n, nparts;
+  const int32_t* part_rows;  // nparts + 1 row boundaries
+  float* X;
+  void* C[2];
+  int32_t parity;            // C buffer holding the contributions at the start of the tick
+  int32_t pad;
+  PprCol* rec;               // 64 host-visible records
+  ColState* st[2];           // 64 each, by step parity
+  double* psum[2];           // nparts x 3 x 64 each, by step parity
+};
+
+struct StepItem {
+  int32_t slot, part;
+};
+
+enum : int { kStepInit = 0, kStepRun = 1, kStepFinish = 2 };
+
+void ppr_step_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int32_t nitems, int mode, int32_t step,
+                     gpr_dtype dt, cudaStream_t s);
+void ppr_part_bounds(const int32_t* col_ptr, int32_t n, int64_t m, int32_t nparts, int32_t* part_rows,
+                     cudaStream_t s);
 
 int ppr_max_clusters(gpr_dtype dt);
 int ppr_cluster_size();

@@ -8,12 +8,11 @@
 //      num_seeds free places of a slot of its graph and storage type (a new
 //      slot if none has room) and an n x num_seeds result buffer, if the
 //      device budget allows; otherwise it waits (no overtaking);
-//   2. launch a few steps over every slot with live columns (about
-//      edges_per_tick / m steps for a graph of m edges, at most
-//      steps_per_tick), one
-//      persistent launch per storage type (ppr_kernel in slot mode: new
-//      columns start at e_seed, finished ones freeze and are written to
-//      their result buffer by node id);
+//   2. run steps_per_tick steps of every slot with live columns: each slot's
+//      rows are split into parts of about edges_per_part edges and one
+//      launch runs one step of every (slot, part) on all SMs (ppr.cu,
+//      ppr_step_kernel: new columns start at e_seed, finished ones freeze
+//      and are written to their result buffer by node id);
 //   3. read back the column records, complete requests whose columns are
 //      all finished, free their places and slots that became empty.
 // A column's arithmetic does not depend on the other columns, so a result
@@ -42,8 +41,13 @@ struct Slot {
   void* C1 = nullptr;
   int32_t parity = 0;
   int64_t bytes = 0;
-  PprCol cols[kPprCols];
-  uint64_t owner[kPprCols];  // ticket holding each place (0: free)
+  int32_t nparts = 1;
+  int32_t* part_rows = nullptr;  // device, nparts + 1
+  PprCol* d_rec = nullptr;       // device, 64
+  ColState* d_st = nullptr;      // device, 2 x 64
+  double* d_psum = nullptr;      // device, 2 x nparts x 3 x 64
+  PprCol cols[kPprCols];         // host mirror of d_rec
+  uint64_t owner[kPprCols];      // ticket holding each place (0: free)
   int used = 0;
 };
 
@@ -86,44 +90,65 @@ struct gpr_server {
   std::thread th;
   int alloc_attempts = 0;
   gpr_server_stats st{};
-  // device staging for one launch
-  gpr::PprJob* d_jobs = nullptr;
-  gpr::PprCol* d_cols = nullptr;
-  int32_t* d_order = nullptr;
-  uint32_t* d_queue = nullptr;
-  int cap_jobs = 0;
+  // device staging for one tick
+  gpr::SlotDesc* d_desc = nullptr;
+  gpr::StepItem* d_items = nullptr;
+  int cap_desc = 0, cap_items = 0;
 };
 
 namespace gpr {
 
 static size_t elem_bytes(gpr_dtype dt) { return dt == GPR_FP32 ? 4 : 2; }
 
-static int64_t slot_bytes(const gpr_graph* g, gpr_dtype dt) {
-  return (int64_t)g->n * kPprCols * (4 + 2 * (int64_t)elem_bytes(dt));
+static int32_t parts_for(const gpr_server* S, const gpr_graph* g) {
+  const int64_t p = (g->m + S->cfg.edges_per_part - 1) / std::max<int64_t>(S->cfg.edges_per_part, 1);
+  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(p, 1024), std::max(g->n, 1)));
 }
 
-static void fill_job(PprJob& J, const gpr_graph* g) {
-  J = PprJob{};
-  J.col_ptr = g->col_ptr;
-  J.row_idx = g->row_idx;
-  J.inv_deg = g->plan.inv_deg;
-  J.old2new = g->plan.old2new;
-  J.n = g->n;
-  J.heavy_rows = g->plan.rows;
-  J.n_heavy = 0;
-  J.heavy_deg = INT_MAX;
+static int64_t slot_bytes(const gpr_server* S, const gpr_graph* g, gpr_dtype dt) {
+  const int64_t P = parts_for(S, g);
+  return (int64_t)g->n * kPprCols * (4 + 2 * (int64_t)elem_bytes(dt)) + (P + 1) * 4 +
+         kPprCols * (int64_t)(sizeof(PprCol) + 2 * sizeof(ColState)) + 2 * P * 3 * kPprCols * 8;
+}
+
+static void fill_desc(SlotDesc& D, const gpr_graph* g, const Slot* sl) {
+  D = SlotDesc{};
+  D.col_ptr = g->col_ptr;
+  D.row_idx = g->row_idx;
+  D.inv_deg = g->plan.inv_deg;
+  D.old2new = g->plan.old2new;
+  D.new2old = g->plan.new2old;
+  D.n = g->n;
+  D.heavy_rows = g->plan.rows;
+  D.n_heavy = 0;
+  D.heavy_deg = INT_MAX;
   for (int b = 0; b < g->plan.nbuckets; ++b)
     if (g->plan.bucket[b].lanes == 0) {
-      J.heavy_rows = g->plan.rows + g->plan.bucket[b].row_begin;
-      J.n_heavy = g->plan.bucket[b].row_end - g->plan.bucket[b].row_begin;
-      J.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : 0;
+      D.heavy_rows = g->plan.rows + g->plan.bucket[b].row_begin;
+      D.n_heavy = g->plan.bucket[b].row_end - g->plan.bucket[b].row_begin;
+      D.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : 0;
     }
+  D.nparts = sl->nparts;
+  D.part_rows = sl->part_rows;
+  D.X = sl->X;
+  D.C[0] = sl->C0;
+  D.C[1] = sl->C1;
+  D.parity = sl->parity;
+  D.rec = sl->d_rec;
+  D.st[0] = sl->d_st;
+  D.st[1] = sl->d_st + kPprCols;
+  D.psum[0] = sl->d_psum;
+  D.psum[1] = sl->d_psum + (int64_t)sl->nparts * 3 * kPprCols;
 }
 
 static void free_slot(gpr_server* S, Slot* sl) {
   dfree(sl->X, S->stream);
   dfree(sl->C0, S->stream);
   dfree(sl->C1, S->stream);
+  dfree(sl->part_rows, S->stream);
+  dfree(sl->d_rec, S->stream);
+  dfree(sl->d_st, S->stream);
+  dfree(sl->d_psum, S->stream);
   S->bytes_in_use -= sl->bytes;
   delete sl;
 }
@@ -138,7 +163,7 @@ static bool try_admit(gpr_server* S, Req& r) {
       target = sl;
       break;
     }
-  const int64_t need = (target ? 0 : slot_bytes(g, r.dt)) + (int64_t)g->n * k * 4;
+  const int64_t need = (target ? 0 : slot_bytes(S, g, r.dt)) + (int64_t)g->n * k * 4;
   if (S->bytes_in_use + need > S->cfg.budget_bytes) return false;
   try {
     if (!target) {
@@ -148,15 +173,25 @@ static bool try_admit(gpr_server* S, Req& r) {
       Slot* sl = new Slot();
       sl->graph = r.graph;
       sl->dt = r.dt;
-      sl->bytes = slot_bytes(g, r.dt);
+      sl->bytes = slot_bytes(S, g, r.dt);
+      sl->nparts = parts_for(S, g);
       try {
         sl->X = (float*)dalloc((size_t)g->n * kPprCols * 4, S->stream);
         sl->C0 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
         sl->C1 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
+        sl->part_rows = (int32_t*)dalloc(((size_t)sl->nparts + 1) * 4, S->stream);
+        sl->d_rec = (PprCol*)dalloc(kPprCols * sizeof(PprCol), S->stream);
+        sl->d_st = (ColState*)dalloc(2 * kPprCols * sizeof(ColState), S->stream);
+        sl->d_psum = (double*)dalloc((size_t)2 * sl->nparts * 3 * kPprCols * 8, S->stream);
+        ppr_part_bounds(g->col_ptr, g->n, g->m, sl->nparts, sl->part_rows, S->stream);
       } catch (...) {
         dfree(sl->X, S->stream);
         dfree(sl->C0, S->stream);
         dfree(sl->C1, S->stream);
+        dfree(sl->part_rows, S->stream);
+        dfree(sl->d_rec, S->stream);
+        dfree(sl->d_st, S->stream);
+        dfree(sl->d_psum, S->stream);
         delete sl;
         throw;
       }
@@ -171,6 +206,15 @@ static bool try_admit(gpr_server* S, Req& r) {
       target = sl;
     }
     r.result = (float*)dalloc((size_t)g->n * k * 4, S->stream);
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    r.state = kFailed;
+    r.status = GPR_ECUDA;
+    r.t_done = Clock::now();
+    ++S->st.failed;
+    S->finished.push_back(r.ticket);
+    S->cv_done.notify_all();
+    return true;
   } catch (const StatusFail& f) {
     r.state = kFailed;
     r.status = f.st;
@@ -204,69 +248,48 @@ static bool try_admit(gpr_server* S, Req& r) {
   return true;
 }
 
-static void ensure_staging(gpr_server* S, int jobs) {
-  if (jobs <= S->cap_jobs) return;
-  dfree(S->d_jobs, S->stream);
-  dfree(S->d_cols, S->stream);
-  dfree(S->d_order, S->stream);
-  S->d_jobs = nullptr;
-  S->d_cols = nullptr;
-  S->d_order = nullptr;
-  S->cap_jobs = 0;
-  const int cap = std::max(jobs, 2 * S->cap_jobs + 16);
-  S->d_jobs = (PprJob*)dalloc((size_t)cap * sizeof(PprJob), S->stream);
-  S->d_cols = (PprCol*)dalloc((size_t)cap * kPprCols * sizeof(PprCol), S->stream);
-  S->d_order = (int32_t*)dalloc((size_t)cap * 4, S->stream);
-  S->cap_jobs = cap;
+template <typename V>
+static V* grow(V* p, int& cap, int need, cudaStream_t s) {
+  if (need <= cap) return p;
+  dfree(p, s);
+  cap = std::max(need, 2 * cap + 16);
+  return (V*)dalloc((size_t)cap * sizeof(V), s);
 }
 
-// One launch per storage type over the slots with live columns; then the
-// column records come back.  Runs without the lock: only the scheduler
-// thread touches slots.
+// One tick: per storage type, kStepInit, steps_per_tick run launches and
+// kStepFinish over every (slot, part) of the slots with live columns, then
+// the records come back.  Runs without the lock: only the scheduler thread
+// touches slots.
 static void run_tick(gpr_server* S, const std::vector<Slot*>& live) {
-  ensure_staging(S, (int)live.size());
-  std::vector<PprJob> jobs(live.size());
-  std::vector<PprCol> cols(live.size() * kPprCols);
-  std::vector<int32_t> order(live.size());
+  std::vector<SlotDesc> desc(live.size());
   for (size_t i = 0; i < live.size(); ++i) {
     Slot* sl = live[i];
-    fill_job(jobs[i], S->pool[sl->graph]);
-    jobs[i].X = sl->X;
-    jobs[i].C0 = sl->C0;
-    jobs[i].C1 = sl->C1;
-    jobs[i].parity = sl->parity;
-    {
-      const int64_t m = std::max<int64_t>(S->pool[sl->graph]->m, 1);
-      jobs[i].iters = (int32_t)std::max<int64_t>(1, std::min<int64_t>(S->cfg.steps_per_tick, S->cfg.edges_per_tick / m));
-    }
-    jobs[i].cols = S->d_cols + i * kPprCols;
-    std::copy(sl->cols, sl->cols + kPprCols, cols.begin() + i * kPprCols);
+    fill_desc(desc[i], S->pool[sl->graph], sl);
+    GPR_CUDA(cudaMemcpyAsync(sl->d_rec, sl->cols, kPprCols * sizeof(PprCol), cudaMemcpyHostToDevice, S->stream));
   }
-  GPR_CUDA(cudaMemcpyAsync(S->d_jobs, jobs.data(), jobs.size() * sizeof(PprJob), cudaMemcpyHostToDevice, S->stream));
-  GPR_CUDA(cudaMemcpyAsync(S->d_cols, cols.data(), cols.size() * sizeof(PprCol), cudaMemcpyHostToDevice, S->stream));
+  S->d_desc = grow(S->d_desc, S->cap_desc, (int)desc.size(), S->stream);
+  GPR_CUDA(cudaMemcpyAsync(S->d_desc, desc.data(), desc.size() * sizeof(SlotDesc), cudaMemcpyHostToDevice, S->stream));
+  const int32_t T = S->cfg.steps_per_tick;
   for (gpr_dtype dt : {GPR_FP32, GPR_BF16, GPR_FP16}) {
-    int cnt = 0;
+    std::vector<StepItem> items;
     for (size_t i = 0; i < live.size(); ++i)
-      if (live[i]->dt == dt) order[cnt++] = (int32_t)i;
-    if (!cnt) continue;
-    // largest graphs first
-    std::stable_sort(order.begin(), order.begin() + cnt, [&](int32_t a, int32_t b) {
-      return S->pool[live[a]->graph]->m > S->pool[live[b]->graph]->m;
-    });
-    GPR_CUDA(cudaMemcpyAsync(S->d_order, order.data(), cnt * 4, cudaMemcpyHostToDevice, S->stream));
-    GPR_CUDA(cudaMemsetAsync(S->d_queue, 0, 16, S->stream));
-    const int clusters = std::max(1, std::min(ppr_max_clusters(dt), cnt));
-    ppr_launch(S->d_jobs, S->d_order, cnt, S->d_queue, nullptr, 0, clusters, dt, S->stream);
-    // the launch reads order/queue asynchronously: finish it before reusing them
+      if (live[i]->dt == dt)
+        for (int32_t q = 0; q < live[i]->nparts; ++q) items.push_back(StepItem{(int32_t)i, q});
+    if (items.empty()) continue;
+    S->d_items = grow(S->d_items, S->cap_items, (int)items.size(), S->stream);
+    GPR_CUDA(cudaMemcpyAsync(S->d_items, items.data(), items.size() * sizeof(StepItem), cudaMemcpyHostToDevice,
+                             S->stream));
+    const int32_t ni = (int32_t)items.size();
+    ppr_step_launch(S->d_desc, S->d_items, ni, kStepInit, 0, dt, S->stream);
+    for (int32_t st = 1; st <= T; ++st) ppr_step_launch(S->d_desc, S->d_items, ni, kStepRun, st, dt, S->stream);
+    ppr_step_launch(S->d_desc, S->d_items, ni, kStepFinish, T + 1, dt, S->stream);
+    // the host copy of `items` must outlive the copy above
     GPR_CUDA(cudaStreamSynchronize(S->stream));
   }
-  GPR_CUDA(cudaMemcpyAsync(cols.data(), S->d_cols, cols.size() * sizeof(PprCol), cudaMemcpyDeviceToHost, S->stream));
-  GPR_CUDA(cudaMemcpyAsync(jobs.data(), S->d_jobs, jobs.size() * sizeof(PprJob), cudaMemcpyDeviceToHost, S->stream));
+  for (Slot* sl : live)
+    GPR_CUDA(cudaMemcpyAsync(sl->cols, sl->d_rec, kPprCols * sizeof(PprCol), cudaMemcpyDeviceToHost, S->stream));
   GPR_CUDA(cudaStreamSynchronize(S->stream));
-  for (size_t i = 0; i < live.size(); ++i) {
-    std::copy(cols.begin() + i * kPprCols, cols.begin() + (i + 1) * kPprCols, live[i]->cols);
-    live[i]->parity = jobs[i].parity;
-  }
+  for (Slot* sl : live) sl->parity = (sl->parity + T) & 1;
 }
 
 static void fail_running(gpr_server* S, gpr_status st) {
@@ -392,8 +415,8 @@ gpr_status serve_create(const gpr_graph* const* pool, int32_t num_graphs, const 
   S->pool.assign(pool, pool + num_graphs);
   S->cfg = *cfg;
   if (S->cfg.max_queue <= 0) S->cfg.max_queue = 65536;
-  if (S->cfg.steps_per_tick <= 0) S->cfg.steps_per_tick = 64;
-  if (S->cfg.edges_per_tick <= 0) S->cfg.edges_per_tick = (int64_t)1 << 24;
+  if (S->cfg.steps_per_tick <= 0) S->cfg.steps_per_tick = 8;
+  if (S->cfg.edges_per_part <= 0) S->cfg.edges_per_part = (int64_t)1 << 20;
   std::vector<const gpr_graph*> uniq(S->pool);
   std::sort(uniq.begin(), uniq.end());
   uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
@@ -406,7 +429,6 @@ gpr_status serve_create(const gpr_graph* const* pool, int32_t num_graphs, const 
   }
   try {
     GPR_CUDA(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
-    S->d_queue = (uint32_t*)dalloc(16, S->stream);
   } catch (const StatusFail& f) {
     if (S->stream) cudaStreamDestroy(S->stream);
     delete S;
@@ -449,7 +471,7 @@ gpr_status serve_submit(gpr_server* S, const gpr_request* r, uint64_t* ticket) {
     set_error("serve_submit: damping, tol, max_iters or dtype out of range");
     return GPR_EINVAL;
   }
-  const int64_t alone = S->pool_bytes + slot_bytes(g, r->dt) + (int64_t)g->n * r->num_seeds * 4;
+  const int64_t alone = S->pool_bytes + slot_bytes(S, g, r->dt) + (int64_t)g->n * r->num_seeds * 4;
   std::lock_guard<std::mutex> lk(S->mu);
   ++S->st.submitted;
   if (alone > S->cfg.budget_bytes) {
@@ -610,10 +632,8 @@ gpr_status serve_destroy(gpr_server* S) {
   S->slots.clear();
   for (auto& kv : S->reqs)
     if (kv.second.result) dfree(kv.second.result, S->stream);
-  dfree(S->d_jobs, S->stream);
-  dfree(S->d_cols, S->stream);
-  dfree(S->d_order, S->stream);
-  dfree(S->d_queue, S->stream);
+  dfree(S->d_desc, S->stream);
+  dfree(S->d_items, S->stream);
   cudaError_t e = cudaStreamSynchronize(S->stream);
   cudaStreamDestroy(S->stream);
   delete S;
