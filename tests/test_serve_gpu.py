@@ -98,7 +98,7 @@ def test_budget_admission_and_rejections(torch, pool):
     slot = g2.n * 64 * 12
     res = g2.n * 64 * 4
     # room for one 64-seed request on graph 2 at a time
-    srv = gpr.Server(graphs, budget_bytes=pool_bytes + slot + res + 1024, max_queue=1)
+    srv = gpr.Server(graphs, budget_bytes=pool_bytes + slot + res + (1 << 20), max_queue=1)  # + small per-slot step state
     with pytest.raises(gpr.GprError) as ei:  # the pool alone exceeds the budget
         gpr.Server(graphs, budget_bytes=pool_bytes - 1)
     assert ei.value.status == gpr.ENOMEM
