@@ -62,12 +62,16 @@ def workload(name):
     return {"rmat25": workloads.RMAT_25, "rmat-lj": workloads.RMAT_LJ, "er10k": workloads.ER_10K}[name]
 
 
+# sources of the kernels a recorded DRAM-traffic figure depends on (the
+# graph layout and the PageRank step)
+TRAFFIC_SOURCES = ("build.cu", "plan.cu", "pagerank.cu", "gpr_internal.cuh")
+
+
 def src_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1606_07550_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
