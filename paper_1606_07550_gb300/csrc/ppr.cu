@@ -112,22 +112,17 @@ __device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx
   for (int32_t e = e0; e < e1; e += 32) {
     const int32_t idx = (e + lane < e1) ? __ldcs(row_idx + e + lane) : 0;
     const int cnt = min(32, e1 - e);
-    int j = 0;
-    for (; j + 8 <= cnt; j += 8) {  // eight 256-byte row gathers in flight per warp
+    for (int j = 0; j < cnt; j += 8) {
+      // eight 256-byte row gathers in flight per warp; the tail of a group
+      // is masked (warp-uniform), never gathered one load at a time
       float2 v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int32_t u = __shfl_sync(0xffffffffu, idx, j + q);
-        v[q] = ld_pair(C + (int64_t)u * kPprCols + 2 * lane);
+        const int32_t u = __shfl_sync(0xffffffffu, idx, (j + q) & 31);
+        v[q] = (j + q < cnt) ? ld_pair(C + (int64_t)u * kPprCols + 2 * lane) : make_float2(0.f, 0.f);
       }
       ax += ((v[0].x + v[1].x) + (v[2].x + v[3].x)) + ((v[4].x + v[5].x) + (v[6].x + v[7].x));
       ay += ((v[0].y + v[1].y) + (v[2].y + v[3].y)) + ((v[4].y + v[5].y) + (v[6].y + v[7].y));
-    }
-    for (; j < cnt; ++j) {
-      const int32_t u = __shfl_sync(0xffffffffu, idx, j);
-      const float2 v = ld_pair(C + (int64_t)u * kPprCols + 2 * lane);
-      ax += v.x;
-      ay += v.y;
     }
   }
   return make_float2(ax, ay);
@@ -141,13 +136,17 @@ struct ColRegs {
   uint32_t k0, k1;   // rounding-hash keys of (column, step)
 };
 
+// The row's previous state: loaded before the gathers so its latency overlaps them.
+__device__ __forceinline__ float2 ld_state(const float* X, int32_t p, int lane) {
+  return *reinterpret_cast<const float2*>(X + (int64_t)p * kPprCols + 2 * lane);
+}
+
 template <typename T>
-__device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, const ColRegs& c, float* __restrict__ X,
-                                               T* __restrict__ Cout, const float* __restrict__ inv_deg, int lane,
-                                               float (&acc)[2][3]) {
+__device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, float2 xo, const ColRegs& c,
+                                               float* __restrict__ X, T* __restrict__ Cout,
+                                               const float* __restrict__ inv_deg, int lane, float (&acc)[2][3]) {
   const float inv = inv_deg[p];
   float* xp = X + (int64_t)p * kPprCols + 2 * lane;
-  const float2 xo = *reinterpret_cast<const float2*>(xp);
   const float n0 = c.l0 ? fmaf(c.a0, y.x, p == c.s0 ? c.b0 : 0.f) : xo.x;
   const float n1 = c.l1 ? fmaf(c.a1, y.y, p == c.s1 ? c.b1 : 0.f) : xo.y;
   *reinterpret_cast<float2*>(xp) = make_float2(n0, n1);
@@ -299,8 +298,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
+        const float2 xo = ld_state(X, p, lane);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
-        finish_ppr_row(p, y, c, X, Cout, inv_deg, lane, acc);
+        finish_ppr_row(p, y, xo, c, X, Cout, inv_deg, lane, acc);
       }
       // long rows: the whole block, fixed-order combine
       for (int32_t hi = h0; hi < h1; ++hi) {
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
             yx += s_heavy[w][2 * lane];
             yy += s_heavy[w][2 * lane + 1];
           }
-          finish_ppr_row(p, make_float2(yx, yy), c, X, Cout, inv_deg, lane, acc);
+          finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), c, X, Cout, inv_deg, lane, acc);
         }
         __syncthreads();
       }
@@ -527,8 +527,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
+        const float2 xo = ld_state(X, p, lane);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
-        finish_ppr_row(p, y, c, X, Cout, inv_deg, lane, acc);
+        finish_ppr_row(p, y, xo, c, X, Cout, inv_deg, lane, acc);
       }
       const int32_t h0 = lower_bound_i32(S->heavy_rows, S->n_heavy, r0);
       const int32_t h1 = lower_bound_i32(S->heavy_rows, S->n_heavy, r1);
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
             yx += s_heavy[w][2 * lane];
             yy += s_heavy[w][2 * lane + 1];
           }
-          finish_ppr_row(p, make_float2(yx, yy), c, X, Cout, inv_deg, lane, acc);
+          finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), c, X, Cout, inv_deg, lane, acc);
         }
         __syncthreads();
       }

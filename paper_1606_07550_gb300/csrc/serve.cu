@@ -7,7 +7,9 @@
 //   1. admit queued requests first come, first served: a request takes
 //      num_seeds free places of a slot of its graph and storage type (a new
 //      slot if none has room) and an n x num_seeds result buffer, if the
-//      device budget allows; otherwise it waits (no overtaking);
+//      device budget allows; otherwise it waits.  While the head waits (at
+//      most kOvertakeMs), later requests may take free places of running
+//      slots, which needs no new slot;
 //   2. run steps_per_tick steps of every slot with live columns: each slot's
 //      rows are split into parts of about edges_per_part edges and one
 //      launch runs one step of every (slot, part) on all SMs (ppr.cu,
@@ -32,6 +34,11 @@
 namespace gpr {
 
 using Clock = std::chrono::steady_clock;
+
+// Later requests may fill free places of running slots while the queue head
+// has waited less than this; they are looked for among this many queued ones.
+constexpr int kOvertakeMs = 2000;
+constexpr int kOvertakeScan = 4096;
 
 struct Slot {
   int graph = -1;
@@ -153,8 +160,9 @@ static void free_slot(gpr_server* S, Slot* sl) {
   delete sl;
 }
 
-// Place a queued request (lock held).  Returns false if it must wait.
-static bool try_admit(gpr_server* S, Req& r) {
+// Place a queued request (lock held).  Returns false if it must wait.  With
+// existing_only, only free places of an existing slot are considered.
+static bool try_admit(gpr_server* S, Req& r, bool existing_only = false) {
   const gpr_graph* g = S->pool[r.graph];
   const int k = (int)r.seeds.size();
   Slot* target = nullptr;
@@ -163,6 +171,7 @@ static bool try_admit(gpr_server* S, Req& r) {
       target = sl;
       break;
     }
+  if (existing_only && !target) return false;
   const int64_t need = (target ? 0 : slot_bytes(S, g, r.dt)) + (int64_t)g->n * k * 4;
   if (S->bytes_in_use + need > S->cfg.budget_bytes) return false;
   try {
@@ -325,6 +334,25 @@ static void scheduler(gpr_server* S) {
       }
       if (!try_admit(S, it->second)) break;
       S->queue.pop_front();
+    }
+    // 1b. while the head waits for memory, later requests may take free
+    // places of running slots of their graph (they need no new slot, only a
+    // result buffer); bounded so the head cannot starve
+    if (!S->queue.empty()) {
+      auto head = S->reqs.find(S->queue.front());
+      const bool head_fresh =
+          head != S->reqs.end() && Clock::now() - head->second.t_submit < std::chrono::milliseconds(kOvertakeMs);
+      if (head_fresh) {
+        int scanned = 0;
+        for (auto q = S->queue.begin() + 1; q != S->queue.end() && scanned < kOvertakeScan; ++scanned) {
+          auto it = S->reqs.find(*q);
+          if (it != S->reqs.end() && try_admit(S, it->second, /*existing_only=*/true)) {
+            q = S->queue.erase(q);
+          } else {
+            ++q;
+          }
+        }
+      }
     }
     std::vector<Slot*> live;
     for (Slot* sl : S->slots)
