@@ -175,6 +175,30 @@ __device__ __forceinline__ int32_t lower_bound_i32(const int32_t* a, int32_t n, 
   return lo;
 }
 
+// Rows [r0, r1) split into kPprWarps contiguous ranges of about equal
+// (edges + rows): warp w takes [first, last).  Deterministic, and balanced so
+// that no warp holds the block at its per-step barriers.
+__device__ __forceinline__ void warp_rows(const int32_t* __restrict__ col_ptr, int32_t r0, int32_t r1, int w,
+                                          int32_t& first, int32_t& last) {
+  const int64_t k0 = (int64_t)col_ptr[r0] + r0, k1 = (int64_t)col_ptr[r1] + r1;
+  auto at = [&](int ww) -> int32_t {
+    if (ww <= 0) return r0;
+    if (ww >= kPprWarps) return r1;
+    const int64_t target = k0 + (k1 - k0) * ww / kPprWarps;
+    int32_t lo = r0, hi = r1;  // first p in [r0, r1] with col_ptr[p] + p >= target
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo) / 2;
+      if ((int64_t)col_ptr[mid] + mid < target)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    return lo;
+  };
+  first = at(w);
+  last = at(w + 1);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict__ jobs,
                                                             const int32_t* __restrict__ order, int32_t njobs,
@@ -225,6 +249,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
     const int32_t h0 = lower_bound_i32(J->heavy_rows, J->n_heavy, r0);
     const int32_t h1 = lower_bound_i32(J->heavy_rows, J->n_heavy, r1);
     const int32_t heavy_deg = J->heavy_deg;
+    int32_t wr0, wr1;
+    warp_rows(col_ptr, r0, r1, warp, wr0, wr1);
 
     // column records
     if (tid < kPprCols) {
@@ -294,8 +320,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         c.k1 = hash32(s_key[k1] ^ hash32((uint32_t)s_iters[k1] + 0x632BE5ABu));
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-      // light rows: one warp per row, round-robin
-      for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
+      // light rows: one warp per row, each warp over its balanced range
+      for (int32_t p = wr0; p < wr1; ++p) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
         const float2 xo = ld_state(X, p, lane);
@@ -524,7 +550,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       const int32_t heavy_deg = S->heavy_deg;
-      for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
+      int32_t wr0, wr1;
+      warp_rows(col_ptr, r0, r1, warp, wr0, wr1);
+      for (int32_t p = wr0; p < wr1; ++p) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
         const float2 xo = ld_state(X, p, lane);
@@ -584,7 +612,7 @@ __global__ void part_bounds_kernel(const int32_t* __restrict__ col_ptr, int32_t 
 
 // ---- host side ----------------------------------------------------------------
 
-static int g_cluster_size = 8;
+static int g_cluster_size = 4;
 
 int ppr_cluster_size() { return g_cluster_size; }
 
