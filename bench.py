@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--pool", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--spmv", choices=["auto", "pull", "blocked"], default="auto",
+                    help="schedule of the PageRank step (auto: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-scale", type=int, default=19)
     return ap.parse_args()
@@ -64,7 +66,7 @@ def workload(name):
 
 # sources of the kernels a recorded DRAM-traffic figure depends on (the
 # graph layout and the PageRank step)
-TRAFFIC_SOURCES = ("build.cu", "plan.cu", "pagerank.cu", "gpr_internal.cuh")
+TRAFFIC_SOURCES = ("build.cu", "plan.cu", "pagerank.cu", "blocked.cu", "pr_step.cuh", "gpr_internal.cuh")
 
 
 def src_hash():
@@ -272,15 +274,19 @@ def run_gpr(args, world, rank, local):
     out = torch.empty(spec.n, dtype=torch.float32, device="cuda")
     L = gpr.lib()
 
+    stats = []
+
     def step(ev=None):
         if ev:
             ev[0].record(stream)
         g = gpr.graph_build(src, dst, spec.n, stream=stream)
         if ev:
             ev[1].record(stream)
-        gpr.pagerank(g, out, damping=DAMPING, iters=iters, dtype=gpr.FP32, stream=stream)
+        st = gpr.pagerank(g, out, damping=DAMPING, iters=iters, dtype=gpr.FP32, stream=stream, stats=True,
+                          spmv=args.spmv)
         if ev:
             ev[2].record(stream)
+            stats.append(st)
         return g
 
     g = None
@@ -315,9 +321,15 @@ def run_gpr(args, world, rank, local):
     value = edges_all * iters / (t_step_max * 1e-3) / 1e9
     pr_gteps = m * iters / (t_iter * 1e-3) / 1e9
 
-    # roofline of the PageRank iteration: modelled bytes 8m + 12n + 4 per step
+    # roofline of the PageRank iteration: modelled bytes 8m + 12n + 4 per
+    # step over the device time of the iteration loop alone (the library's
+    # CUDA events around its graph launch), without the per-graph setup
+    # (workspace, blocked edge layout, graph capture) that t_iter includes
+    t_loop = sum(st.t_iter_ms for st in stats) / len(stats)
+    t_setup = sum(st.t_setup_ms for st in stats) / len(stats)
+    schedule = {gpr.SPMV_PULL: "pull", gpr.SPMV_BLOCKED: "blocked"}.get(stats[-1].schedule, "?")
     bytes_per_iter = 8 * m + 12 * n + 4
-    achieved = bytes_per_iter * iters / (t_iter * 1e-3) / 1e9
+    achieved = bytes_per_iter * iters / (t_loop * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
     tr = recorded_traffic(spec.name)
 
@@ -333,14 +345,14 @@ def run_gpr(args, world, rank, local):
         del src, dst
         torch.cuda.empty_cache()
         g = gpr.graph_build(hs, hd, n, stream=stream)
-        gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream)
+        gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream, spmv=args.spmv)
         g.free()
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             g = gpr.graph_build(hs, hd, n, stream=stream)
-            gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream)
+            gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream, spmv=args.spmv)
             g.free()
         torch.cuda.synchronize()
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
@@ -363,12 +375,16 @@ def run_gpr(args, world, rank, local):
             "parallelism": f"replicas x{world}",
         },
         "build_ms": t_build, "iterate_ms": t_iter, "pagerank_gteps": pr_gteps,
+        "schedule": schedule, "iteration_loop_ms": t_loop, "pagerank_setup_host_ms": t_setup,
+        "loop_gteps": m * iters / (t_loop * 1e-3) / 1e9,
         "build_edges_per_s": spec.m / (t_build * 1e-3),
         "roofline": {
-            "kernel": "PageRank iteration (bucketed pull SpMV + fused step + fold)",
+            "kernel": ("PageRank iteration loop (bucketed pull SpMV + fused step + fold)" if schedule == "pull"
+                       else "PageRank iteration loop (blocked expand + accumulate + fused step + fold)"),
+            "timed": "CUDA events around the iteration graph launch, per call, averaged over the timed steps",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": peak_kind, "bytes_model": "8m + 12n + 4 per iteration",
-            "traffic": (tr["dram_bytes_per_iter"] if tr else None),
+            "traffic": (tr["dram_bytes_per_iter"] if tr and tr.get("schedule", "pull") == schedule else None),
         },
         "clocks": clk.summary(),
         "gpu_launches": launches,

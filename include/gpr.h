@@ -55,6 +55,9 @@ typedef enum { GPR_FP32 = 0, GPR_BF16 = 1, GPR_FP16 = 2 } gpr_dtype;
 /* Pointer-space flags */
 #define GPR_PTR_DEVICE 0 /* arrays are device (or managed) memory */
 #define GPR_PTR_HOST 1   /* arrays are host memory; the library copies them */
+/* Schedule of the PageRank step (pagerank only; neither: the library's choice) */
+#define GPR_SPMV_PULL 0x10    /* one gather per edge, rows by in-degree bucket */
+#define GPR_SPMV_BLOCKED 0x20 /* two streaming phases over a bin-major edge copy */
 
 /* A directed simple graph resident in device memory: the CSC (in-adjacency,
  * sources ascending within each destination), out-degrees, and an execution
@@ -76,6 +79,10 @@ typedef struct {
   double residual_l1; /* ||x_k - x_{k-1}||_1 of the last step, FP64 sum of FP32 terms */
   double mass;        /* sum of x_k, FP64 */
   double dangling;    /* dangling mass of x_k, FP64 */
+  double t_setup_ms;  /* host time this call spent making the workspace, the blocked edge
+                         layout and the CUDA graph (0 when all were reused) */
+  double t_iter_ms;   /* device time of the iteration loop (CUDA events on `stream`) */
+  int32_t schedule;   /* the step's schedule: GPR_SPMV_PULL or GPR_SPMV_BLOCKED */
 } gpr_stats;
 
 /* ---- graph construction ------------------------------------------------

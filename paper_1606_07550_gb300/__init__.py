@@ -29,6 +29,8 @@ _NAMES = ["GPR_OK", "GPR_EINVAL", "GPR_ENOMEM", "GPR_ECUDA", "GPR_ETIMEOUT", "GP
           "GPR_ENOTFOUND"]
 FP32, BF16, FP16 = 0, 1, 2
 PTR_DEVICE, PTR_HOST = 0, 1
+SPMV_PULL, SPMV_BLOCKED = 0x10, 0x20
+_SPMV = {"auto": 0, "pull": SPMV_PULL, "blocked": SPMV_BLOCKED}
 
 
 def sources():
@@ -101,7 +103,8 @@ class ServerStats(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
-                ("dangling", ctypes.c_double)]
+                ("dangling", ctypes.c_double), ("t_setup_ms", ctypes.c_double), ("t_iter_ms", ctypes.c_double),
+                ("schedule", ctypes.c_int32)]
 
 
 _lib = None
@@ -233,12 +236,14 @@ def graph_build(src, dst, n: int, stream=None) -> Graph:
 
 
 def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int = FP32, stream=None,
-             stats: bool = False):
+             stats: bool = False, spmv: str = "auto"):
     """Writes PageRank (n floats, by node id) into `out` (a CUDA tensor, or a
-    host array / CPU tensor).  Returns a Stats if stats=True."""
+    host array / CPU tensor).  Returns a Stats if stats=True.  spmv picks the
+    step's schedule: "pull", "blocked", or "auto" (the library's choice)."""
     po, host = _ptr_and_flag(out)
     st = Stats() if stats else None
-    _check(lib().pagerank(g.handle, damping, iters, dtype, PTR_HOST if host else PTR_DEVICE, po,
+    flags = (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv]
+    _check(lib().pagerank(g.handle, damping, iters, dtype, flags, po,
                           ctypes.byref(st) if st is not None else None, _stream_ptr(stream)))
     return st
 

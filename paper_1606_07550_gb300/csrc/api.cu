@@ -130,8 +130,9 @@ gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype
     set_error("pagerank: unknown dtype %d", (int)dt);
     return GPR_EINVAL;
   }
-  if (flags & ~GPR_PTR_HOST) {
-    set_error("pagerank: unknown flags 0x%x", flags);
+  if ((flags & ~(GPR_PTR_HOST | GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) ||
+      (flags & (GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) == (GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) {
+    set_error("pagerank: unknown or conflicting flags 0x%x", flags);
     return GPR_EINVAL;
   }
   return run_pagerank(const_cast<gpr_graph*>(g), damping, iters, dt, flags, x_out, st, (cudaStream_t)stream);

@@ -1,0 +1,665 @@
+// Blocked schedule of the PageRank step (section 4 Table "snap_methods"):
+// the same step as the pull kernels of pagerank.cu, with the per-edge random
+// gather c[u] replaced by two streaming phases.
+//
+// Sources are cut into blocks of 2^sb_bits relabelled ids and rows
+// (destinations) into bins of 2^w_bits.  The edges are stored once in
+// bin-major order: bin b, then source block s, then (row, source) as in the
+// CSC; the edges of one (b, s) pair form segment (b, s).  Per step:
+//   expand      for each source block s, c[block s] is copied into shared
+//               memory and every edge of its segments gets vals[e] = c[u],
+//               reading 16-bit local source ids: a read stream and a write
+//               stream, with the random reads served by shared memory;
+//   accumulate  for each bin, vals and the 16-bit local rows of its edges are
+//               streamed and added into one accumulator per row in shared
+//               memory; the bin's rows are then finished (x', c', partial
+//               sums) exactly as in the pull schedule.
+// Sums are exact integers.  With a unit of 2^-U (U = min(60, 28 +
+// ceil(log2 n))), contribution c is the integer q = floor(c * 2^U), and each
+// row's accumulator holds the exact 64-bit sum of its q, so y[v] does not
+// depend on the order of the additions and runs are bitwise reproducible
+// however units are scheduled.  The expand phase stores a 32-bit code per
+// edge: q itself when q < 2^31 (c < 2^(31-U), about 8 / n: nearly every
+// contribution), else the bits of c with the top bit set, converted again
+// where it is added.  Truncation costs less than 2^-U per edge (at most
+// m * 2^-U in L1, 1.2e-7 for 2^25 nodes and 2^30 edges); y[v] is rounded
+// to the nearest float.
+//
+// Streamed bytes per edge: 2 (source id) + 4 (code written) in expand,
+// 4 (code) + 2 (row id) in accumulate: 12, for FP32 and BF16 storage of c
+// alike (c itself is read once per unit).
+// Long rows need no special case: runs of one row are summed in registers
+// before they reach shared memory (a warp step inside one row is added
+// once), and a bin with many edges is cut into units whose sums meet in a
+// global accumulator.
+#include <algorithm>
+#include <vector>
+
+#include "blocked.cuh"
+
+namespace gpr {
+
+constexpr int kBkThreads = 1024;
+constexpr int kMaxUnitSegs = 1024;  // segments of one expand unit (one per thread in the prefix scan)
+constexpr int kChunk = 256;         // edges per warp step: 8 consecutive edges per lane
+static_assert(kBkThreads == kMaxUnitSegs, "the segment scan gives one segment to each thread");
+
+// floor(v * 2^U) from the bits of v (v >= 0, v * 2^U < 2^63), integer
+// operations only (a float-to-64-bit conversion instruction would run on the
+// FP64 pipe, which GB300 keeps slow).
+__device__ __forceinline__ uint64_t fixed_of(float v, int U) {
+  const uint32_t b = __float_as_uint(v);
+  const int e = (int)(b >> 23);
+  const int sh = e - 150 + U;  // v * 2^U = m * 2^sh
+  const uint64_t m = (b & 0x7FFFFFu) | 0x800000u;
+  if (e == 0 || sh < -24) return 0ull;  // zero, subnormal, or below one unit
+  return sh >= 0 ? m << sh : m >> -sh;
+}
+
+// The 32-bit code of contribution c, and the integer value of a code.
+__device__ __forceinline__ uint32_t code_of(float c, int U) {
+  const uint64_t q = fixed_of(c, U);
+  return q < 0x80000000ull ? (uint32_t)q : 0x80000000u | __float_as_uint(c);
+}
+__device__ __forceinline__ uint64_t value_of(uint32_t w, int U) {
+  return (w >> 31) ? fixed_of(__uint_as_float(w & 0x7FFFFFFFu), U) : (uint64_t)w;
+}
+
+// a * 2^-U rounded to the nearest float (ties to even), integer operations only.
+__device__ __forceinline__ float from_fixed(unsigned long long a, int U) {
+  if (a == 0ull) return 0.f;
+  const int msb = 63 - __clzll((long long)a);
+  uint64_t m;
+  int ex = msb;
+  if (msb <= 23) {
+    m = a << (23 - msb);
+  } else {
+    const int sh = msb - 23;
+    m = a >> sh;
+    const uint64_t rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m >> 24) {  // rounded up to the next power of two
+      m >>= 1;
+      ++ex;
+    }
+  }
+  return __uint_as_float((uint32_t)(ex - U + 127) << 23 | ((uint32_t)m & 0x7FFFFFu));
+}
+
+// Exact 64-bit addition into an accumulator held as two 32-bit words in
+// shared memory, with 32-bit atomics: the low word takes the low half, and
+// the high word the high half plus the carry out of the low word, seen in
+// the value the low atomic returns.  Whatever the order of the additions,
+// the number of carries is floor(sum of low halves / 2^32), so hi:lo ends
+// as the exact sum.  The high atomic is skipped when it would add 0 (every
+// code below 2^31 without a carry).
+__device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int32_t d, uint32_t ql, uint32_t qh) {
+  const uint32_t old = atomicAdd(lo + d, ql);
+  const uint32_t up = qh + (old + ql < old ? 1u : 0u);
+  if (up) atomicAdd(hi + d, up);
+}
+
+// ---- layout construction --------------------------------------------------
+
+// key = row-in-bin | source-in-block | (b * S + s), one per CSC edge, in CSC
+// order.  Warp per row.
+__global__ void bk_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
+                               int sb_bits, int w_bits, int kbits, int32_t S, uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t sb_mask = (1u << sb_bits) - 1;
+  for (int64_t p = warp; p < n; p += nwarps) {
+    const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+    const uint64_t b = (uint64_t)(p >> w_bits);
+    const uint64_t hi = (uint64_t)(p & ((1 << w_bits) - 1)) << (sb_bits + kbits);
+    for (int32_t e = e0 + lane; e < e1; e += 32) {
+      const uint32_t u = (uint32_t)row_idx[e];
+      keys[e] = hi | ((uint64_t)(u & sb_mask) << kbits) | (b * (uint64_t)S + (u >> sb_bits));
+    }
+  }
+}
+
+// From the keys sorted (stably) on their low kbits bits: the local ids of
+// every edge in bin-major order, and seg[k] = first edge of segment k
+// (seg[nseg] = m).
+__global__ void bk_extract_kernel(const uint64_t* __restrict__ keys, int64_t m, int sb_bits, int kbits,
+                                  int64_t nseg, uint16_t* __restrict__ src_lo, uint16_t* __restrict__ dst_lo,
+                                  int32_t* __restrict__ seg) {
+  const uint64_t kmask = (1ull << kbits) - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = keys[i];
+    const int64_t k = (int64_t)(key & kmask);
+    src_lo[i] = (uint16_t)((key >> kbits) & ((1u << sb_bits) - 1));
+    dst_lo[i] = (uint16_t)(key >> (kbits + sb_bits));
+    const int64_t first = i > 0 ? (int64_t)(keys[i - 1] & kmask) + 1 : 0;
+    for (int64_t kk = first; kk <= k; ++kk) seg[kk] = (int32_t)i;
+    if (i == m - 1)
+      for (int64_t kk = k + 1; kk <= nseg; ++kk) seg[kk] = (int32_t)m;
+  }
+}
+
+// xseg[s * B + b] = edges of segment (b, s).
+__global__ void bk_transpose_kernel(const int32_t* __restrict__ seg, int32_t S, int32_t B, int2* __restrict__ xseg) {
+  const int64_t nseg = (int64_t)S * B;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nseg; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = k / S, s = k - b * S;
+    xseg[s * B + b] = make_int2(seg[k], seg[k + 1]);
+  }
+}
+
+// ---- expand ---------------------------------------------------------------
+
+// 8 consecutive edges with local sources packed in q: their codes to out.
+__device__ __forceinline__ void expand8(const uint32_t* s_code, uint4 q, uint32_t* out) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  uint32_t v[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[2 * j] = s_code[w[j] & 0xFFFFu];
+    v[2 * j + 1] = s_code[w[j] >> 16];
+  }
+  reinterpret_cast<uint4*>(out)[0] = make_uint4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<uint4*>(out)[1] = make_uint4(v[4], v[5], v[6], v[7]);
+}
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__global__ void __launch_bounds__(kBkThreads, 1) bk_expand_kernel(
+    const T* __restrict__ c_in, int32_t n, int sb_bits, int U, int32_t B, const int2* __restrict__ xseg,
+    const ExpandUnit* __restrict__ units, int32_t nunits, const uint16_t* __restrict__ src_lo,
+    uint32_t* __restrict__ vals, unsigned int* __restrict__ ctr, unsigned int epoch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int32_t SB = 1 << sb_bits;
+  uint32_t* s_code = reinterpret_cast<uint32_t*>(smem);
+  int32_t* s_pref = reinterpret_cast<int32_t*>(smem + (size_t)SB * 4);  // kMaxUnitSegs + 1
+  int32_t* s_lo = s_pref + kMaxUnitSegs + 1;
+  int32_t* s_hi = s_lo + kMaxUnitSegs;
+  __shared__ int32_t s_unit;
+  __shared__ int32_t s_wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (;;) {
+    __syncthreads();  // the previous unit is done with s_code and the segment tables
+    if (tid == 0) s_unit = (int32_t)(atomicAdd(ctr, 1u) - epoch);
+    __syncthreads();
+    const int32_t u = s_unit;
+    if (u < 0 || u >= nunits) return;
+    const ExpandUnit eu = units[u];
+    // the block's contributions, as codes
+    const int64_t v0 = (int64_t)eu.s << sb_bits;
+    const int32_t nb = (int32_t)(n - v0 < SB ? n - v0 : SB);
+    {
+      // 16-byte loads, four in flight per thread, then the conversions
+      constexpr int kPer = 16 / sizeof(T);
+      const int32_t nvec = nb / kPer;
+      const uint4* src = reinterpret_cast<const uint4*>(c_in + v0);
+      for (int32_t i0 = tid; i0 < nvec; i0 += 4 * blockDim.x) {
+        uint4 r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i0 + k * (int32_t)blockDim.x < nvec) r[k] = __ldg(src + i0 + k * blockDim.x);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int32_t i = i0 + k * blockDim.x;
+          if (i < nvec) {
+            const T* e = reinterpret_cast<const T*>(&r[k]);
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) s_code[i * kPer + j] = code_of(to_f32(e[j]), U);
+          }
+        }
+      }
+      for (int32_t i = nvec * kPer + tid; i < nb; i += blockDim.x) s_code[i] = code_of(to_f32(c_in[v0 + i]), U);
+    }
+    // clipped segment ranges and the prefix of their chunk counts
+    const int nseg = eu.b_hi - eu.b_lo;
+    int32_t chunks = 0;
+    if (tid < nseg) {
+      const int2 r = xseg[(int64_t)eu.s * B + eu.b_lo + tid];
+      const int32_t lo = max(r.x, eu.lo), hi = min(r.y, eu.hi);
+      s_lo[tid] = lo;
+      s_hi[tid] = hi;
+      chunks = hi > lo ? (hi - 1) / kChunk - lo / kChunk + 1 : 0;
+    }
+    int32_t v = chunks;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) s_wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t t = lane < nwarps ? s_wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      s_wsum[lane] = t;
+    }
+    __syncthreads();
+    const int32_t excl = v - chunks + (warp > 0 ? s_wsum[warp - 1] : 0);
+    s_pref[tid] = excl;
+    if (tid == blockDim.x - 1) s_pref[blockDim.x] = excl + chunks;
+    __syncthreads();
+    const int32_t total = s_pref[nseg];
+    // two chunks per warp step, both index loads issued before either is used
+    for (int32_t ch = warp; ch < total; ch += 2 * nwarps) {
+      int32_t g[2], lo[2], hi[2];
+      bool full[2];
+      uint4 q[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int32_t c = ch + t * nwarps;
+        if (c >= total) {  // no second chunk: an empty range
+          g[t] = lo[t] = hi[t] = 0;
+          full[t] = false;
+          continue;
+        }
+        int k0 = 0, k1 = nseg - 1;  // the last segment whose first chunk is <= c
+        while (k0 < k1) {
+          const int mid = (k0 + k1 + 1) >> 1;
+          if (s_pref[mid] <= c)
+            k0 = mid;
+          else
+            k1 = mid - 1;
+        }
+        lo[t] = s_lo[k0];
+        hi[t] = s_hi[k0];
+        g[t] = (lo[t] / kChunk + (c - s_pref[k0])) * kChunk + 8 * lane;
+        full[t] = g[t] >= lo[t] && g[t] + 8 <= hi[t];
+        if (full[t]) q[t] = __ldcs(reinterpret_cast<const uint4*>(src_lo + g[t]));
+      }
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (full[t]) {
+          expand8(s_code, q[t], vals + g[t]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int32_t e = g[t] + j;
+            if (e >= lo[t] && e < hi[t]) vals[e] = s_code[src_lo[e]];
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---- accumulate -----------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
+    const uint32_t* __restrict__ vals, const uint16_t* __restrict__ dst_lo, int32_t n, int w_bits, int U,
+    const AccumUnit* __restrict__ units, int32_t nunits, unsigned int* __restrict__ ctr, unsigned int epoch,
+    unsigned long long* __restrict__ acc_g, unsigned int* __restrict__ bin_arrive, const float* __restrict__ x_in,
+    const float* __restrict__ inv_deg, float* __restrict__ x_out, T* __restrict__ c_out, StepParams* __restrict__ prm,
+    double* __restrict__ partials, int32_t nbins, double* __restrict__ log_row) {
+  extern __shared__ __align__(16) uint32_t s_acc32[];
+  __shared__ int32_t s_unit;
+  __shared__ int s_flag;
+  const int32_t W = 1 << w_bits;
+  uint32_t* s_lo = s_acc32;
+  uint32_t* s_hi = s_acc32 + W;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_unit = (int32_t)(atomicAdd(ctr + 1, 1u) - epoch);
+    __syncthreads();
+    const int32_t u = s_unit;
+    if (u < 0 || u >= nunits) return;
+    const AccumUnit un = units[u];
+    const int32_t v0 = un.b << w_bits;
+    const int32_t nv = min(W, n - v0);
+    for (int32_t i = tid; i < nv; i += blockDim.x) s_lo[i] = s_hi[i] = 0u;
+    __syncthreads();
+    for (int32_t base = (un.lo & ~(kChunk - 1)) + warp * kChunk; base < un.hi; base += nwarps * kChunk) {
+      const int32_t g0 = base + 8 * lane;
+      uint32_t w[8];
+      int32_t d[8];
+      if (g0 >= un.lo && g0 + 8 <= un.hi) {
+        const uint4 wa = __ldcs(reinterpret_cast<const uint4*>(vals + g0));
+        const uint4 wb = __ldcs(reinterpret_cast<const uint4*>(vals + g0) + 1);
+        w[0] = wa.x, w[1] = wa.y, w[2] = wa.z, w[3] = wa.w;
+        w[4] = wb.x, w[5] = wb.y, w[6] = wb.z, w[7] = wb.w;
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(dst_lo + g0));
+        const uint32_t r[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          d[2 * j] = (int32_t)(r[j] & 0xFFFFu);
+          d[2 * j + 1] = (int32_t)(r[j] >> 16);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const bool ok = g0 + j >= un.lo && g0 + j < un.hi;
+          w[j] = ok ? vals[g0 + j] : 0u;
+          d[j] = ok ? (int32_t)dst_lo[g0 + j] : -1;
+        }
+      }
+      // values: codes below 2^31 are the value; the rest are converted
+      unsigned long long q[8];
+      bool big = false;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        q[j] = w[j];
+        big = big || (w[j] >> 31);
+      }
+      if (__any_sync(0xffffffffu, big)) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) q[j] = value_of(w[j], U);
+      }
+      // runs of equal rows are folded into their first edge (backward, so a
+      // head holds its whole run: consecutive edges of one row would
+      // otherwise meet in one atomic instruction)
+#pragma unroll
+      for (int j = 6; j >= 0; --j) {
+        if (d[j] >= 0 && d[j] == d[j + 1]) {
+          q[j] += q[j + 1];
+          d[j + 1] = -1;
+        }
+      }
+      // a warp step inside one row (long rows): one shared-memory addition
+      const int32_t c0 = __shfl_sync(0xffffffffu, d[0], 0);
+      bool one = d[0] >= 0 && d[0] == c0;
+#pragma unroll
+      for (int j = 1; j < 8; ++j) one = one && d[j] < 0;
+      if (__all_sync(0xffffffffu, one)) {
+        unsigned long long r = q[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (lane == 0) acc_add(s_lo, s_hi, c0, (uint32_t)r, (uint32_t)(r >> 32));
+      } else {
+        // every head's low word with independent atomics, then the carries
+        uint32_t old[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (d[j] >= 0) old[j] = atomicAdd(s_lo + d[j], (uint32_t)q[j]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (d[j] >= 0) {
+            const uint32_t ql = (uint32_t)q[j];
+            const uint32_t up = (uint32_t)(q[j] >> 32) + (old[j] + ql < old[j] ? 1u : 0u);
+            if (up) atomicAdd(s_hi + d[j], up);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (un.nparts > 1) {
+      unsigned long long* g = acc_g + (int64_t)un.split * W;
+      for (int32_t i = tid; i < nv; i += blockDim.x) {
+        const unsigned long long a = ((unsigned long long)s_hi[i] << 32) | s_lo[i];
+        if (a) atomicAdd(g + i, a);
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) s_flag = atomicAdd(bin_arrive + un.split, 1u) == (unsigned)(un.nparts - 1);
+      __syncthreads();
+      if (!s_flag) continue;
+      __threadfence();
+      // the last unit of the bin takes the totals and clears them for the next step
+      for (int32_t i = tid; i < nv; i += blockDim.x) {
+        const unsigned long long a = atomicExch(g + i, 0ull);
+        s_lo[i] = (uint32_t)a;
+        s_hi[i] = (uint32_t)(a >> 32);
+      }
+      if (tid == 0) bin_arrive[un.split] = 0;
+      __syncthreads();
+    }
+    const float A = prm->coefA, Bc = prm->coefB;
+    float mass = 0.f, dang = 0.f, res = 0.f;
+    for (int32_t i = tid; i < nv; i += blockDim.x) {
+      const float y = from_fixed(((unsigned long long)s_hi[i] << 32) | s_lo[i], U);
+      finish_row(v0 + i, y, A, Bc, x_in, inv_deg, x_out, c_out, mass, dang, res);
+    }
+    block_partials3(mass, dang, res, partials + 3 * (int64_t)un.b);
+    if (tid == 0) {
+      __threadfence();
+      s_flag = atomicAdd(ctr + 2, 1u) == (unsigned)(nbins - 1);
+    }
+    __syncthreads();
+    if (s_flag) {
+      // every bin of the step is finished: fold them, in bin order
+      __threadfence();
+      fold_step(partials, nbins, prm, log_row);
+      if (tid == 0) ctr[2] = 0;
+    }
+  }
+}
+
+// ---- host side --------------------------------------------------------------
+
+static int bits_to_hold(uint64_t v) {
+  int b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return b;
+}
+
+// Key bits of the segment index: the radix sort orders whole 8-bit digits,
+// so the index takes whole digits and the payload above it stays out of them.
+static int segment_key_bits(int64_t nseg) {
+  const int b = std::max(1, bits_to_hold((uint64_t)(nseg - 1)));
+  return (b + 7) & ~7;
+}
+
+static int smem_optin() {
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device_ordinal());
+  return optin;
+}
+
+static size_t expand_smem(int sb_bits) { return ((size_t)4 << sb_bits) + (size_t)(3 * kMaxUnitSegs + 1) * 4; }
+static size_t accum_smem(int w_bits) { return (size_t)8 << w_bits; }
+
+bool blocked_eligible(const gpr_graph* g, int sb_bits, int w_bits) {
+  if (sb_bits < 4 || sb_bits > 16 || w_bits < 4 || w_bits > 16) return false;
+  if (g->n < 1 || g->m > (int64_t)INT32_MAX - 2 * kChunk) return false;
+  const int64_t S = ((int64_t)g->n + (1 << sb_bits) - 1) >> sb_bits;
+  const int64_t B = ((int64_t)g->n + (1 << w_bits) - 1) >> w_bits;
+  const int64_t nseg = S * B;
+  if (nseg > ((int64_t)1 << 26)) return false;  // segment tables of at most 2^26 entries
+  const int kbits = segment_key_bits(nseg);
+  if (kbits + sb_bits + w_bits > 64) return false;
+  const size_t optin = (size_t)smem_optin();
+  // static shared memory of the kernels is below 1 KB
+  return expand_smem(sb_bits) + 1024 <= optin && accum_smem(w_bits) + 1024 <= optin;
+}
+
+void blocked_free(Blocked* k, cudaStream_t s) {
+  if (!k) return;
+  dfree(k->src_lo, s);
+  dfree(k->dst_lo, s);
+  dfree(k->vals, s);
+  dfree(k->xseg, s);
+  dfree(k->xu, s);
+  dfree(k->au, s);
+  dfree(k->acc_g, s);
+  dfree(k->bin_arrive, s);
+  dfree(k->ctr, s);
+  dfree(k->partials, s);
+  delete k;
+}
+
+template <typename K>
+static int persistent_grid(K kernel, size_t smem) {
+  GPR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBkThreads, smem));
+  return num_sms() * std::max(per_sm, 1);
+}
+
+Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit_edges, cudaStream_t s) {
+  const int64_t unit = std::max<int64_t>(unit_edges, 1 << 12);
+  const int64_t xunit = std::min<int64_t>(1 << 20, 4 * unit);  // expand units stage a source block each
+  if (!blocked_eligible(g, sb_bits, w_bits))
+    throw StatusFail{GPR_EINVAL, "the blocked schedule does not fit this graph"};
+  Blocked* k = new Blocked();
+  k->sb_bits = sb_bits;
+  k->w_bits = w_bits;
+  k->unit_edges = unit;
+  {
+    int lg = 0;
+    while (((int64_t)1 << lg) < g->n) ++lg;  // ceil(log2 n)
+    k->ubits = std::min(60, 28 + lg);
+  }
+  const int32_t n = g->n;
+  const int64_t m = g->m;
+  k->S = (int32_t)(((int64_t)n + (1 << sb_bits) - 1) >> sb_bits);
+  k->B = (int32_t)(((int64_t)n + (1 << w_bits) - 1) >> w_bits);
+  const int32_t S = k->S, B = k->B;
+  const int64_t nseg = (int64_t)S * B;
+  const int kbits = segment_key_bits(nseg);
+  uint64_t* keys = nullptr;
+  uint64_t* alt = nullptr;
+  int32_t* seg = nullptr;
+  int* derr = nullptr;
+  try {
+    const size_t me = (size_t)std::max<int64_t>(m, 1);
+    k->src_lo = (uint16_t*)dalloc(me * 2, s);
+    k->dst_lo = (uint16_t*)dalloc(me * 2, s);
+    k->vals = (uint32_t*)dalloc(me * 4, s);
+    seg = (int32_t*)dalloc((size_t)(nseg + 1) * 4, s);
+    derr = (int*)dalloc(sizeof(int) * 2, s);
+    GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
+    const int grid = num_sms() * 8;
+    if (m > 0) {
+      keys = (uint64_t*)dalloc((size_t)m * 8, s);
+      alt = (uint64_t*)dalloc((size_t)m * 8, s);
+      bk_keys_kernel<<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, n, sb_bits, w_bits, kbits, S, keys);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      const uint64_t* sorted = radix_sort_u64(keys, alt, m, kbits, s, derr);
+      bk_extract_kernel<<<grid, 256, 0, s>>>(sorted, m, sb_bits, kbits, nseg, k->src_lo, k->dst_lo, seg);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      dfree(keys, s);
+      dfree(alt, s);
+      keys = alt = nullptr;
+    } else {
+      GPR_CUDA(cudaMemsetAsync(seg, 0, (size_t)(nseg + 1) * 4, s));
+    }
+    k->xseg = (int2*)dalloc((size_t)nseg * sizeof(int2), s);
+    bk_transpose_kernel<<<grid, 256, 0, s>>>(seg, S, B, k->xseg);
+    GPR_CUDA(cudaGetLastError());
+    count_launches(1);
+    std::vector<int32_t> h((size_t)nseg + 1);
+    int herr = 0;
+    GPR_CUDA(cudaMemcpyAsync(h.data(), seg, (size_t)(nseg + 1) * 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    dfree(seg, s);
+    dfree(derr, s);
+    seg = nullptr;
+    derr = nullptr;
+    if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "blocked layout: a look-back wait of the sort timed out"};
+
+    // expand units: per source block, runs of consecutive bins' segments of
+    // at most unit edges and kMaxUnitSegs segments; a longer segment
+    // is cut into pieces of its own
+    std::vector<ExpandUnit> xu;
+    for (int32_t sb = 0; sb < S; ++sb) {
+      int32_t first = -1, last = -1, clo = 0, chi = 0;
+      int64_t edges = 0;
+      auto flush = [&]() {
+        if (first >= 0 && edges > 0) xu.push_back(ExpandUnit{sb, first, last + 1, clo, chi});
+        first = -1;
+        edges = 0;
+      };
+      for (int32_t b = 0; b < B; ++b) {
+        const int32_t lo = h[(size_t)b * S + sb], hi = h[(size_t)b * S + sb + 1];
+        const int64_t len = hi - lo;
+        if (len == 0) continue;
+        if (len > xunit) {
+          flush();
+          for (int64_t o = 0; o < len; o += xunit)
+            xu.push_back(ExpandUnit{sb, b, b + 1, (int32_t)(lo + o), (int32_t)std::min<int64_t>(hi, lo + o + xunit)});
+          continue;
+        }
+        if (first >= 0 && (edges + len > xunit || b - first >= kMaxUnitSegs)) flush();
+        if (first < 0) {
+          first = b;
+          clo = lo;
+        }
+        last = b;
+        chi = hi;
+        edges += len;
+      }
+      flush();
+    }
+    // accumulate units: each bin whole, or cut into near-equal edge ranges
+    std::vector<AccumUnit> au;
+    int32_t n_split = 0;
+    for (int32_t b = 0; b < B; ++b) {
+      const int64_t lo = h[(size_t)b * S], hi = h[(size_t)(b + 1) * S];
+      const int64_t e = hi - lo;
+      const int32_t parts = (int32_t)std::max<int64_t>(1, (e + unit - 1) / unit);
+      const int32_t split = parts > 1 ? n_split++ : -1;
+      for (int32_t q = 0; q < parts; ++q)
+        au.push_back(AccumUnit{b, (int32_t)(lo + e * q / parts), (int32_t)(lo + e * (q + 1) / parts), parts, split});
+    }
+    // largest first: the dynamic queues then end with small units
+    std::stable_sort(xu.begin(), xu.end(),
+                     [](const ExpandUnit& a, const ExpandUnit& b) { return a.hi - a.lo > b.hi - b.lo; });
+    std::stable_sort(au.begin(), au.end(),
+                     [](const AccumUnit& a, const AccumUnit& b) { return a.hi - a.lo > b.hi - b.lo; });
+    k->n_xu = (int32_t)xu.size();
+    k->n_au = (int32_t)au.size();
+    k->n_split = n_split;
+    k->xu = (ExpandUnit*)dalloc(std::max<size_t>(xu.size(), 1) * sizeof(ExpandUnit), s);
+    k->au = (AccumUnit*)dalloc(au.size() * sizeof(AccumUnit), s);
+    if (!xu.empty())
+      GPR_CUDA(cudaMemcpyAsync(k->xu, xu.data(), xu.size() * sizeof(ExpandUnit), cudaMemcpyHostToDevice, s));
+    GPR_CUDA(cudaMemcpyAsync(k->au, au.data(), au.size() * sizeof(AccumUnit), cudaMemcpyHostToDevice, s));
+    const size_t W = (size_t)1 << w_bits;
+    if (n_split > 0) {
+      k->acc_g = (unsigned long long*)dalloc((size_t)n_split * W * 8, s);
+      k->bin_arrive = (unsigned int*)dalloc((size_t)n_split * 4, s);
+      GPR_CUDA(cudaMemsetAsync(k->acc_g, 0, (size_t)n_split * W * 8, s));
+      GPR_CUDA(cudaMemsetAsync(k->bin_arrive, 0, (size_t)n_split * 4, s));
+    }
+    k->ctr = (unsigned int*)dalloc(16, s);
+    GPR_CUDA(cudaMemsetAsync(k->ctr, 0, 16, s));
+    k->partials = (double*)dalloc((size_t)B * 3 * sizeof(double), s);
+    k->xgrid = std::max(persistent_grid(bk_expand_kernel<float>, expand_smem(sb_bits)),
+                        persistent_grid(bk_expand_kernel<__nv_bfloat16>, expand_smem(sb_bits)));
+    k->agrid = std::max(persistent_grid(bk_accum_kernel<float>, accum_smem(w_bits)),
+                        persistent_grid(bk_accum_kernel<__nv_bfloat16>, accum_smem(w_bits)));
+    k->bytes = (int64_t)me * 8 + nseg * (int64_t)sizeof(int2) + (int64_t)xu.size() * sizeof(ExpandUnit) +
+               (int64_t)au.size() * sizeof(AccumUnit) + (int64_t)n_split * (int64_t)W * 8 + (int64_t)B * 24;
+    return k;
+  } catch (...) {
+    dfree(keys, s);
+    dfree(alt, s);
+    dfree(seg, s);
+    dfree(derr, s);
+    blocked_free(k, s);
+    throw;
+  }
+}
+
+void blocked_record_reset(Blocked* k, cudaStream_t s) { GPR_CUDA(cudaMemsetAsync(k->ctr, 0, 16, s)); }
+
+template <typename T>
+void blocked_record_step(Blocked* k, const gpr_graph* g, const T* c_in, const float* x_in, float* x_out, T* c_out,
+                         StepParams* prm, double* log_row, int32_t it, cudaStream_t s) {
+  // every CTA of a launch takes units until one fetch fails: a launch moves
+  // a counter by exactly (units + grid)
+  const unsigned int ex = (unsigned int)((int64_t)it * (k->n_xu + k->xgrid));
+  const unsigned int ea = (unsigned int)((int64_t)it * (k->n_au + k->agrid));
+  bk_expand_kernel<T><<<k->xgrid, kBkThreads, expand_smem(k->sb_bits), s>>>(
+      c_in, g->n, k->sb_bits, k->ubits, k->B, k->xseg, k->xu, k->n_xu, k->src_lo, k->vals, k->ctr, ex);
+  bk_accum_kernel<T><<<k->agrid, kBkThreads, accum_smem(k->w_bits), s>>>(
+      k->vals, k->dst_lo, g->n, k->w_bits, k->ubits, k->au, k->n_au, k->ctr, ea, k->acc_g, k->bin_arrive, x_in,
+      g->plan.inv_deg, x_out, c_out, prm, k->partials, k->B, log_row);
+  GPR_CUDA(cudaGetLastError());
+}
+
+template void blocked_record_step<float>(Blocked*, const gpr_graph*, const float*, const float*, float*, float*,
+                                         StepParams*, double*, int32_t, cudaStream_t);
+template void blocked_record_step<__nv_bfloat16>(Blocked*, const gpr_graph*, const __nv_bfloat16*, const float*,
+                                                 float*, __nv_bfloat16*, StepParams*, double*, int32_t, cudaStream_t);
+
+}  // namespace gpr

@@ -22,88 +22,15 @@
 // kernel.  The bucket kernels of a step are independent and run as parallel
 // branches of one CUDA graph that holds the whole iteration loop.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
-#include "gpr_internal.cuh"
+#include "blocked.cuh"
+#include "pr_step.cuh"
 
 namespace gpr {
-
-struct StepParams {
-  float coefA, coefB;
-  double d;
-  double n;
-};
-
-// ---- storage of the gathered contributions c = x / outdeg: FP32 or BF16.
-// The rank vector x itself and all accumulation stay FP32. --------------
-template <typename T>
-__device__ __forceinline__ float ld_rank(const T* p, int64_t i);
-template <>
-__device__ __forceinline__ float ld_rank<float>(const float* p, int64_t i) {
-  return __ldg(p + i);
-}
-template <>
-__device__ __forceinline__ float ld_rank<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
-  return __bfloat162float(__ldg(p + i));
-}
-template <typename T>
-__device__ __forceinline__ void store_rank(T* p, int64_t i, float v);
-template <>
-__device__ __forceinline__ void store_rank<float>(float* p, int64_t i, float v) {
-  p[i] = v;
-}
-template <>
-__device__ __forceinline__ void store_rank<__nv_bfloat16>(__nv_bfloat16* p, int64_t i, float v) {
-  p[i] = __float2bfloat16_rn(v);
-}
-
-// ---- reductions ----------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block partial of three per-thread FP32 sums: FP32 within each warp, FP64
-// across warps, written to out[0..2].  Call with all threads of the block.
-__device__ __forceinline__ void block_partials3(float a, float b, float c, double* out) {
-  __shared__ double s[3][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
-  if (lane == 0) {
-    s[0][w] = a;
-    s[1][w] = b;
-    s[2][w] = c;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double ta = 0, tb = 0, tc = 0;
-    for (int i = 0; i < nw; ++i) {
-      ta += s[0][i];
-      tb += s[1][i];
-      tc += s[2][i];
-    }
-    out[0] = ta;
-    out[1] = tb;
-    out[2] = tc;
-  }
-}
-
-// Finish one row: store x' and c', accumulate mass, dangling mass, residual.
-template <typename T>
-__device__ __forceinline__ void finish_row(int64_t r, float y, float A, float B, const float* __restrict__ x_in,
-                                           const float* __restrict__ inv_deg, float* __restrict__ x_out,
-                                           T* __restrict__ c_out, float& mass, float& dang, float& res) {
-  const float idg = inv_deg[r];
-  const float xs = fmaf(A, y, B);
-  x_out[r] = xs;
-  store_rank(c_out, r, xs * idg);
-  mass += xs;
-  res += fabsf(xs - x_in[r]);
-  if (idg == 0.0f) dang += xs;
-}
 
 // Warp-cooperative sum of c over edges [e0, e1): 128-bit index loads on the
 // 16-byte-aligned body, up to 16 gathers in flight per lane.  Every lane
@@ -329,41 +256,8 @@ __global__ void __launch_bounds__(256) finish_kernel(
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  __shared__ double s[3][8];
-  double a = 0, b = 0, c = 0;
-  for (int32_t i = threadIdx.x; i < npartials; i += blockDim.x) {
-    a += __ldcg(partials + 3 * (int64_t)i);
-    b += __ldcg(partials + 3 * (int64_t)i + 1);
-    c += __ldcg(partials + 3 * (int64_t)i + 2);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    s[0][w] = a;
-    s[1][w] = b;
-    s[2][w] = c;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mass = 0, dang = 0, res = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      mass += s[0][i];
-      dang += s[1][i];
-      res += s[2][i];
-    }
-    log_row[0] = mass;
-    log_row[1] = dang;
-    log_row[2] = res;
-    const double d = prm->d, n = prm->n;
-    prm->coefA = (float)(d / mass);
-    prm->coefB = (float)((1.0 - d) / n + d * dang / (n * mass));
-    *arrive = 0;  // ready for the next step
-  }
+  fold_step(partials, npartials, prm, log_row);
+  if (threadIdx.x == 0) *arrive = 0;  // ready for the next step
 }
 
 __global__ void output_kernel(const float* __restrict__ x, const int32_t* __restrict__ old2new, int32_t n,
@@ -398,12 +292,15 @@ struct PagerankWork {
   int finish_grid = 1;
   int init_grid = 1;
   cudaStream_t cap = nullptr;
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // around the iteration graph, for gpr_stats
   cudaStream_t side[kMaxBuckets] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kMaxBuckets] = {};
+  Blocked* blk = nullptr;  // the blocked schedule's edge layout, made on first use
   cudaGraphExec_t exec = nullptr;
   int32_t exec_iters = -1;
   int exec_dt = -1;
+  int exec_sched = -1;
   int64_t exec_kernels = 0;  // kernel nodes in `exec`
 };
 
@@ -411,6 +308,7 @@ void pagerank_work_free(PagerankWork* w) {
   if (!w) return;
   if (w->exec) cudaGraphExecDestroy(w->exec);
   cudaStream_t s = w->cap;
+  blocked_free(w->blk, s);
   for (int i = 0; i < 2; ++i) {
     dfree(w->x[i], s);
     dfree(w->c[i], s);
@@ -423,6 +321,8 @@ void pagerank_work_free(PagerankWork* w) {
   dfree(w->arrive, s);
   dfree(w->log, s);
   if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+  if (w->ev_t0) cudaEventDestroy(w->ev_t0);
+  if (w->ev_t1) cudaEventDestroy(w->ev_t1);
   for (int i = 0; i < kMaxBuckets; ++i) {
     if (w->ev_join[i]) cudaEventDestroy(w->ev_join[i]);
     if (w->side[i]) cudaStreamDestroy(w->side[i]);
@@ -503,7 +403,7 @@ static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_g
 // hot pass, then the cold-pass bucket kernels forked onto side streams, joined
 // before the finish kernel.
 template <typename T>
-static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters) {
+static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, int sched) {
   const Plan& P = g->plan;
   cudaStream_t s = w->cap;
   float* x[2] = {w->x[0], w->x[1]};
@@ -521,6 +421,14 @@ static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters) {
   finish_kernel<T><<<1, 256, 0, s>>>(x[0], P.inv_deg, x[0], c[0], P.split_row, P.split_hbeg, P.split_hend,
                                     P.split_cbeg, P.split_cend, 0, w->chunk_sum, w->partials, w->init_grid + 1,
                                     w->prm, w->log, w->arrive);
+  if (sched == kSchedBlocked) {
+    blocked_record_reset(w->blk, s);
+    for (int32_t it = 0; it < iters; ++it) {
+      const int a = it & 1, b = a ^ 1;
+      blocked_record_step<T>(w->blk, g, c[a], x[a], x[b], c[b], w->prm, w->log + 3 * (int64_t)(it + 1), it, s);
+    }
+    return;
+  }
   for (int32_t it = 0; it < iters; ++it) {
     const int a = it & 1, b = a ^ 1;
     if (hot)
@@ -552,6 +460,8 @@ static PagerankWork* work_make(gpr_graph* g, cudaStream_t s) {
       GPR_CUDA(cudaEventCreateWithFlags(&w->ev_join[i], cudaEventDisableTiming));
     }
     GPR_CUDA(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
+    GPR_CUDA(cudaEventCreate(&w->ev_t0));
+    GPR_CUDA(cudaEventCreate(&w->ev_t1));
     const size_t vb = (size_t)g->n * 4;
     for (int i = 0; i < 2; ++i) {
       w->x[i] = (float*)dalloc(vb, s);
@@ -590,12 +500,64 @@ static PagerankWork* work_make(gpr_graph* g, cudaStream_t s) {
   }
 }
 
+// Shape of the blocked schedule: GPR_BLOCK_BITS="sb,w[,u]" (source block
+// and bin bits, log2 of the edges per work unit), else 2^15-node source
+// blocks, 2^14-row bins and units of about m / 2048 edges, between 2^16 and
+// 2^20, so every SM gets several units.
+static void block_bits(const gpr_graph* g, int* sb, int* wb, int64_t* unit) {
+  *sb = 15;
+  *wb = 14;
+  int64_t u = 1 << 16;
+  while (u < (1 << 20) && u * 2048 < g->m) u <<= 1;
+  *unit = u;
+  if (const char* e = getenv("GPR_BLOCK_BITS")) {
+    int a = 0, b = 0, c = 0;
+    const int k = sscanf(e, "%d,%d,%d", &a, &b, &c);
+    if (k >= 2) {
+      *sb = a;
+      *wb = b;
+    }
+    if (k == 3 && c >= 12 && c <= 30) *unit = (int64_t)1 << c;
+  }
+}
+
+// The schedule of a call: forced by flags, else GPR_SPMV=pull|blocked,
+// else pull.
+static int pick_schedule(const gpr_graph* g, int flags) {
+  if (flags & GPR_SPMV_PULL) return kSchedPull;
+  if (flags & GPR_SPMV_BLOCKED) return kSchedBlocked;
+  if (const char* e = getenv("GPR_SPMV")) {
+    int sb, wb;
+    int64_t ue;
+    block_bits(g, &sb, &wb, &ue);
+    if (!strcmp(e, "blocked") && blocked_eligible(g, sb, wb)) return kSchedBlocked;
+  }
+  return kSchedPull;
+}
+
 gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
                         gpr_stats* st, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g->mu);
   try {
+    const auto t_setup0 = std::chrono::steady_clock::now();
     if (!g->work) g->work = work_make(g, s);
     PagerankWork* w = g->work;
+    const int sched = pick_schedule(g, flags);
+    if (sched == kSchedBlocked) {
+      int sb, wb;
+      int64_t ue;
+      block_bits(g, &sb, &wb, &ue);
+      if (w->blk && (w->blk->sb_bits != sb || w->blk->w_bits != wb || w->blk->unit_edges != ue)) {
+        if (w->exec) {
+          cudaGraphExecDestroy(w->exec);
+          w->exec = nullptr;
+        }
+        GPR_CUDA(cudaStreamSynchronize(s));
+        blocked_free(w->blk, s);
+        w->blk = nullptr;
+      }
+      if (!w->blk) w->blk = blocked_build(g, sb, wb, ue, s);
+    }
     if (w->log_cap < iters + 1) {
       dfree(w->log, s);
       w->log = nullptr;
@@ -610,7 +572,7 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
     }
     StepParams hp{0.f, 0.f, damping, (double)g->n};
     GPR_CUDA(cudaMemcpyAsync(w->prm, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
-    if (!w->exec || w->exec_iters != iters || w->exec_dt != (int)dt) {
+    if (!w->exec || w->exec_iters != iters || w->exec_dt != (int)dt || w->exec_sched != sched) {
       if (w->exec) {
         cudaGraphExecDestroy(w->exec);
         w->exec = nullptr;
@@ -621,9 +583,9 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
       GPR_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
       try {
         if (dt == GPR_BF16)
-          record_iterations<__nv_bfloat16>(g, w, iters);
+          record_iterations<__nv_bfloat16>(g, w, iters, sched);
         else
-          record_iterations<float>(g, w, iters);
+          record_iterations<float>(g, w, iters, sched);
       } catch (...) {
         cudaGraph_t junk = nullptr;
         cudaStreamEndCapture(w->cap, &junk);
@@ -640,9 +602,16 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
       }
       w->exec_iters = iters;
       w->exec_dt = (int)dt;
-      w->exec_kernels = 2 + (int64_t)iters * (g->plan.nbuckets + 1 + (w->hot_grid > 0 ? 1 : 0));
+      w->exec_sched = sched;
+      w->exec_kernels = sched == kSchedBlocked
+                            ? 2 + (int64_t)iters * 2
+                            : 2 + (int64_t)iters * (g->plan.nbuckets + 1 + (w->hot_grid > 0 ? 1 : 0));
     }
+    const double t_setup =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_setup0).count();
+    if (st) GPR_CUDA(cudaEventRecord(w->ev_t0, s));
     GPR_CUDA(cudaGraphLaunch(w->exec, s));
+    if (st) GPR_CUDA(cudaEventRecord(w->ev_t1, s));
     count_launches(w->exec_kernels);
     const float* xf = w->x[iters & 1];
     float* dst = (flags & GPR_PTR_HOST) ? nullptr : x_out;
@@ -665,6 +634,11 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
       st->mass = row[0];
       st->dangling = row[1];
       st->residual_l1 = iters > 0 ? row[2] : 0.0;
+      float ms = 0.f;
+      GPR_CUDA(cudaEventElapsedTime(&ms, w->ev_t0, w->ev_t1));
+      st->t_iter_ms = ms;
+      st->t_setup_ms = t_setup;
+      st->schedule = sched == kSchedBlocked ? GPR_SPMV_BLOCKED : GPR_SPMV_PULL;
     } else if (flags & GPR_PTR_HOST) {
       GPR_CUDA(cudaStreamSynchronize(s));
     }

@@ -26,14 +26,14 @@ def torch():
     return torch
 
 
-def gpu_pr(torch, g, iters, d=0.85, dt=gpr.FP32, stats=False):
+def gpu_pr(torch, g, iters, d=0.85, dt=gpr.FP32, stats=False, spmv="auto"):
     out = torch.empty(g.n, dtype=torch.float32, device="cuda")
-    st = gpr.pagerank(g, out, damping=d, iters=iters, dtype=dt, stats=stats)
+    st = gpr.pagerank(g, out, damping=d, iters=iters, dtype=dt, stats=stats, spmv=spmv)
     x = out.cpu().numpy()
     return (x, st) if stats else x
 
 
-def check(torch, n, src, dst, iters, dt=gpr.FP32, d=0.85, buckets=None, hot=None):
+def check(torch, n, src, dst, iters, dt=gpr.FP32, d=0.85, buckets=None, hot=None, spmv="auto"):
     if buckets is not None:
         os.environ["GPR_BUCKETS"] = buckets
     if hot is not None:
@@ -44,7 +44,7 @@ def check(torch, n, src, dst, iters, dt=gpr.FP32, d=0.85, buckets=None, hot=None
         os.environ.pop("GPR_BUCKETS", None)
         os.environ.pop("GPR_HOT", None)
     ref = oracle.pagerank(oracle.build_csc(n, src, dst), d, iters)
-    x, st = gpu_pr(torch, g, iters, d, dt, stats=True)
+    x, st = gpu_pr(torch, g, iters, d, dt, stats=True, spmv=spmv)
     err = l1(x, ref)
     assert err <= TOL[dt], (err, max_rel(x, ref))
     # BF16 rounding of the gathered contributions moves the mass by up to ~2^-9 d
@@ -91,21 +91,87 @@ def test_random_graphs(torch, n, m_raw, seed):
         check(torch, n, src, dst, 25, dt)
 
 
-def test_closed_forms_on_gpu(torch):
+@pytest.fixture
+def block_bits():
+    """Sets the blocked schedule's block sizes ("sb,w") for one test."""
+    def set_bits(v):
+        os.environ["GPR_BLOCK_BITS"] = v
+    yield set_bits
+    os.environ.pop("GPR_BLOCK_BITS", None)
+
+
+# "4,5": 16-node source blocks and 32-row bins, so a 30k-node graph has
+# ~1.8M segments, expand units cut at 1024 segments, and hub bins cut into
+# several accumulate units meeting in the global accumulator
+@pytest.mark.parametrize("bits", ["15,14", "4,5", "9,4", "13,13"])
+@pytest.mark.parametrize("n,m_raw,seed", [(1, 5, 0), (2, 1, 1), (257, 3000, 2), (30_000, 600_000, 31),
+                                          (100_003, 3_000_000, 4)])
+def test_blocked_schedule_matches_oracle(torch, block_bits, bits, n, m_raw, seed):
+    block_bits(bits)
+    if n == 30_000:
+        src, dst = gen.rmat_coo(n, m_raw, seed=seed)
+    else:
+        src, dst = random_coo_with_dups(np.random.default_rng(seed), n, m_raw)
+    for dt in (gpr.FP32, gpr.BF16):
+        check(torch, n, src, dst, 25, dt, spmv="blocked")
+
+
+def test_blocked_schedule_rejects_block_sizes_that_do_not_fit(torch, block_bits):
+    g = gpr.graph_build(np.array([0, 1], np.int32), np.array([1, 0], np.int32), 2)
+    out = torch.empty(2, device="cuda")
+    for bits in ("16,16", "3,8", "8,17"):  # shared memory too small / blocks out of range
+        block_bits(bits)
+        with pytest.raises(gpr.GprError) as ei:
+            gpr.pagerank(g, out, iters=3, spmv="blocked")
+        assert ei.value.status == gpr.EINVAL
+    block_bits("8,8")
+    gpr.pagerank(g, out, iters=3, spmv="blocked")
+    assert np.abs(out.cpu().numpy() - 0.5).max() < 1e-7
+
+
+def test_blocked_schedule_long_rows_and_split_bins(torch, block_bits):
+    # a hub row with 2M in-edges (longer than an accumulate unit) and a
+    # source block whose segment is longer than an expand unit
+    n = 70_000
+    rng = np.random.default_rng(12)
+    src = rng.integers(0, n, 3_000_000).astype(np.int32)
+    dst = np.where(rng.random(3_000_000) < 0.7, 5, rng.integers(0, n, 3_000_000)).astype(np.int32)
+    for bits in ("15,14", "12,12"):
+        block_bits(bits)
+        check(torch, n, src, dst, 20, gpr.FP32, spmv="blocked")
+
+
+def test_blocked_schedule_deterministic_and_switching(torch):
+    src, dst = gen.rmat_coo(40_000, 900_000, seed=7)
+    g = gpr.graph_build(src, dst, 40_000)
+    a = gpu_pr(torch, g, 30, spmv="blocked")
+    p = gpu_pr(torch, g, 30, spmv="pull")
+    b = gpu_pr(torch, g, 30, spmv="blocked")
+    assert (a == b).all()
+    assert l1(a, p) <= 2e-6
+    out = torch.empty(g.n, device="cuda")
+    with pytest.raises(gpr.GprError) as ei:  # both schedules at once
+        gpr._check(gpr.lib().pagerank(g.handle, 0.85, 3, gpr.FP32, gpr.SPMV_PULL | gpr.SPMV_BLOCKED,
+                                      out.data_ptr(), None, None))
+    assert ei.value.status == gpr.EINVAL
+
+
+@pytest.mark.parametrize("spmv", ["pull", "blocked"])
+def test_closed_forms_on_gpu(torch, spmv):
     N = 1000
     cyc = np.arange(N, dtype=np.int32)
     g = gpr.graph_build(torch.from_numpy(cyc).cuda(), torch.from_numpy((cyc + 1) % N).cuda(), N)
-    x = gpu_pr(torch, g, 50)
+    x = gpu_pr(torch, g, 50, spmv=spmv)
     assert np.abs(x - 1.0 / N).max() < 1e-9
     # out-star: hub 0 -> leaves, fixed point x_hub = 1 / (N + d)
     leaves = np.arange(1, N, dtype=np.int32)
     g = gpr.graph_build(torch.from_numpy(np.zeros_like(leaves)).cuda(), torch.from_numpy(leaves).cuda(), N)
-    x = gpu_pr(torch, g, 200)
+    x = gpu_pr(torch, g, 200, spmv=spmv)
     assert abs(x[0] - 1.0 / (N + 0.85)) < 1e-7
     # no edges at all: uniform
     z = torch.zeros(0, dtype=torch.int32, device="cuda")
     g = gpr.graph_build(z, z, 77)
-    x = gpu_pr(torch, g, 10)
+    x = gpu_pr(torch, g, 10, spmv=spmv)
     assert np.abs(x - 1.0 / 77).max() < 1e-9
 
 
