@@ -130,6 +130,27 @@ gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, 
 gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags,
                     float* x_out, gpr_stats* st, void* stream);
 
+/* ---- autotuner for the PageRank step ---------------------------------------
+ * pagerank_tune: times trial_steps steps (>= 1) of the pull schedule and of
+ * several shapes of the blocked schedule (source-block bits, bin bits,
+ * edges per work unit) on g, and keeps the fastest: later pagerank calls on
+ * g, and on graphs of the same shape (ceil log2 n, ceil log2 m, dt) in this
+ * process, use it unless flags force a schedule.  A pagerank call on a graph
+ * of at least 2^22 edges with no tuned choice for its shape runs this first,
+ * with 5 trial steps.  The workspace's rank vectors are overwritten.
+ * Synchronous.  out may be NULL. */
+typedef struct {
+  int32_t schedule;         /* GPR_SPMV_PULL or GPR_SPMV_BLOCKED */
+  int32_t sb_bits, w_bits;  /* blocked: log2 of the source-block and bin sizes (else 0) */
+  int64_t unit_edges;       /* blocked: edges per work unit (else 0) */
+  double ms_per_step;       /* the winner's device time per step */
+  double pull_ms_per_step;  /* the pull schedule's */
+  int32_t candidates;       /* schedules timed */
+} gpr_tune_result;
+
+gpr_status pagerank_tune(const gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out,
+                         void* stream);
+
 /* ---- batched personalised PageRank ---------------------------------------
  * Personalised PageRank (section 4 Table "snap_methods"; section 4,
  * "Fast Random Walk Algorithms": scores from the point of view of a given

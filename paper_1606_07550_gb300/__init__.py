@@ -101,6 +101,12 @@ class ServerStats(ctypes.Structure):
                                                "device_bytes_in_use")]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("sb_bits", ctypes.c_int32), ("w_bits", ctypes.c_int32),
+                ("unit_edges", ctypes.c_int64), ("ms_per_step", ctypes.c_double),
+                ("pull_ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
                 ("dangling", ctypes.c_double), ("t_setup_ms", ctypes.c_double), ("t_iter_ms", ctypes.c_double),
@@ -126,6 +132,7 @@ def lib():
         L.graph_export.argtypes = [_VP, _VP, _VP, _VP]
         L.pagerank.argtypes = [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int, ctypes.c_int, _VP,
                                ctypes.POINTER(Stats), _VP]
+        L.pagerank_tune.argtypes = [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult), _VP]
         L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                 ctypes.c_int, _VP]
         L.gpr_kernel_launches.restype = ctypes.c_int64
@@ -141,7 +148,7 @@ def lib():
         L.serve_destroy.argtypes = [_VP]
         L.pagerank_csc_noalloc.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _VP, _VP]
         L.pagerank_csc_noalloc.restype = ctypes.c_int
-        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "ppr_batch",
+        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "pagerank_tune", "ppr_batch",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
                      "serve_destroy", "serve_completed"):
             getattr(L, name).restype = ctypes.c_int
@@ -246,6 +253,14 @@ def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int =
     _check(lib().pagerank(g.handle, damping, iters, dtype, flags, po,
                           ctypes.byref(st) if st is not None else None, _stream_ptr(stream)))
     return st
+
+
+def pagerank_tune(g: Graph, dtype: int = FP32, trial_steps: int = 5, stream=None) -> TuneResult:
+    """Times the PageRank step's schedules on g and keeps the fastest for g
+    and for graphs of its shape (see pagerank_tune in include/gpr.h)."""
+    r = TuneResult()
+    _check(lib().pagerank_tune(g.handle, dtype, trial_steps, ctypes.byref(r), _stream_ptr(stream)))
+    return r
 
 
 def ppr_batch(requests, max_iters: int = 50, tol: float = 0.0, dtype: int = FP32, stream=None):

@@ -9,6 +9,7 @@ gpr_status build_graph(const int32_t* src, const int32_t* dst, int64_t m_raw, in
                        gpr_graph** out);
 gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
                         gpr_stats* st, cudaStream_t s);
+gpr_status run_pagerank_tune(gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out, cudaStream_t s);
 gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
                          cudaStream_t s);
 
@@ -136,6 +137,24 @@ gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype
     return GPR_EINVAL;
   }
   return run_pagerank(const_cast<gpr_graph*>(g), damping, iters, dt, flags, x_out, st, (cudaStream_t)stream);
+}
+
+gpr_status pagerank_tune(const gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out,
+                         void* stream) {
+  clear_error();
+  if (!g) {
+    set_error("pagerank_tune: NULL graph");
+    return GPR_EINVAL;
+  }
+  if (dt != GPR_FP32 && dt != GPR_BF16) {
+    set_error("pagerank_tune: unknown dtype %d", (int)dt);
+    return GPR_EINVAL;
+  }
+  if (trial_steps < 1 || trial_steps > 1000) {
+    set_error("pagerank_tune: trial_steps %d outside [1, 1000]", (int)trial_steps);
+    return GPR_EINVAL;
+  }
+  return run_pagerank_tune(const_cast<gpr_graph*>(g), dt, trial_steps, out, (cudaStream_t)stream);
 }
 
 gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,

@@ -41,7 +41,9 @@ namespace gpr {
 
 constexpr int kBkThreads = 1024;
 constexpr int kMaxUnitSegs = 1024;  // segments of one expand unit (one per thread in the prefix scan)
-constexpr int kChunk = 256;         // edges per warp step: 8 consecutive edges per lane
+constexpr int kChunk = 256;         // edges per warp step: two runs of 4 consecutive edges per lane
+constexpr int kMaxUnitChunks = (1 << 20) / kChunk + kMaxUnitSegs;  // chunks of one expand unit
+constexpr int kPad = kChunk;        // entries after the end of the edge arrays (whole chunks are copied)
 static_assert(kBkThreads == kMaxUnitSegs, "the segment scan gives one segment to each thread");
 
 // floor(v * 2^U) from the bits of v (v >= 0, v * 2^U < 2^63), integer
@@ -93,9 +95,32 @@ __device__ __forceinline__ float from_fixed(unsigned long long a, int U) {
 // the number of carries is floor(sum of low halves / 2^32), so hi:lo ends
 // as the exact sum.  The high atomic is skipped when it would add 0 (every
 // code below 2^31 without a carry).
+// qh plus the carry out of old + ql.
+__device__ __forceinline__ uint32_t carry_into(uint32_t old, uint32_t ql, uint32_t qh) {
+  uint32_t up;
+  asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, 0;\n\t}" : "=r"(up) : "r"(old), "r"(ql), "r"(qh));
+  return up;
+}
+// Predicated shared-memory additions at 32-bit shared addresses (no branch):
+// the low-word add returns the old value; the high-word add happens only
+// for a non-zero amount.
+__device__ __forceinline__ uint32_t atom_add_if(uint32_t addr, uint32_t v, bool on) {
+  uint32_t old = 0;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t@p atom.shared.add.u32 %0, [%1], %2;\n\t}"
+      : "+r"(old)
+      : "r"(addr), "r"(v), "r"((uint32_t)on)
+      : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_nonzero(uint32_t addr, uint32_t v) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr),
+               "r"(v)
+               : "memory");
+}
+
 __device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int32_t d, uint32_t ql, uint32_t qh) {
-  const uint32_t old = atomicAdd(lo + d, ql);
-  const uint32_t up = qh + (old + ql < old ? 1u : 0u);
+  const uint32_t up = carry_into(atomicAdd(lo + d, ql), ql, qh);
   if (up) atomicAdd(hi + d, up);
 }
 
@@ -148,20 +173,35 @@ __global__ void bk_transpose_kernel(const int32_t* __restrict__ seg, int32_t S, 
   }
 }
 
+// ---- asynchronous copies to shared memory (cp.async) ------------------------
+// Each lane copies exactly the bytes it later reads, so a wait on its own
+// copy groups is the only synchronisation the staged data needs.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---- expand ---------------------------------------------------------------
 
-// 8 consecutive edges with local sources packed in q: their codes to out.
-__device__ __forceinline__ void expand8(const uint32_t* s_code, uint4 q, uint32_t* out) {
-  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-  uint32_t v[8];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    v[2 * j] = s_code[w[j] & 0xFFFFu];
-    v[2 * j + 1] = s_code[w[j] >> 16];
-  }
-  reinterpret_cast<uint4*>(out)[0] = make_uint4(v[0], v[1], v[2], v[3]);
-  reinterpret_cast<uint4*>(out)[1] = make_uint4(v[4], v[5], v[6], v[7]);
+// Shared memory of the expand kernel: codes (4 << sb_bits bytes), segment
+// tables, the chunk map, then 16-byte-aligned per-warp staging slots.
+__host__ __device__ constexpr size_t expand_ids_offset(int sb_bits) {
+  return (((size_t)4 << sb_bits) + (size_t)(3 * kMaxUnitSegs + 1) * 4 + (size_t)kMaxUnitChunks * 2 + 15) & ~(size_t)15;
 }
+constexpr size_t kExpandStageBytes = (size_t)(kBkThreads / 32) * 128 * 8;
+// Shared memory of the accumulate kernel: two 32-bit words per row of the
+// bin, then per-warp staging slots (2 x (256 codes + 256 row ids)).
+constexpr size_t kAccumSlotBytes = kChunk * 4 + kChunk * 2;
+constexpr size_t kAccumStageBytes = (size_t)(kBkThreads / 32) * 2 * kAccumSlotBytes;
 
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -177,9 +217,12 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_expand_kernel(
   int32_t* s_pref = reinterpret_cast<int32_t*>(smem + (size_t)SB * 4);  // kMaxUnitSegs + 1
   int32_t* s_lo = s_pref + kMaxUnitSegs + 1;
   int32_t* s_hi = s_lo + kMaxUnitSegs;
+  uint16_t* s_map = reinterpret_cast<uint16_t*>(s_hi + kMaxUnitSegs);  // chunk -> segment, kMaxUnitChunks
+  uint2* s_ids = reinterpret_cast<uint2*>(smem + expand_ids_offset(sb_bits));  // per warp: 2 slots x 64 x 8 bytes
   __shared__ int32_t s_unit;
   __shared__ int32_t s_wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  uint2* w_ids = s_ids + warp * 128;
   for (;;) {
     __syncthreads();  // the previous unit is done with s_code and the segment tables
     if (tid == 0) s_unit = (int32_t)(atomicAdd(ctr, 1u) - epoch);
@@ -245,46 +288,65 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_expand_kernel(
     if (tid == blockDim.x - 1) s_pref[blockDim.x] = excl + chunks;
     __syncthreads();
     const int32_t total = s_pref[nseg];
-    // two chunks per warp step, both index loads issued before either is used
-    for (int32_t ch = warp; ch < total; ch += 2 * nwarps) {
-      int32_t g[2], lo[2], hi[2];
-      bool full[2];
-      uint4 q[2];
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int32_t c = ch + t * nwarps;
-        if (c >= total) {  // no second chunk: an empty range
-          g[t] = lo[t] = hi[t] = 0;
-          full[t] = false;
-          continue;
-        }
-        int k0 = 0, k1 = nseg - 1;  // the last segment whose first chunk is <= c
-        while (k0 < k1) {
-          const int mid = (k0 + k1 + 1) >> 1;
-          if (s_pref[mid] <= c)
-            k0 = mid;
-          else
-            k1 = mid - 1;
-        }
-        lo[t] = s_lo[k0];
-        hi[t] = s_hi[k0];
-        g[t] = (lo[t] / kChunk + (c - s_pref[k0])) * kChunk + 8 * lane;
-        full[t] = g[t] >= lo[t] && g[t] + 8 <= hi[t];
-        if (full[t]) q[t] = __ldcs(reinterpret_cast<const uint4*>(src_lo + g[t]));
+    // the segment of every chunk, found once per chunk by all threads
+    for (int32_t c = tid; c < total; c += blockDim.x) {
+      int k0 = 0, k1 = nseg - 1;  // the last segment whose first chunk is <= c
+      while (k0 < k1) {
+        const int mid = (k0 + k1 + 1) >> 1;
+        if (s_pref[mid] <= c)
+          k0 = mid;
+        else
+          k1 = mid - 1;
       }
+      s_map[c] = (uint16_t)k0;
+    }
+    __syncthreads();
+    // a warp takes chunks warp, warp + nwarps, ...; lane l handles edges
+    // 4l..4l+3 and 128+4l..128+4l+3 of a chunk, whose 16-bit source ids it
+    // copies into its slot while the previous chunk is expanded
+    int32_t base = 0, lo = 0, hi = 0;
+    auto locate = [&](int32_t c, int32_t& b, int32_t& l, int32_t& h) {
+      const int k = s_map[c];
+      l = s_lo[k];
+      h = s_hi[k];
+      b = (l / kChunk + (c - s_pref[k])) * kChunk;
+    };
+    auto stage = [&](int slot, int32_t b) {
+      cp_async8(w_ids + slot * 64 + lane, src_lo + b + 4 * lane);
+      cp_async8(w_ids + slot * 64 + 32 + lane, src_lo + b + 128 + 4 * lane);
+    };
+    if (warp < total) {
+      locate(warp, base, lo, hi);
+      stage(0, base);
+    }
+    cp_async_commit();
+    int slot = 0;
+    for (int32_t ch = warp; ch < total; ch += nwarps, slot ^= 1) {
+      int32_t nbase = 0, nlo = 0, nhi = 0;
+      if (ch + nwarps < total) {
+        locate(ch + nwarps, nbase, nlo, nhi);
+        stage(slot ^ 1, nbase);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();  // this lane's copies for the current chunk are in
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        if (full[t]) {
-          expand8(s_code, q[t], vals + g[t]);
+      for (int h = 0; h < 2; ++h) {
+        const uint2 q = w_ids[slot * 64 + h * 32 + lane];
+        const int32_t g = base + h * 128 + 4 * lane;
+        const uint32_t id[4] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16};
+        if (g >= lo && g + 4 <= hi) {
+          *reinterpret_cast<uint4*>(vals + g) = make_uint4(s_code[id[0]], s_code[id[1]], s_code[id[2]], s_code[id[3]]);
         } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int32_t e = g[t] + j;
-            if (e >= lo[t] && e < hi[t]) vals[e] = s_code[src_lo[e]];
-          }
+          for (int j = 0; j < 4; ++j)
+            if (g + j >= lo && g + j < hi) vals[g + j] = s_code[id[j]];
         }
       }
+      base = nbase;
+      lo = nlo;
+      hi = nhi;
     }
+    cp_async_wait<0>();
   }
 }
 
@@ -303,7 +365,10 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
   const int32_t W = 1 << w_bits;
   uint32_t* s_lo = s_acc32;
   uint32_t* s_hi = s_acc32 + W;
+  const uint32_t a_lo = (uint32_t)__cvta_generic_to_shared(s_lo), a_hi = (uint32_t)__cvta_generic_to_shared(s_hi);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  // this warp's two staging slots: 256 codes, then 256 row ids
+  unsigned char* w_stage = reinterpret_cast<unsigned char*>(s_acc32 + 2 * W) + (size_t)warp * 2 * kAccumSlotBytes;
   for (;;) {
     __syncthreads();
     if (tid == 0) s_unit = (int32_t)(atomicAdd(ctr + 1, 1u) - epoch);
@@ -315,28 +380,40 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
     const int32_t nv = min(W, n - v0);
     for (int32_t i = tid; i < nv; i += blockDim.x) s_lo[i] = s_hi[i] = 0u;
     __syncthreads();
-    for (int32_t base = (un.lo & ~(kChunk - 1)) + warp * kChunk; base < un.hi; base += nwarps * kChunk) {
-      const int32_t g0 = base + 8 * lane;
-      uint32_t w[8];
-      int32_t d[8];
-      if (g0 >= un.lo && g0 + 8 <= un.hi) {
-        const uint4 wa = __ldcs(reinterpret_cast<const uint4*>(vals + g0));
-        const uint4 wb = __ldcs(reinterpret_cast<const uint4*>(vals + g0) + 1);
-        w[0] = wa.x, w[1] = wa.y, w[2] = wa.z, w[3] = wa.w;
-        w[4] = wb.x, w[5] = wb.y, w[6] = wb.z, w[7] = wb.w;
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(dst_lo + g0));
-        const uint32_t r[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          d[2 * j] = (int32_t)(r[j] & 0xFFFFu);
-          d[2 * j + 1] = (int32_t)(r[j] >> 16);
-        }
-      } else {
+    // lane l handles edges 4l..4l+3 and 128+4l..128+4l+3 of each 256-edge
+    // chunk; it copies exactly those codes and row ids into its slot while
+    // the previous chunk is added
+    auto stage = [&](int slot, int32_t b) {
+      unsigned char* st = w_stage + slot * kAccumSlotBytes;
+      cp_async16(st + 16 * lane, vals + b + 4 * lane);
+      cp_async16(st + 512 + 16 * lane, vals + b + 128 + 4 * lane);
+      cp_async8(st + 1024 + 8 * lane, dst_lo + b + 4 * lane);
+      cp_async8(st + 1280 + 8 * lane, dst_lo + b + 128 + 4 * lane);
+    };
+    const int32_t first = (un.lo & ~(kChunk - 1)) + warp * kChunk;
+    if (first < un.hi) stage(0, first);
+    cp_async_commit();
+    int slot = 0;
+    for (int32_t base = first; base < un.hi; base += nwarps * kChunk, slot ^= 1) {
+      if (base + nwarps * kChunk < un.hi) stage(slot ^ 1, base + nwarps * kChunk);
+      cp_async_commit();
+      cp_async_wait<1>();  // this lane's copies for the current chunk are in
+      const unsigned char* st = w_stage + slot * kAccumSlotBytes;
+      const uint4 wa = *reinterpret_cast<const uint4*>(st + 16 * lane);
+      const uint4 wb = *reinterpret_cast<const uint4*>(st + 512 + 16 * lane);
+      const uint2 ra = *reinterpret_cast<const uint2*>(st + 1024 + 8 * lane);
+      const uint2 rb = *reinterpret_cast<const uint2*>(st + 1280 + 8 * lane);
+      uint32_t w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+      int32_t d[8] = {(int32_t)(ra.x & 0xFFFFu), (int32_t)(ra.x >> 16), (int32_t)(ra.y & 0xFFFFu), (int32_t)(ra.y >> 16),
+                      (int32_t)(rb.x & 0xFFFFu), (int32_t)(rb.x >> 16), (int32_t)(rb.y & 0xFFFFu), (int32_t)(rb.y >> 16)};
+      if (base < un.lo || base + kChunk > un.hi) {  // a boundary chunk: edges outside the unit are not added here
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const bool ok = g0 + j >= un.lo && g0 + j < un.hi;
-          w[j] = ok ? vals[g0 + j] : 0u;
-          d[j] = ok ? (int32_t)dst_lo[g0 + j] : -1;
+          const int32_t e = base + (j < 4 ? 4 * lane + j : 128 + 4 * lane + j - 4);
+          if (e < un.lo || e >= un.hi) {
+            w[j] = 0u;
+            d[j] = -1;
+          }
         }
       }
       // values: codes below 2^31 are the value; the rest are converted
@@ -351,42 +428,51 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
 #pragma unroll
         for (int j = 0; j < 8; ++j) q[j] = value_of(w[j], U);
       }
-      // runs of equal rows are folded into their first edge (backward, so a
-      // head holds its whole run: consecutive edges of one row would
-      // otherwise meet in one atomic instruction)
+      // runs of equal rows within each group of 4 consecutive edges are
+      // folded into their first edge (backward, so a head holds its whole
+      // run: consecutive edges of one row would otherwise meet in one
+      // atomic instruction); skipped when the warp step has no such pair
+      bool dup = false;
 #pragma unroll
-      for (int j = 6; j >= 0; --j) {
-        if (d[j] >= 0 && d[j] == d[j + 1]) {
-          q[j] += q[j + 1];
-          d[j + 1] = -1;
+      for (int j = 0; j < 7; ++j)
+        if (j != 3) dup = dup || (d[j] >= 0 && d[j] == d[j + 1]);
+      bool whole = false;
+      int32_t c0 = -1;
+      if (__any_sync(0xffffffffu, dup)) {
+#pragma unroll
+        for (int j = 6; j >= 0; --j) {
+          if (j != 3 && d[j] >= 0 && d[j] == d[j + 1]) {
+            q[j] += q[j + 1];
+            d[j + 1] = -1;
+          }
         }
-      }
-      // a warp step inside one row (long rows): one shared-memory addition
-      const int32_t c0 = __shfl_sync(0xffffffffu, d[0], 0);
-      bool one = d[0] >= 0 && d[0] == c0;
+        // a warp step inside one row (long rows): one shared-memory addition
+        c0 = __shfl_sync(0xffffffffu, d[0], 0);
+        bool one = d[0] >= 0 && d[0] == c0 && d[4] == c0;
 #pragma unroll
-      for (int j = 1; j < 8; ++j) one = one && d[j] < 0;
-      if (__all_sync(0xffffffffu, one)) {
-        unsigned long long r = q[0];
+        for (int j = 1; j < 8; ++j)
+          if (j != 4) one = one && d[j] < 0;
+        whole = __all_sync(0xffffffffu, one);
+      }
+      if (whole) {
+        unsigned long long r = q[0] + q[4];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
         if (lane == 0) acc_add(s_lo, s_hi, c0, (uint32_t)r, (uint32_t)(r >> 32));
       } else {
         // every head's low word with independent atomics, then the carries
+        // (predicated: no branches)
         uint32_t old[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (d[j] >= 0) old[j] = atomicAdd(s_lo + d[j], (uint32_t)q[j]);
+        for (int j = 0; j < 8; ++j) old[j] = atom_add_if(a_lo + 4u * (uint32_t)d[j], (uint32_t)q[j], d[j] >= 0);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          if (d[j] >= 0) {
-            const uint32_t ql = (uint32_t)q[j];
-            const uint32_t up = (uint32_t)(q[j] >> 32) + (old[j] + ql < old[j] ? 1u : 0u);
-            if (up) atomicAdd(s_hi + d[j], up);
-          }
+          const uint32_t up = carry_into(old[j], (uint32_t)q[j], (uint32_t)(q[j] >> 32));
+          red_add_nonzero(a_hi + 4u * (uint32_t)d[j], d[j] >= 0 ? up : 0u);
         }
       }
     }
+    cp_async_wait<0>();
     __syncthreads();
     if (un.nparts > 1) {
       unsigned long long* g = acc_g + (int64_t)un.split * W;
@@ -451,8 +537,8 @@ static int smem_optin() {
   return optin;
 }
 
-static size_t expand_smem(int sb_bits) { return ((size_t)4 << sb_bits) + (size_t)(3 * kMaxUnitSegs + 1) * 4; }
-static size_t accum_smem(int w_bits) { return (size_t)8 << w_bits; }
+static size_t expand_smem(int sb_bits) { return expand_ids_offset(sb_bits) + kExpandStageBytes; }
+static size_t accum_smem(int w_bits) { return ((size_t)8 << w_bits) + kAccumStageBytes; }
 
 bool blocked_eligible(const gpr_graph* g, int sb_bits, int w_bits) {
   if (sb_bits < 4 || sb_bits > 16 || w_bits < 4 || w_bits > 16) return false;
@@ -464,8 +550,8 @@ bool blocked_eligible(const gpr_graph* g, int sb_bits, int w_bits) {
   const int kbits = segment_key_bits(nseg);
   if (kbits + sb_bits + w_bits > 64) return false;
   const size_t optin = (size_t)smem_optin();
-  // static shared memory of the kernels is below 1 KB
-  return expand_smem(sb_bits) + 1024 <= optin && accum_smem(w_bits) + 1024 <= optin;
+  // static shared memory of the kernels is below 2 KB
+  return expand_smem(sb_bits) + 2048 <= optin && accum_smem(w_bits) + 2048 <= optin;
 }
 
 void blocked_free(Blocked* k, cudaStream_t s) {
@@ -517,10 +603,14 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
   int32_t* seg = nullptr;
   int* derr = nullptr;
   try {
-    const size_t me = (size_t)std::max<int64_t>(m, 1);
+    // whole 256-edge chunks are copied: kPad entries past the end, zeroed
+    const size_t me = (size_t)m + kPad;
     k->src_lo = (uint16_t*)dalloc(me * 2, s);
     k->dst_lo = (uint16_t*)dalloc(me * 2, s);
     k->vals = (uint32_t*)dalloc(me * 4, s);
+    GPR_CUDA(cudaMemsetAsync(k->src_lo + m, 0, kPad * 2, s));
+    GPR_CUDA(cudaMemsetAsync(k->dst_lo + m, 0, kPad * 2, s));
+    GPR_CUDA(cudaMemsetAsync(k->vals + m, 0, kPad * 4, s));
     seg = (int32_t*)dalloc((size_t)(nseg + 1) * 4, s);
     derr = (int*)dalloc(sizeof(int) * 2, s);
     GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));

@@ -22,6 +22,9 @@
 // kernel.  The bucket kernels of a step are independent and run as parallel
 // branches of one CUDA graph that holds the whole iteration loop.
 #include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -273,6 +276,13 @@ struct LaunchShape {
   int partial_off;
 };
 
+// A schedule with, for the blocked one, its shape.
+struct Choice {
+  int sched = kSchedPull;
+  int sb = 15, wb = 14;   // source-block and bin bits
+  int64_t unit = 1 << 16; // edges per work unit
+};
+
 struct PagerankWork {
   int device = 0;
   float* x[2] = {nullptr, nullptr};  // n floats each: the rank vector, always FP32
@@ -297,6 +307,8 @@ struct PagerankWork {
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kMaxBuckets] = {};
   Blocked* blk = nullptr;  // the blocked schedule's edge layout, made on first use
+  bool tuned = false;      // `choice` was measured on this graph
+  Choice choice;
   cudaGraphExec_t exec = nullptr;
   int32_t exec_iters = -1;
   int exec_dt = -1;
@@ -500,39 +512,191 @@ static PagerankWork* work_make(gpr_graph* g, cudaStream_t s) {
   }
 }
 
-// Shape of the blocked schedule: GPR_BLOCK_BITS="sb,w[,u]" (source block
-// and bin bits, log2 of the edges per work unit), else 2^15-node source
-// blocks, 2^14-row bins and units of about m / 2048 edges, between 2^16 and
-// 2^20, so every SM gets several units.
-static void block_bits(const gpr_graph* g, int* sb, int* wb, int64_t* unit) {
-  *sb = 15;
-  *wb = 14;
+// ---- schedule choice and the autotuner ----------------------------------------
+
+// Units of about m / 2048 edges, between 2^16 and 2^20: every SM gets several.
+static int64_t default_unit(const gpr_graph* g) {
   int64_t u = 1 << 16;
   while (u < (1 << 20) && u * 2048 < g->m) u <<= 1;
-  *unit = u;
-  if (const char* e = getenv("GPR_BLOCK_BITS")) {
-    int a = 0, b = 0, c = 0;
-    const int k = sscanf(e, "%d,%d,%d", &a, &b, &c);
-    if (k >= 2) {
-      *sb = a;
-      *wb = b;
-    }
-    if (k == 3 && c >= 12 && c <= 30) *unit = (int64_t)1 << c;
+  return u;
+}
+
+// GPR_BLOCK_BITS="sb,w[,log2 unit]" overrides the blocked shape (tests,
+// experiments); returns false if unset.
+static bool env_block_shape(Choice* c) {
+  const char* e = getenv("GPR_BLOCK_BITS");
+  if (!e) return false;
+  int a = 0, b = 0, u = 0;
+  const int k = sscanf(e, "%d,%d,%d", &a, &b, &u);
+  if (k < 2) return false;
+  c->sb = a;
+  c->wb = b;
+  if (k == 3 && u >= 12 && u <= 30) c->unit = (int64_t)1 << u;
+  return true;
+}
+
+// Tuned choices by graph shape (ceil log2 n, ceil log2 m, storage type):
+// graphs of one shape reuse the first one's measurement.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, Choice> g_tuned;
+
+static int ceil_log2(int64_t v) {
+  int b = 0;
+  while (((int64_t)1 << b) < v) ++b;
+  return b;
+}
+static std::tuple<int, int, int> shape_key(const gpr_graph* g, gpr_dtype dt) {
+  return std::make_tuple(ceil_log2(g->n), ceil_log2(std::max<int64_t>(g->m, 1)), (int)dt);
+}
+
+// Graphs below this many edges are launch- and latency-bound: the pull
+// schedule, without tuning.
+constexpr int64_t kTuneMinEdges = 1 << 22;
+
+static void drop_exec(PagerankWork* w) {
+  if (w->exec) {
+    cudaGraphExecDestroy(w->exec);
+    w->exec = nullptr;
   }
 }
 
-// The schedule of a call: forced by flags, else GPR_SPMV=pull|blocked,
-// else pull.
-static int pick_schedule(const gpr_graph* g, int flags) {
-  if (flags & GPR_SPMV_PULL) return kSchedPull;
-  if (flags & GPR_SPMV_BLOCKED) return kSchedBlocked;
-  if (const char* e = getenv("GPR_SPMV")) {
-    int sb, wb;
-    int64_t ue;
-    block_bits(g, &sb, &wb, &ue);
-    if (!strcmp(e, "blocked") && blocked_eligible(g, sb, wb)) return kSchedBlocked;
+// The blocked layout of shape c (rebuilt if another shape is held).
+static void ensure_layout(gpr_graph* g, PagerankWork* w, const Choice& c, cudaStream_t s) {
+  if (w->blk && (w->blk->sb_bits != c.sb || w->blk->w_bits != c.wb || w->blk->unit_edges != c.unit)) {
+    drop_exec(w);
+    GPR_CUDA(cudaStreamSynchronize(s));
+    blocked_free(w->blk, s);
+    w->blk = nullptr;
   }
-  return kSchedPull;
+  if (!w->blk) w->blk = blocked_build(g, c.sb, c.wb, c.unit, s);
+}
+
+// The iteration loop of `iters` steps with schedule `sched`, as a CUDA graph.
+static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype dt, int sched, cudaStream_t s) {
+  if (w->log_cap < iters + 1) {
+    dfree(w->log, s);
+    w->log = nullptr;
+    w->log_cap = 0;
+    const int32_t cap = std::max(iters + 1, 128);
+    w->log = (double*)dalloc((size_t)cap * 3 * sizeof(double), s);
+    w->log_cap = cap;
+    drop_exec(w);
+  }
+  if (w->exec && w->exec_iters == iters && w->exec_dt == (int)dt && w->exec_sched == sched) return;
+  drop_exec(w);
+  // the capture stream must see the allocations made on `s`
+  GPR_CUDA(cudaStreamSynchronize(s));
+  cudaGraph_t graph = nullptr;
+  GPR_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
+  try {
+    if (dt == GPR_BF16)
+      record_iterations<__nv_bfloat16>(g, w, iters, sched);
+    else
+      record_iterations<float>(g, w, iters, sched);
+  } catch (...) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(w->cap, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    throw;
+  }
+  cudaError_t e = cudaStreamEndCapture(w->cap, &graph);
+  if (e != cudaSuccess) throw CudaFail{e, "cudaStreamEndCapture"};
+  e = cudaGraphInstantiate(&w->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    w->exec = nullptr;
+    throw CudaFail{e, "cudaGraphInstantiate"};
+  }
+  w->exec_iters = iters;
+  w->exec_dt = (int)dt;
+  w->exec_sched = sched;
+  w->exec_kernels = sched == kSchedBlocked ? 2 + (int64_t)iters * 2
+                                           : 2 + (int64_t)iters * (g->plan.nbuckets + 1 + (w->hot_grid > 0 ? 1 : 0));
+}
+
+// Device time of `iters` steps of schedule c, after one untimed run.
+static double time_choice(gpr_graph* g, PagerankWork* w, const Choice& c, int32_t iters, gpr_dtype dt,
+                          cudaStream_t s) {
+  if (c.sched == kSchedBlocked) ensure_layout(g, w, c, s);
+  ensure_exec(g, w, iters, dt, c.sched, s);
+  const StepParams hp{0.f, 0.f, 0.85, (double)g->n};
+  float best = 0.f;
+  for (int rep = 0; rep < 2; ++rep) {
+    GPR_CUDA(cudaMemcpyAsync(w->prm, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    GPR_CUDA(cudaEventRecord(w->ev_t0, s));
+    GPR_CUDA(cudaGraphLaunch(w->exec, s));
+    GPR_CUDA(cudaEventRecord(w->ev_t1, s));
+    count_launches(w->exec_kernels);
+    GPR_CUDA(cudaStreamSynchronize(s));
+    GPR_CUDA(cudaEventElapsedTime(&best, w->ev_t0, w->ev_t1));
+  }
+  return best;
+}
+
+// Times the pull schedule and blocked shapes on g (trial_steps steps each),
+// keeps the fastest for g and for its shape.  Lock held.
+static Choice tune(gpr_graph* g, PagerankWork* w, gpr_dtype dt, int32_t trial_steps, cudaStream_t s,
+                   gpr_tune_result* out) {
+  std::vector<Choice> cands;
+  cands.push_back(Choice{});  // pull
+  const int64_t u = default_unit(g);
+  const int shapes[][2] = {{15, 14}, {14, 14}, {15, 13}, {13, 13}};
+  for (const auto& sh : shapes)
+    for (int64_t uu : {u, std::max<int64_t>(u / 4, 1 << 14)}) {
+      Choice c{kSchedBlocked, sh[0], sh[1], uu};
+      if (blocked_eligible(g, c.sb, c.wb)) cands.push_back(c);
+    }
+  Choice best;
+  double best_ms = 0.0, pull_ms = 0.0;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const double ms = time_choice(g, w, cands[i], trial_steps, dt, s) / std::max(trial_steps, 1);
+    if (i == 0) pull_ms = ms;
+    if (i == 0 || ms < best_ms) {
+      best = cands[i];
+      best_ms = ms;
+    }
+  }
+  w->tuned = true;
+  w->choice = best;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[shape_key(g, dt)] = best;
+  }
+  if (out) {
+    out->schedule = best.sched == kSchedBlocked ? GPR_SPMV_BLOCKED : GPR_SPMV_PULL;
+    out->sb_bits = best.sched == kSchedBlocked ? best.sb : 0;
+    out->w_bits = best.sched == kSchedBlocked ? best.wb : 0;
+    out->unit_edges = best.sched == kSchedBlocked ? best.unit : 0;
+    out->ms_per_step = best_ms;
+    out->pull_ms_per_step = pull_ms;
+    out->candidates = (int32_t)cands.size();
+  }
+  return best;
+}
+
+// The schedule of a call: forced by flags (blocked with the tuned or default
+// shape), else GPR_SPMV=pull|blocked, else the graph's tuned choice, else
+// the choice tuned for its shape, else (graphs of at least kTuneMinEdges
+// edges) tuned now, else pull.
+static Choice pick(gpr_graph* g, PagerankWork* w, int flags, gpr_dtype dt, cudaStream_t s) {
+  Choice blocked{kSchedBlocked, 15, 14, default_unit(g)};
+  if (w->tuned && w->choice.sched == kSchedBlocked) blocked = w->choice;
+  const bool env_shape = env_block_shape(&blocked);
+  if (flags & GPR_SPMV_PULL) return Choice{};
+  if (flags & GPR_SPMV_BLOCKED) return blocked;
+  if (const char* e = getenv("GPR_SPMV")) {
+    if (!strcmp(e, "blocked") && blocked_eligible(g, blocked.sb, blocked.wb)) return blocked;
+    if (!strcmp(e, "pull")) return Choice{};
+  }
+  if (env_shape && blocked_eligible(g, blocked.sb, blocked.wb)) return blocked;
+  if (w->tuned) return w->choice;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(shape_key(g, dt));
+    if (it != g_tuned.end()) return it->second;
+  }
+  if (g->m >= kTuneMinEdges) return tune(g, w, dt, 5, s, nullptr);
+  return Choice{};
 }
 
 gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
@@ -542,71 +706,12 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
     const auto t_setup0 = std::chrono::steady_clock::now();
     if (!g->work) g->work = work_make(g, s);
     PagerankWork* w = g->work;
-    const int sched = pick_schedule(g, flags);
-    if (sched == kSchedBlocked) {
-      int sb, wb;
-      int64_t ue;
-      block_bits(g, &sb, &wb, &ue);
-      if (w->blk && (w->blk->sb_bits != sb || w->blk->w_bits != wb || w->blk->unit_edges != ue)) {
-        if (w->exec) {
-          cudaGraphExecDestroy(w->exec);
-          w->exec = nullptr;
-        }
-        GPR_CUDA(cudaStreamSynchronize(s));
-        blocked_free(w->blk, s);
-        w->blk = nullptr;
-      }
-      if (!w->blk) w->blk = blocked_build(g, sb, wb, ue, s);
-    }
-    if (w->log_cap < iters + 1) {
-      dfree(w->log, s);
-      w->log = nullptr;
-      w->log_cap = 0;
-      const int32_t cap = std::max(iters + 1, 128);
-      w->log = (double*)dalloc((size_t)cap * 3 * sizeof(double), s);
-      w->log_cap = cap;
-      if (w->exec) {
-        cudaGraphExecDestroy(w->exec);
-        w->exec = nullptr;
-      }
-    }
+    const Choice ch = pick(g, w, flags, dt, s);
+    const int sched = ch.sched;
+    if (sched == kSchedBlocked) ensure_layout(g, w, ch, s);
+    ensure_exec(g, w, iters, dt, sched, s);
     StepParams hp{0.f, 0.f, damping, (double)g->n};
     GPR_CUDA(cudaMemcpyAsync(w->prm, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
-    if (!w->exec || w->exec_iters != iters || w->exec_dt != (int)dt || w->exec_sched != sched) {
-      if (w->exec) {
-        cudaGraphExecDestroy(w->exec);
-        w->exec = nullptr;
-      }
-      // the capture stream must see the allocations made on `s`
-      GPR_CUDA(cudaStreamSynchronize(s));
-      cudaGraph_t graph = nullptr;
-      GPR_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
-      try {
-        if (dt == GPR_BF16)
-          record_iterations<__nv_bfloat16>(g, w, iters, sched);
-        else
-          record_iterations<float>(g, w, iters, sched);
-      } catch (...) {
-        cudaGraph_t junk = nullptr;
-        cudaStreamEndCapture(w->cap, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        throw;
-      }
-      cudaError_t e = cudaStreamEndCapture(w->cap, &graph);
-      if (e != cudaSuccess) throw CudaFail{e, "cudaStreamEndCapture"};
-      e = cudaGraphInstantiate(&w->exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) {
-        w->exec = nullptr;
-        throw CudaFail{e, "cudaGraphInstantiate"};
-      }
-      w->exec_iters = iters;
-      w->exec_dt = (int)dt;
-      w->exec_sched = sched;
-      w->exec_kernels = sched == kSchedBlocked
-                            ? 2 + (int64_t)iters * 2
-                            : 2 + (int64_t)iters * (g->plan.nbuckets + 1 + (w->hot_grid > 0 ? 1 : 0));
-    }
     const double t_setup =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_setup0).count();
     if (st) GPR_CUDA(cudaEventRecord(w->ev_t0, s));
@@ -649,6 +754,23 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
   } catch (const CudaFail& f) {
     cudaGetLastError();
     set_error("pagerank: %s failed: %s", f.what, cudaGetErrorString(f.err));
+    return GPR_ECUDA;
+  }
+}
+
+gpr_status run_pagerank_tune(gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out,
+                             cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g->mu);
+  try {
+    if (!g->work) g->work = work_make(g, s);
+    tune(g, g->work, dt, trial_steps, s, out);
+    return GPR_OK;
+  } catch (const StatusFail& f) {
+    set_error("pagerank_tune: %s", f.msg.c_str());
+    return f.st;
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    set_error("pagerank_tune: %s failed: %s", f.what, cudaGetErrorString(f.err));
     return GPR_ECUDA;
   }
 }

@@ -249,8 +249,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
     const int32_t h0 = lower_bound_i32(J->heavy_rows, J->n_heavy, r0);
     const int32_t h1 = lower_bound_i32(J->heavy_rows, J->n_heavy, r1);
     const int32_t heavy_deg = J->heavy_deg;
-    int32_t wr0, wr1;
-    warp_rows(col_ptr, r0, r1, warp, wr0, wr1);
 
     // column records
     if (tid < kPprCols) {
@@ -320,8 +318,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         c.k1 = hash32(s_key[k1] ^ hash32((uint32_t)s_iters[k1] + 0x632BE5ABu));
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-      // light rows: one warp per row, each warp over its balanced range
-      for (int32_t p = wr0; p < wr1; ++p) {
+      // light rows: one warp per row, round-robin (neighbouring rows share
+      // sources, so warps that walk them together share cache lines)
+      for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
         const float2 xo = ld_state(X, p, lane);
@@ -612,7 +611,7 @@ __global__ void part_bounds_kernel(const int32_t* __restrict__ col_ptr, int32_t 
 
 // ---- host side ----------------------------------------------------------------
 
-static int g_cluster_size = 4;
+static int g_cluster_size = 8;
 
 int ppr_cluster_size() { return g_cluster_size; }
 

@@ -156,6 +156,32 @@ def test_blocked_schedule_deterministic_and_switching(torch):
     assert ei.value.status == gpr.EINVAL
 
 
+def test_tuner_records_its_choice_for_the_graph_and_its_shape(torch):
+    # 2^18 nodes, 2^23 raw edges: above the size at which pagerank tunes
+    n, m_raw = 1 << 18, 1 << 23
+    src, dst = gen.rmat_coo(n, m_raw, seed=41)
+    g = gpr.graph_build(src, dst, n)
+    r = gpr.pagerank_tune(g, trial_steps=3)
+    assert r.schedule in (gpr.SPMV_PULL, gpr.SPMV_BLOCKED)
+    assert r.candidates >= 2 and r.ms_per_step > 0 and r.pull_ms_per_step >= r.ms_per_step
+    if r.schedule == gpr.SPMV_BLOCKED:
+        assert 4 <= r.sb_bits <= 16 and 4 <= r.w_bits <= 16 and r.unit_edges > 0
+    x, st = gpu_pr(torch, g, 30, stats=True)
+    assert st.schedule == r.schedule
+    ref_g = oracle.build_csc(n, src, dst)
+    assert l1(x, oracle.pagerank(ref_g, 0.85, 30)) <= 1e-5
+    # another graph of the same shape takes the recorded choice without timing
+    src2, dst2 = gen.rmat_coo(n, m_raw, seed=42)
+    g2 = gpr.graph_build(src2, dst2, n)
+    x2, st2 = gpu_pr(torch, g2, 30, stats=True)
+    assert st2.schedule == r.schedule
+    assert l1(x2, oracle.pagerank(oracle.build_csc(n, src2, dst2), 0.85, 30)) <= 1e-5
+    for bad in (0, 1001):
+        with pytest.raises(gpr.GprError) as ei:
+            gpr.pagerank_tune(g, trial_steps=bad)
+        assert ei.value.status == gpr.EINVAL
+
+
 @pytest.mark.parametrize("spmv", ["pull", "blocked"])
 def test_closed_forms_on_gpu(torch, spmv):
     N = 1000
