@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--serve-warmup", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--pool", type=int, default=256)
+    ap.add_argument("--stable-rates", default="", help="serve: lower request rates to find the max stable load")
+    ap.add_argument("--stable-seconds", type=float, default=20.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--spmv", choices=["auto", "pull", "blocked"], default="auto",
                     help="schedule of the PageRank step (auto: the library's choice)")
@@ -271,6 +273,7 @@ def run_gpr(args, world, rank, local):
 
     stream = torch.cuda.current_stream()
     src, dst = make_coo_device(torch, spec)
+    m_raw = int(src.numel())  # the raw stream (G(n,m) draws until m distinct edges)
     out = torch.empty(spec.n, dtype=torch.float32, device="cuda")
     L = gpr.lib()
 
@@ -337,8 +340,8 @@ def run_gpr(args, world, rank, local):
     # of the ranks inside the timed region
     e2e = None
     if args.e2e_steps > 0:
-        hs = torch.empty(spec.m, dtype=torch.int32, pin_memory=True)
-        hd = torch.empty(spec.m, dtype=torch.int32, pin_memory=True)
+        hs = torch.empty(m_raw, dtype=torch.int32, pin_memory=True)
+        hd = torch.empty(m_raw, dtype=torch.int32, pin_memory=True)
         hs.copy_(src)
         hd.copy_(dst)
         hout = torch.empty(n, dtype=torch.float32, pin_memory=True)
@@ -358,7 +361,7 @@ def run_gpr(args, world, rank, local):
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
         t_e2e = max_over_ranks(world, t_e2e)
         e2e = {"value": edges_all * iters / t_e2e / 1e9, "unit": "GTEPS",
-               "h2d_bytes_per_step": 8 * spec.m, "d2h_bytes_per_step": 4 * n, "ms_per_step": t_e2e * 1e3}
+               "h2d_bytes_per_step": 8 * m_raw, "d2h_bytes_per_step": 4 * n, "ms_per_step": t_e2e * 1e3}
 
     if rank != 0:
         return
@@ -367,17 +370,17 @@ def run_gpr(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": t_step_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {
-            "workload": spec.name, "n": n, "m_raw": spec.m, "m": m, "iters": iters, "damping": DAMPING,
+            "workload": spec.name, "n": n, "m_raw": m_raw, "m": m, "iters": iters, "damping": DAMPING,
             "step": "graph_build (COO resident in HBM) + PageRank iterations + rank write-back",
             "value_counts": "m * iters / (build + iterate) per step",
-            "l2": "inputs larger than L2 (COO 8 GiB, CSC 4 GiB per replica)" if spec.m > (1 << 25) else
+            "l2": "inputs larger than L2 (COO 8 GiB, CSC 4 GiB per replica)" if m_raw > (1 << 25) else
                   "small graph: L2-resident (launch-bound)",
             "parallelism": f"replicas x{world}",
         },
         "build_ms": t_build, "iterate_ms": t_iter, "pagerank_gteps": pr_gteps,
         "schedule": schedule, "iteration_loop_ms": t_loop, "pagerank_setup_host_ms": t_setup,
         "loop_gteps": m * iters / (t_loop * 1e-3) / 1e9,
-        "build_edges_per_s": spec.m / (t_build * 1e-3),
+        "build_edges_per_s": m_raw / (t_build * 1e-3),
         "roofline": {
             "kernel": ("PageRank iteration loop (bucketed pull SpMV + fused step + fold)" if schedule == "pull"
                        else "PageRank iteration loop (blocked expand + accumulate + fused step + fold)"),
@@ -509,34 +512,13 @@ def run_batched(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def run_serve(args, world, rank, local):
-    """Config: a resident pool of 256 R-MAT graphs (scales 14-22, edge factor
-    16); Poisson arrivals at 2,000 requests/s, each naming a graph, 1-64 seeds,
-    damping in [0.80, 0.90] and tolerance 1e-6 or 1e-3 (BF16 contributions for
-    half of the 1e-3 requests); admission under a 40 GB device budget that
-    includes the pool.  Reports submit-to-completion p50/p99 over the requests
-    that arrived in the measured window, solves/s completed in the window (one
-    seed = one solve), rejections and the backlog.  Baseline on the same GPU:
-    one-at-a-time plain PageRank, one call per solve with the step count the
-    request needed, on a sample of the trace."""
+def serve_window(torch, gpr, graphs, specs, rate, warm, window, budget, seed=7):
+    """One run of the server on a Poisson trace at `rate` requests/s:
+    `warm` seconds of warm-up, then a `window`-second measured window, then
+    up to 30 s to drain.  Returns (summary dict, completed-request steps)."""
     import threading
 
-    import numpy as np
-    import torch
-
-    import paper_1606_07550_gb300 as gpr
-    from gen import workloads
-
-    torch.cuda.set_device(local)
-    specs = workloads.serving_pool_specs(args.pool)
-    t0 = time.perf_counter()
-    graphs = [build_graph_dev(torch, gpr, sp) for sp in specs]
-    torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    t_setup = time.perf_counter() - t0
-    warm, window = args.serve_warmup, args.serve_seconds
-    trace = workloads.serving_trace([sp.n for sp in specs], rate=args.serve_rate, duration=warm + window, seed=7)
-    budget = 40 << 30
+    trace = workloads_trace(specs, rate, warm + window, seed)
     srv = gpr.Server(graphs, budget_bytes=budget, max_queue=1 << 20)
     info = {}     # ticket -> (arrival s, seeds)
     done = {}     # ticket -> (latency ms, status, steps, completion s)
@@ -558,6 +540,7 @@ def run_serve(args, world, rank, local):
     th = threading.Thread(target=collector, daemon=True)
     th.start()
     i = 0
+    tickets = []
     while i < len(trace):
         now = time.perf_counter() - tstart
         while i < len(trace) and trace[i].t_arrive <= now:
@@ -566,6 +549,7 @@ def run_serve(args, world, rank, local):
                 t = srv.submit(q.graph, q.seeds, damping=q.damping, tol=q.tol, max_iters=1000,
                                dtype=gpr.BF16 if q.bf16 else gpr.FP32)
                 info[t] = (q.t_arrive, len(q.seeds))
+                tickets.append((t, q))
             except gpr.GprError as e:
                 rejected["busy" if e.status == gpr.EBUSY else "nomem"] += 1
             i += 1
@@ -588,14 +572,70 @@ def run_serve(args, world, rank, local):
     def pct(a, q):
         return a[min(len(a) - 1, int(q * len(a)))] if a else None
 
+    out = {"rate_req_per_s": rate, "window_s": window, "solves_per_s": solves / window,
+           "offered_solves_per_s": offered / window, "arrived_in_window": len(in_window),
+           "completed_in_window": len(lat), "unfinished_after_drain": unfinished,
+           "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99), "rejected": rejected, "server": st}
+    steps = [(q, done[t][2]) for t, q in tickets if t in done and done[t][1] == gpr.OK]
+    return out, steps
+
+
+def workloads_trace(specs, rate, duration, seed):
+    from gen import workloads
+    return workloads.serving_trace([sp.n for sp in specs], rate=rate, duration=duration, seed=seed)
+
+
+def run_serve(args, world, rank, local):
+    """Config: a resident pool of 256 R-MAT graphs (scales 14-22, edge factor
+    16); Poisson arrivals at 2,000 requests/s, each naming a graph, 1-64 seeds,
+    damping in [0.80, 0.90] and tolerance 1e-6 or 1e-3 (BF16 contributions for
+    half of the 1e-3 requests); admission under a 40 GB device budget that
+    includes the pool.  Reports submit-to-completion p50/p99 over the requests
+    that arrived in the measured window, solves/s completed in the window (one
+    seed = one solve), rejections and the backlog.  The offered load is far
+    above capacity, so the same measurement is repeated at the lower rates of
+    --stable-rates: the highest rate whose window drains (no request left
+    unfinished, completions keeping up with arrivals) is the maximum stable
+    load, with its latencies.  Baseline on the same GPU: one-at-a-time plain
+    PageRank, one call per solve with the step count the request needed, on a
+    sample of the trace."""
+    import torch
+
+    import paper_1606_07550_gb300 as gpr
+    from gen import workloads
+
+    torch.cuda.set_device(local)
+    specs = workloads.serving_pool_specs(args.pool)
+    t0 = time.perf_counter()
+    graphs = [build_graph_dev(torch, gpr, sp) for sp in specs]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    t_setup = time.perf_counter() - t0
+    budget = 40 << 30
+    main_run, steps = serve_window(torch, gpr, graphs, specs, args.serve_rate, args.serve_warmup,
+                                   args.serve_seconds, budget)
+    sweep = []
+    for r in [float(x) for x in args.stable_rates.split(",") if x]:
+        res, _ = serve_window(torch, gpr, graphs, specs, r, args.serve_warmup, args.stable_seconds, budget)
+        res["stable"] = res["unfinished_after_drain"] == 0 and res["solves_per_s"] >= 0.9 * res[
+            "offered_solves_per_s"]
+        sweep.append(res)
+    stable = [r for r in sweep if r["stable"]]
+    max_stable = max(stable, key=lambda r: r["rate_req_per_s"]) if stable else None
+
     # baseline: one-at-a-time plain PageRank, one call per solve, each with
     # the step count the served request needed; sampled requests of the
     # trace, at most ~10 s of GPU time
-    steps = {}
-    for t, d in done.items():
-        if d[1] == gpr.OK:
-            steps[t] = d[2]
-    sample = [(q, steps.get(t, 60)) for t, q in zip(sorted(info), trace)][:: max(1, len(info) // 200)]
+    sample = steps[:: max(1, len(steps) // 200)]
+    # the library tunes the step's schedule once per graph shape: do that
+    # before the timed baseline
+    tuned = set()
+    for g in graphs:
+        key = (int(g.n).bit_length(), int(g.info().m).bit_length())
+        if g.info().m >= (1 << 22) and key not in tuned:
+            gpr.pagerank_tune(g)
+            tuned.add(key)
+    torch.cuda.synchronize()
     b0 = time.perf_counter()
     nb = 0
     for q, k in sample:
@@ -606,23 +646,29 @@ def run_serve(args, world, rank, local):
         torch.cuda.synchronize()
         if time.perf_counter() - b0 > 10.0:
             break
-    base = nb / (time.perf_counter() - b0)
+    base = nb / (time.perf_counter() - b0) if nb else None
+    value = main_run["solves_per_s"]
     line = {
-        "metric": "PPR solves/s (served)", "value": solves / window, "unit": "solves/s", "n_gpus": world,
-        "steps": 1, "warmup": 1, "ms_per_step": window * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": "PPR solves/s (served)", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": args.serve_seconds * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serving-pool256-poisson", "pool_graphs": len(specs),
                    "pool_raw_edges": sum(sp.m for sp in specs), "rate_req_per_s": args.serve_rate,
-                   "warmup_s": warm, "window_s": window, "budget_bytes": budget,
-                   "steps_per_tick": 8, "edges_per_part": 1 << 20,
-                   "max_iters": 1000},
-        "latency_ms": {"p50": pct(lat, 0.50), "p99": pct(lat, 0.99), "completed": len(lat),
-                       "arrived_in_window": len(in_window), "unfinished_after_drain": unfinished},
-        "offered_solves_per_s": offered / window,
-        "rejected": rejected,
-        "server": st,
+                   "warmup_s": args.serve_warmup, "window_s": args.serve_seconds, "budget_bytes": budget,
+                   "steps_per_tick": 8, "edges_per_part": 1 << 20, "max_iters": 1000},
+        "latency_ms": {"p50": main_run["p50_ms"], "p99": main_run["p99_ms"],
+                       "completed": main_run["completed_in_window"],
+                       "arrived_in_window": main_run["arrived_in_window"],
+                       "unfinished_after_drain": main_run["unfinished_after_drain"]},
+        "offered_solves_per_s": main_run["offered_solves_per_s"],
+        "rejected": main_run["rejected"],
+        "server": main_run["server"],
+        "stable_load_sweep": sweep,
+        "max_stable_load": ({"rate_req_per_s": max_stable["rate_req_per_s"],
+                             "solves_per_s": max_stable["solves_per_s"], "p50_ms": max_stable["p50_ms"],
+                             "p99_ms": max_stable["p99_ms"]} if max_stable else None),
         "one_at_a_time_solves_per_s": base, "baseline_sample_solves": nb,
-        "speedup_vs_one_at_a_time": (solves / window) / base if base else None,
+        "speedup_vs_one_at_a_time": value / base if base else None,
         "setup_s": t_setup,
     }
     if rank == 0:

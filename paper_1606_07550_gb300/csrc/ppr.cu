@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
   __shared__ float s_heavy[kPprWarps][kPprCols];
   __shared__ int32_t s_seed[kPprCols];
   __shared__ float s_d[kPprCols], s_tol[kPprCols];
+  __shared__ double s_best[kPprCols];
+  __shared__ int32_t s_stall[kPprCols];
   __shared__ double s_D[kPprCols], s_res[kPprCols];
   __shared__ int32_t s_status[kPprCols], s_iters[kPprCols], s_maxit[kPprCols], s_newdone[kPprCols];
   __shared__ uint32_t s_key[kPprCols];
@@ -260,11 +262,15 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         s_D[tid] = inv_deg[s_seed[tid]] == 0.f ? 1.0 : 0.0;
         s_iters[tid] = 0;
         s_res[tid] = 0.0;
+        s_best[tid] = INFINITY;
+        s_stall[tid] = 0;
       } else {
         s_seed[tid] = cr.status == kColEmpty ? -1 : J->old2new[cr.seed];
         s_D[tid] = cr.dangling;
         s_iters[tid] = cr.iters;
         s_res[tid] = cr.residual;
+        s_best[tid] = cr.best;
+        s_stall[tid] = cr.stall;
       }
       s_d[tid] = cr.damping;
       s_tol[tid] = cr.tol;
@@ -373,7 +379,14 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         const int32_t k_it = s_iters[tid] + 1;
         s_iters[tid] = k_it;
         const double d = s_d[tid];
-        const bool converged = s_tol[tid] > 0.f && (d / (1.0 - d)) * tot[2] <= (double)s_tol[tid];
+        if (tot[2] < s_best[tid]) {
+          s_best[tid] = tot[2];
+          s_stall[tid] = 0;
+        } else {
+          ++s_stall[tid];
+        }
+        const bool converged =
+            s_tol[tid] > 0.f && ((d / (1.0 - d)) * tot[2] <= (double)s_tol[tid] || s_stall[tid] >= kStallSteps);
         if (converged || k_it >= s_maxit[tid]) {
           s_status[tid] = kColDone;
           s_newdone[tid] = 1;
@@ -402,6 +415,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         cr->iters = s_iters[tid];
         cr->dangling = s_D[tid];
         cr->residual = s_res[tid];
+        cr->best = s_best[tid];
+        cr->stall = s_stall[tid];
       }
     }
     cl.sync();  // the workspace and s_job are reused by the next job
@@ -445,18 +460,22 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       s_seed[tid] = seed_row;
       s_d[tid] = cr.damping;
       s_key[tid] = hash32((uint32_t)cr.seed * 0x85EBCA6Bu ^ __float_as_uint(cr.damping));
-      int32_t status, iters;
-      double D, res;
+      int32_t status, iters, stall;
+      double D, res, best;
       int newdone = 0;
       if (mode == kStepInit) {
         status = cr.status;
         iters = cr.iters;
         D = cr.dangling;
         res = cr.residual;
+        best = cr.best;
+        stall = cr.stall;
         if (status == kColFresh) {
           status = kColRunning;
           iters = 0;
           res = 0.0;
+          best = INFINITY;
+          stall = 0;
           D = inv_deg[seed_row] == 0.f ? 1.0 : 0.0;
           if (iters >= cr.max_iters) {
             status = kColDone;
@@ -469,6 +488,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         iters = cs.iters;
         D = cs.dangling;
         res = cs.residual;
+        best = cs.best;
+        stall = cs.stall;
         const bool fold = mode == kStepFinish || step > 1;
         if (fold && status == kColRunning) {
           double dsum = 0.0, rsum = 0.0;
@@ -481,7 +502,14 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
           res = rsum;
           iters += 1;
           const double d = cr.damping;
-          if ((cr.tol > 0.f && (d / (1.0 - d)) * rsum <= (double)cr.tol) || iters >= cr.max_iters) {
+          if (rsum < best) {
+            best = rsum;
+            stall = 0;
+          } else {
+            ++stall;
+          }
+          if ((cr.tol > 0.f && ((d / (1.0 - d)) * rsum <= (double)cr.tol || stall >= kStallSteps)) ||
+              iters >= cr.max_iters) {
             status = kColDone;
             newdone = 1;
           }
@@ -498,8 +526,10 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
           w->iters = iters;
           w->dangling = D;
           w->residual = res;
+          w->best = best;
+          w->stall = stall;
         } else {
-          S->st[mode == kStepInit ? 0 : cur][tid] = ColState{status, iters, D, res};
+          S->st[mode == kStepInit ? 0 : cur][tid] = ColState{status, iters, D, res, best, stall, 0};
         }
       }
     }

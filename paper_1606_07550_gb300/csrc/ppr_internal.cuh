@@ -21,10 +21,17 @@ struct PprCol {
   int32_t iters;      // steps run so far
   double dangling;    // dangling mass of the current iterate
   double residual;    // last ||x_k - x_{k-1}||_1
+  double best;        // smallest residual so far
   float* out;         // where the finished column goes: out[v * ldo], v = node id
   int32_t ldo;
-  int32_t pad;
+  int32_t stall;      // steps since the residual last reached a new minimum
 };
+
+// A column with tol > 0 also stops once its residual has not reached a new
+// minimum for this many steps: the update contracts L1 distances by d per
+// step, so a residual that stops shrinking has met the floor of the storage
+// precision, and no further step brings the iterate closer.
+constexpr int32_t kStallSteps = 8;
 
 // One ppr_batch job: a graph and 64 column places; its state lives in the
 // workspace of the cluster that runs it.
@@ -49,7 +56,8 @@ struct PprJob {
 // start of the next launch; column state is double-buffered by step parity.
 struct ColState {
   int32_t status, iters;
-  double dangling, residual;
+  double dangling, residual, best;
+  int32_t stall, pad;
 };
 
 struct SlotDesc {

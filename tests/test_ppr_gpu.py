@@ -116,6 +116,21 @@ def test_tolerance_stop(torch):
             assert l1(xs[0][:, k], xstar) <= tol + 1e-5
 
 
+@pytest.mark.parametrize("dt,tol,err", [(gpr.FP32, 1e-12, 1e-5), (gpr.FP16, 1e-6, 1e-3), (gpr.BF16, 1e-6, 3e-3)])
+def test_tolerance_below_the_storage_floor_stops_at_the_floor(torch, dt, tol, err):
+    # the bound d/(1-d)||x_k - x_{k-1}||_1 cannot reach tol in this storage:
+    # a column stops once its residual has stopped shrinking, long before
+    # max_iters, at the fixed point within the storage's tolerance
+    g, ref = make_graph(torch, 6000, 80_000, 12)
+    seeds = np.array([1, 77, 5999], np.int32)
+    xs, res = run(torch, [(g, seeds, 0.9)], 5000, tol=tol, dt=dt)
+    it, resid = res[0]
+    for k, s in enumerate(seeds):
+        assert 20 < int(it[k]) < 1000, int(it[k])
+        xstar, _ = oracle.ppr(ref, int(s), 0.9, 600)
+        assert l1(xs[0][:, k], xstar) <= err
+
+
 def test_zero_iterations_is_the_seed_vector(torch):
     g, _ = make_graph(torch, 1000, 10_000, 11)
     xs, res = run(torch, [(g, np.array([4, 999], np.int32), 0.85)], 0)
