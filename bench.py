@@ -655,7 +655,7 @@ def run_serve(args, world, rank, local):
         "config": {"workload": "serving-pool256-poisson", "pool_graphs": len(specs),
                    "pool_raw_edges": sum(sp.m for sp in specs), "rate_req_per_s": args.serve_rate,
                    "warmup_s": args.serve_warmup, "window_s": args.serve_seconds, "budget_bytes": budget,
-                   "steps_per_tick": 8, "edges_per_part": 1 << 20, "max_iters": 1000},
+                   "steps_per_tick": 8, "edges_per_part": 1 << 18, "max_iters": 1000},
         "latency_ms": {"p50": main_run["p50_ms"], "p99": main_run["p99_ms"],
                        "completed": main_run["completed_in_window"],
                        "arrived_in_window": main_run["arrived_in_window"],

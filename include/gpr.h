@@ -195,9 +195,9 @@ typedef struct {
   int64_t budget_bytes;    /* device memory for the pool + batch state + results */
   int32_t max_queue;       /* queued (not yet admitted) requests before GPR_EBUSY; <= 0: 65536 */
   int32_t steps_per_tick;  /* steps between two admission rounds; <= 0: 8 */
-  int64_t edges_per_part;  /* a batch's rows are split into parts of about this many edges,
-                              each part one unit of work per step, so large graphs spread
-                              over every SM; <= 0: 2^20 */
+  int64_t edges_per_part;  /* a batch's rows are split into parts of about this much work
+                              (an edge counts 1, a row 3), each part one unit of work per
+                              step, so large graphs spread over every SM; <= 0: 2^18 */
   int32_t fail_alloc_at;   /* test hook: the k-th batch allocation fails as if out of memory (0: off) */
 } gpr_server_config;
 

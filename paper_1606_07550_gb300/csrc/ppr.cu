@@ -163,6 +163,24 @@ __device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, float2 xo, c
   acc[1][2] += fabsf(n1 - xo.y);
 }
 
+// A row costs three 256-byte row accesses (its state read and written, its
+// contributions written) besides one gather per edge: rows are split among
+// CTAs and parts by edges + kRowWeight * rows.
+constexpr int64_t kRowWeight = 3;
+
+// The first row p in [0, n] with col_ptr[p] + kRowWeight * p >= key.
+__device__ __forceinline__ int32_t lower_bound_work(const int32_t* col_ptr, int32_t n, int64_t key) {
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int32_t mid = lo + (hi - lo) / 2;
+    if ((int64_t)col_ptr[mid] + kRowWeight * mid < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int32_t lower_bound_i32(const int32_t* a, int32_t n, int64_t key) {
   int32_t lo = 0, hi = n;
   while (lo < hi) {
@@ -239,12 +257,12 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
     Cb[1] = Cb[0] + (int64_t)J->n_cap * kPprCols;
     int parity = 0;
 
-    // this block's rows: split by edge count
-    const int64_t m = col_ptr[n];
+    // this block's rows: split by edges + kRowWeight * rows
+    const int64_t work = (int64_t)col_ptr[n] + kRowWeight * n;
     auto split = [&](int r) -> int32_t {
       if (r <= 0) return 0;
       if (r >= cluster_size) return n;
-      return lower_bound_i32(col_ptr, n + 1, (m * r + cluster_size - 1) / cluster_size);
+      return lower_bound_work(col_ptr, n, (work * r + cluster_size - 1) / cluster_size);
     };
     const int32_t r0 = min(split(crank), n), r1 = max(r0, min(split(crank + 1), n));
     // long rows of this block: the part of the (ascending) long-row list in [r0, r1)
@@ -440,7 +458,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
                                                                  int mode, int32_t step) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ float s_wpart[kPprWarps][3][kPprCols];
-  __shared__ float s_heavy[kPprWarps][kPprCols];
   __shared__ int32_t s_seed[kPprCols], s_status[kPprCols], s_iters[kPprCols], s_newdone[kPprCols];
   __shared__ float s_d[kPprCols];
   __shared__ double s_D[kPprCols];
@@ -537,25 +554,46 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
 
     // ---- fresh columns start at e_seed (X and the current contributions)
     if (mode == kStepInit) {
+      // one pass over the part's rows: every fresh column of a row at once
       T* Cc = (T*)S->C[S->parity];
-      for (int k = 0; k < kPprCols; ++k) {
-        if (S->rec[k].status != kColFresh) continue;
-        const int32_t sr = s_seed[k];
-        for (int32_t p = r0 + tid; p < r1; p += kPprThreads) {
-          const float v = p == sr ? 1.f : 0.f;
-          X[(int64_t)p * kPprCols + k] = v;
-          st_one(Cc + (int64_t)p * kPprCols + k, v * inv_deg[p]);
+      const int k0 = 2 * lane, k1 = 2 * lane + 1;
+      const bool f0 = S->rec[k0].status == kColFresh, f1 = S->rec[k1].status == kColFresh;
+      const int32_t sr0 = s_seed[k0], sr1 = s_seed[k1];
+      if (__any_sync(0xffffffffu, f0 || f1)) {
+        for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
+          const float idg = inv_deg[p];
+          const int64_t o = (int64_t)p * kPprCols;
+          if (f0) {
+            const float v = p == sr0 ? 1.f : 0.f;
+            X[o + k0] = v;
+            st_one(Cc + o + k0, v * idg);
+          }
+          if (f1) {
+            const float v = p == sr1 ? 1.f : 0.f;
+            X[o + k1] = v;
+            st_one(Cc + o + k1, v * idg);
+          }
         }
       }
       __syncthreads();
     }
 
-    // ---- columns finished by now: this part's rows go out by node id
-    for (int k = 0; k < kPprCols; ++k) {
-      if (!s_newdone[k]) continue;
-      const PprCol cr = S->rec[k];
-      for (int32_t p = r0 + tid; p < r1; p += kPprThreads)
-        cr.out[(int64_t)S->new2old[p] * cr.ldo] = X[(int64_t)p * kPprCols + k];
+    // ---- columns finished by now: this part's rows go out by node id, in
+    // one pass over the rows (a warp per row, two columns per lane)
+    {
+      const int k0 = 2 * lane, k1 = 2 * lane + 1;
+      const bool d0 = s_newdone[k0] != 0, d1 = s_newdone[k1] != 0;
+      if (__any_sync(0xffffffffu, d0 || d1)) {
+        float* o0 = d0 ? S->rec[k0].out : nullptr;
+        float* o1 = d1 ? S->rec[k1].out : nullptr;
+        const int64_t l0 = d0 ? S->rec[k0].ldo : 0, l1 = d1 ? S->rec[k1].ldo : 0;
+        for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
+          const int64_t v = S->new2old[p];
+          const float2 x = ld_state(X, p, lane);
+          if (d0) o0[v * l0] = x.x;
+          if (d1) o1[v * l1] = x.y;
+        }
+      }
     }
 
     if (mode == kStepRun) {
@@ -588,26 +626,24 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
         finish_ppr_row(p, y, xo, c, X, Cout, inv_deg, lane, acc);
       }
+      // long rows: their chunk sums (this step's chunk launch), in chunk
+      // order, a warp per row
       const int32_t h0 = lower_bound_i32(S->heavy_rows, S->n_heavy, r0);
       const int32_t h1 = lower_bound_i32(S->heavy_rows, S->n_heavy, r1);
-      for (int32_t hi = h0; hi < h1; ++hi) {
+      for (int32_t hi = h0 + warp; hi < h1; hi += kPprWarps) {
         const int32_t p = S->heavy_rows[hi];
-        const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
-        const int32_t per = (((e1 - e0) + kPprWarps - 1) / kPprWarps + 31) & ~31;
-        const int32_t a = min(e1, e0 + warp * per), b = min(e1, a + per);
-        const float2 y = gather_row(row_idx, Cin, a, b, lane);
-        s_heavy[warp][2 * lane] = y.x;
-        s_heavy[warp][2 * lane + 1] = y.y;
-        __syncthreads();
-        if (warp == 0) {
-          float yx = 0.f, yy = 0.f;
-          for (int w = 0; w < kPprWarps; ++w) {
-            yx += s_heavy[w][2 * lane];
-            yy += s_heavy[w][2 * lane + 1];
+        const int32_t sp = S->heavy_split0 + hi;
+        float yx = 0.f, yy = 0.f;
+        for (int pass = 0; pass < 2; ++pass) {
+          const int32_t c0 = pass == 0 ? S->split_hbeg[sp] : S->split_cbeg[sp];
+          const int32_t c1 = pass == 0 ? S->split_hend[sp] : S->split_cend[sp];
+          for (int32_t c = c0; c < c1; ++c) {
+            const float2 v = __ldcg(reinterpret_cast<const float2*>(S->chunk_sum + (int64_t)c * kPprCols) + lane);
+            yx += v.x;
+            yy += v.y;
           }
-          finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), c, X, Cout, inv_deg, lane, acc);
         }
-        __syncthreads();
+        finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), c, X, Cout, inv_deg, lane, acc);
       }
       for (int v = 0; v < 3; ++v) {
         s_wpart[warp][v][2 * lane] = acc[0][v];
@@ -625,6 +661,26 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
   }
 }
 
+// Long-row chunk sums of one step: item (slot, q) covers chunks
+// [q * kChunksPerItem, (q + 1) * kChunksPerItem) of the slot's plan; a warp
+// gathers a chunk's edges for all 64 columns.
+template <typename T>
+__global__ void __launch_bounds__(kPprThreads, 1) ppr_chunk_kernel(const SlotDesc* __restrict__ slots,
+                                                                  const StepItem* __restrict__ items, int32_t nitems,
+                                                                  int32_t step) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int32_t ii = blockIdx.x; ii < nitems; ii += gridDim.x) {
+    const StepItem item = items[ii];
+    const SlotDesc* S = slots + item.slot;
+    const T* __restrict__ Cin = (const T*)S->C[(S->parity + step - 1) & 1];
+    const int32_t c_end = min(S->nchunks, (item.part + 1) * kChunksPerItem);
+    for (int32_t ch = item.part * kChunksPerItem + warp; ch < c_end; ch += kPprWarps) {
+      const float2 y = gather_row(S->row_idx, Cin, S->chunk_begin[ch], S->chunk_end[ch], lane);
+      reinterpret_cast<float2*>(S->chunk_sum + (int64_t)ch * kPprCols)[lane] = y;
+    }
+  }
+}
+
 __global__ void part_bounds_kernel(const int32_t* __restrict__ col_ptr, int32_t n, int64_t m, int32_t nparts,
                                    int32_t* __restrict__ part_rows) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= nparts; i += gridDim.x * blockDim.x) {
@@ -633,8 +689,9 @@ __global__ void part_bounds_kernel(const int32_t* __restrict__ col_ptr, int32_t 
     } else if (i == nparts) {
       part_rows[i] = n;
     } else {
-      const int64_t target = (m * i + nparts - 1) / nparts;
-      part_rows[i] = min(n, lower_bound_i32(col_ptr, n + 1, target));
+      const int64_t work = m + kRowWeight * n;  // edges + kRowWeight * rows
+      const int64_t target = (work * i + nparts - 1) / nparts;
+      part_rows[i] = min(n, lower_bound_work(col_ptr, n, target));
     }
   }
 }
@@ -690,6 +747,27 @@ void ppr_step_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int32
     ppr_step_kernel<__half><<<step_grid<__half>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev, nitems, mode, step);
   else
     ppr_step_kernel<float><<<step_grid<float>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev, nitems, mode, step);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+template <typename T>
+static int chunk_grid(int32_t nitems) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ppr_chunk_kernel<T>, kPprThreads, 0);
+  return std::max(1, std::min(nitems, num_sms() * std::max(per_sm, 1)));
+}
+
+void ppr_chunk_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int32_t nitems, int32_t step,
+                      gpr_dtype dt, cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (dt == GPR_BF16)
+    ppr_chunk_kernel<__nv_bfloat16><<<chunk_grid<__nv_bfloat16>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev,
+                                                                                            nitems, step);
+  else if (dt == GPR_FP16)
+    ppr_chunk_kernel<__half><<<chunk_grid<__half>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev, nitems, step);
+  else
+    ppr_chunk_kernel<float><<<chunk_grid<float>(nitems), kPprThreads, 0, s>>>(slots_dev, items_dev, nitems, step);
   GPR_CUDA(cudaGetLastError());
   count_launches(1);
 }
@@ -758,7 +836,7 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
           if (g->plan.bucket[b].lanes == 0) {
             J.heavy_rows = g->plan.rows + g->plan.bucket[b].row_begin;
             J.n_heavy = g->plan.bucket[b].row_end - g->plan.bucket[b].row_begin;
-            J.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : 0;
+            J.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : -1;  // bucket 0 holds every degree from 0
           }
         J.iters = max_iters;
         J.n_cap = 0;  // set below

@@ -77,16 +77,32 @@ struct SlotDesc {
   PprCol* rec;               // 64 host-visible records
   ColState* st[2];           // 64 each, by step parity
   double* psum[2];           // nparts x 3 x 64 each, by step parity
+  // long rows (heavy_rows) as edge chunks of the graph's plan: long row i
+  // sums chunks [hbeg, hend) then [cbeg, cend) of split entry heavy_split0 + i
+  const int32_t* chunk_begin;
+  const int32_t* chunk_end;
+  const int32_t* split_hbeg;
+  const int32_t* split_hend;
+  const int32_t* split_cbeg;
+  const int32_t* split_cend;
+  int32_t nchunks, heavy_split0;
+  float* chunk_sum;          // nchunks x 64: the chunk's sums of this step
 };
 
 struct StepItem {
   int32_t slot, part;
 };
 
+// 64 consecutive long-row chunks of one slot.
+constexpr int32_t kChunksPerItem = 64;
+
 enum : int { kStepInit = 0, kStepRun = 1, kStepFinish = 2 };
 
 void ppr_step_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int32_t nitems, int mode, int32_t step,
                      gpr_dtype dt, cudaStream_t s);
+// The long-row chunk sums of step `step` for chunk items (slot, first chunk / kChunksPerItem).
+void ppr_chunk_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int32_t nitems, int32_t step,
+                      gpr_dtype dt, cudaStream_t s);
 void ppr_part_bounds(const int32_t* col_ptr, int32_t n, int64_t m, int32_t nparts, int32_t* part_rows,
                      cudaStream_t s);
 

@@ -11,8 +11,9 @@
 //      most kOvertakeMs), later requests may take free places of running
 //      slots, which needs no new slot;
 //   2. run steps_per_tick steps of every slot with live columns: each slot's
-//      rows are split into parts of about edges_per_part edges and one
-//      launch runs one step of every (slot, part) on all SMs (ppr.cu,
+//      rows are split into parts of about edges_per_part units of work (an
+//      edge counts 1, a row 3); per step, one launch gathers the long rows'
+//      edge chunks of every slot and one runs every (slot, part) (ppr.cu,
 //      ppr_step_kernel: new columns start at e_seed, finished ones freeze
 //      and are written to their result buffer by node id);
 //   3. read back the column records, complete requests whose columns are
@@ -53,6 +54,7 @@ struct Slot {
   PprCol* d_rec = nullptr;       // device, 64
   ColState* d_st = nullptr;      // device, 2 x 64
   double* d_psum = nullptr;      // device, 2 x nparts x 3 x 64
+  float* chunk_sum = nullptr;    // device, nchunks x 64: long-row chunk sums of a step
   PprCol cols[kPprCols];         // host mirror of d_rec
   uint64_t owner[kPprCols];      // ticket holding each place (0: free)
   int used = 0;
@@ -100,7 +102,8 @@ struct gpr_server {
   // device staging for one tick
   gpr::SlotDesc* d_desc = nullptr;
   gpr::StepItem* d_items = nullptr;
-  int cap_desc = 0, cap_items = 0;
+  gpr::StepItem* d_citems = nullptr;
+  int cap_desc = 0, cap_items = 0, cap_citems = 0;
 };
 
 namespace gpr {
@@ -108,14 +111,17 @@ namespace gpr {
 static size_t elem_bytes(gpr_dtype dt) { return dt == GPR_FP32 ? 4 : 2; }
 
 static int32_t parts_for(const gpr_server* S, const gpr_graph* g) {
-  const int64_t p = (g->m + S->cfg.edges_per_part - 1) / std::max<int64_t>(S->cfg.edges_per_part, 1);
+  // parts of about edges_per_part units of work (an edge; a row counts as 3)
+  const int64_t work = g->m + 3 * (int64_t)g->n;
+  const int64_t p = (work + S->cfg.edges_per_part - 1) / std::max<int64_t>(S->cfg.edges_per_part, 1);
   return (int32_t)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(p, 1024), std::max(g->n, 1)));
 }
 
 static int64_t slot_bytes(const gpr_server* S, const gpr_graph* g, gpr_dtype dt) {
   const int64_t P = parts_for(S, g);
   return (int64_t)g->n * kPprCols * (4 + 2 * (int64_t)elem_bytes(dt)) + (P + 1) * 4 +
-         kPprCols * (int64_t)(sizeof(PprCol) + 2 * sizeof(ColState)) + 2 * P * 3 * kPprCols * 8;
+         kPprCols * (int64_t)(sizeof(PprCol) + 2 * sizeof(ColState)) + 2 * P * 3 * kPprCols * 8 +
+         (int64_t)std::max(g->plan.nchunks, 1) * kPprCols * 4;
 }
 
 static void fill_desc(SlotDesc& D, const gpr_graph* g, const Slot* sl) {
@@ -129,12 +135,25 @@ static void fill_desc(SlotDesc& D, const gpr_graph* g, const Slot* sl) {
   D.heavy_rows = g->plan.rows;
   D.n_heavy = 0;
   D.heavy_deg = INT_MAX;
+  // the long rows are the last chunked (lanes 0) bucket; the plan's split
+  // entries list the rows of every chunked bucket in bucket order
+  int32_t before = 0;
   for (int b = 0; b < g->plan.nbuckets; ++b)
     if (g->plan.bucket[b].lanes == 0) {
+      D.heavy_split0 = before;
       D.heavy_rows = g->plan.rows + g->plan.bucket[b].row_begin;
       D.n_heavy = g->plan.bucket[b].row_end - g->plan.bucket[b].row_begin;
-      D.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : 0;
+      D.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : -1;  // bucket 0 holds every degree from 0
+      before += D.n_heavy;
     }
+  D.chunk_begin = g->plan.chunk_begin;
+  D.chunk_end = g->plan.chunk_end;
+  D.split_hbeg = g->plan.split_hbeg;
+  D.split_hend = g->plan.split_hend;
+  D.split_cbeg = g->plan.split_cbeg;
+  D.split_cend = g->plan.split_cend;
+  D.nchunks = g->plan.nchunks;
+  D.chunk_sum = sl->chunk_sum;
   D.nparts = sl->nparts;
   D.part_rows = sl->part_rows;
   D.X = sl->X;
@@ -156,6 +175,7 @@ static void free_slot(gpr_server* S, Slot* sl) {
   dfree(sl->d_rec, S->stream);
   dfree(sl->d_st, S->stream);
   dfree(sl->d_psum, S->stream);
+  dfree(sl->chunk_sum, S->stream);
   S->bytes_in_use -= sl->bytes;
   delete sl;
 }
@@ -192,6 +212,7 @@ static bool try_admit(gpr_server* S, Req& r, bool existing_only = false) {
         sl->d_rec = (PprCol*)dalloc(kPprCols * sizeof(PprCol), S->stream);
         sl->d_st = (ColState*)dalloc(2 * kPprCols * sizeof(ColState), S->stream);
         sl->d_psum = (double*)dalloc((size_t)2 * sl->nparts * 3 * kPprCols * 8, S->stream);
+        sl->chunk_sum = (float*)dalloc((size_t)std::max(g->plan.nchunks, 1) * kPprCols * 4, S->stream);
         ppr_part_bounds(g->col_ptr, g->n, g->m, sl->nparts, sl->part_rows, S->stream);
       } catch (...) {
         dfree(sl->X, S->stream);
@@ -201,6 +222,7 @@ static bool try_admit(gpr_server* S, Req& r, bool existing_only = false) {
         dfree(sl->d_rec, S->stream);
         dfree(sl->d_st, S->stream);
         dfree(sl->d_psum, S->stream);
+        dfree(sl->chunk_sum, S->stream);
         delete sl;
         throw;
       }
@@ -288,9 +310,21 @@ static void run_tick(gpr_server* S, const std::vector<Slot*>& live) {
     S->d_items = grow(S->d_items, S->cap_items, (int)items.size(), S->stream);
     GPR_CUDA(cudaMemcpyAsync(S->d_items, items.data(), items.size() * sizeof(StepItem), cudaMemcpyHostToDevice,
                              S->stream));
-    const int32_t ni = (int32_t)items.size();
+    std::vector<StepItem> citems;  // long-row chunk groups of the same slots
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i]->dt == dt)
+        for (int32_t q = 0; q * kChunksPerItem < desc[i].nchunks; ++q) citems.push_back(StepItem{(int32_t)i, q});
+    const int32_t ni = (int32_t)items.size(), nci = (int32_t)citems.size();
+    if (nci > 0) {
+      S->d_citems = grow(S->d_citems, S->cap_citems, nci, S->stream);
+      GPR_CUDA(cudaMemcpyAsync(S->d_citems, citems.data(), citems.size() * sizeof(StepItem),
+                               cudaMemcpyHostToDevice, S->stream));
+    }
     ppr_step_launch(S->d_desc, S->d_items, ni, kStepInit, 0, dt, S->stream);
-    for (int32_t st = 1; st <= T; ++st) ppr_step_launch(S->d_desc, S->d_items, ni, kStepRun, st, dt, S->stream);
+    for (int32_t st = 1; st <= T; ++st) {
+      ppr_chunk_launch(S->d_desc, S->d_citems, nci, st, dt, S->stream);
+      ppr_step_launch(S->d_desc, S->d_items, ni, kStepRun, st, dt, S->stream);
+    }
     ppr_step_launch(S->d_desc, S->d_items, ni, kStepFinish, T + 1, dt, S->stream);
     // the host copy of `items` must outlive the copy above
     GPR_CUDA(cudaStreamSynchronize(S->stream));
@@ -444,7 +478,7 @@ gpr_status serve_create(const gpr_graph* const* pool, int32_t num_graphs, const 
   S->cfg = *cfg;
   if (S->cfg.max_queue <= 0) S->cfg.max_queue = 65536;
   if (S->cfg.steps_per_tick <= 0) S->cfg.steps_per_tick = 8;
-  if (S->cfg.edges_per_part <= 0) S->cfg.edges_per_part = (int64_t)1 << 20;
+  if (S->cfg.edges_per_part <= 0) S->cfg.edges_per_part = (int64_t)1 << 18;
   std::vector<const gpr_graph*> uniq(S->pool);
   std::sort(uniq.begin(), uniq.end());
   uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
@@ -662,6 +696,7 @@ gpr_status serve_destroy(gpr_server* S) {
     if (kv.second.result) dfree(kv.second.result, S->stream);
   dfree(S->d_desc, S->stream);
   dfree(S->d_items, S->stream);
+  dfree(S->d_citems, S->stream);
   cudaError_t e = cudaStreamSynchronize(S->stream);
   cudaStreamDestroy(S->stream);
   delete S;
