@@ -26,7 +26,7 @@ DAMPING = 0.85
 
 def build() -> None:
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                           os.path.join(_HERE, "oracle.c"), "-o", _SO])
+                           os.path.join(_HERE, "oracle.c"), "-o", _SO, "-lm"])
 
 
 _lib = None
@@ -55,6 +55,10 @@ def _L():
         lib.oracle_sample_outdeg.restype = ctypes.c_int32
         lib.oracle_sample_outdeg.argtypes = [ctypes.c_int32, ctypes.c_int64, _i32p, _i32p, ctypes.c_int32,
                                              _i32p, _i32p]
+        lib.oracle_hits.restype = ctypes.c_int32
+        lib.oracle_hits.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _f64p, _f64p]
+        lib.oracle_eigen_centrality.restype = ctypes.c_int32
+        lib.oracle_eigen_centrality.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _f64p]
         _lib = lib
     return _lib
 
@@ -176,3 +180,24 @@ def sample_outdeg(n: int, src, dst, nodes):
     if rc != 0:
         raise ValueError("oracle_sample_outdeg failed")
     return out
+
+
+def hits(g: CSC, iters: int = 50):
+    """HITS hubs and authorities after `iters` steps, each L2-normalised
+    (oracle_hits in oracle/oracle.h).  Returns (hub, auth)."""
+    keep, ptrs = _csc_ptrs(g)
+    hub = np.empty(g.n, np.float64)
+    auth = np.empty(g.n, np.float64)
+    if _L().oracle_hits(g.n, ptrs[0], ptrs[1], iters, hub.ctypes.data_as(_f64p), auth.ctypes.data_as(_f64p)) < 0:
+        raise ValueError("oracle_hits: invalid arguments")
+    return hub, auth
+
+
+def eigen_centrality(g: CSC, iters: int = 50):
+    """Eigenvector centrality after `iters` power steps on A^T, L2-normalised
+    (oracle_eigen_centrality in oracle/oracle.h)."""
+    keep, ptrs = _csc_ptrs(g)
+    x = np.empty(g.n, np.float64)
+    if _L().oracle_eigen_centrality(g.n, ptrs[0], ptrs[1], iters, x.ctypes.data_as(_f64p)) < 0:
+        raise ValueError("oracle_eigen_centrality: invalid arguments")
+    return x

@@ -3,6 +3,7 @@
  * reader to check against the definitions by eye, not for speed. */
 #include "oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -246,5 +247,68 @@ int32_t oracle_sample_outdeg(int32_t n, int64_t m_raw, const int32_t* src, const
   for (int32_t j = 0; j < k; ++j) outdeg_out[j] = (int32_t)(off[j + 1] - off[j]);
   free(list);
   free(off);
+  return 0;
+}
+
+/* ---- HITS and eigenvector centrality -------------------------------------
+ * Both are power iterations with an L2 normalisation after every product
+ * (readings stated in oracle.h).  A^T x pulls over in-neighbours (the CSC
+ * rows); A x sums each node's out-neighbours, written here as a scatter over
+ * the same CSC rows. */
+
+static double l2_norm(int32_t n, const double* x) {
+  double s = 0.0;
+  for (int32_t i = 0; i < n; ++i) s += x[i] * x[i];
+  return sqrt(s);
+}
+
+static void scale_unit(int32_t n, double* x) {
+  const double nrm = l2_norm(n, x);
+  if (nrm > 0.0)
+    for (int32_t i = 0; i < n; ++i) x[i] /= nrm;
+}
+
+/* y = A^T x: y[v] = sum of x[u] over the in-neighbours u of v */
+static void pull_in(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const double* x, double* y) {
+  for (int32_t v = 0; v < n; ++v) {
+    double s = 0.0;
+    for (int32_t e = col_ptr[v]; e < col_ptr[v + 1]; ++e) s += x[row_idx[e]];
+    y[v] = s;
+  }
+}
+
+/* y = A x: y[u] = sum of x[v] over the out-neighbours v of u */
+static void push_out(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const double* x, double* y) {
+  for (int32_t u = 0; u < n; ++u) y[u] = 0.0;
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t e = col_ptr[v]; e < col_ptr[v + 1]; ++e) y[row_idx[e]] += x[v];
+}
+
+int32_t oracle_hits(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t iters, double* hub,
+                    double* auth) {
+  if (n <= 0 || iters < 0 || !col_ptr || !row_idx || !hub || !auth) return -1;
+  const double h0 = 1.0 / sqrt((double)n);
+  for (int32_t i = 0; i < n; ++i) hub[i] = auth[i] = h0;
+  for (int32_t t = 0; t < iters; ++t) {
+    pull_in(n, col_ptr, row_idx, hub, auth);
+    scale_unit(n, auth);
+    push_out(n, col_ptr, row_idx, auth, hub);
+    scale_unit(n, hub);
+  }
+  return 0;
+}
+
+int32_t oracle_eigen_centrality(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t iters,
+                                double* x) {
+  if (n <= 0 || iters < 0 || !col_ptr || !row_idx || !x) return -1;
+  double* y = (double*)malloc((size_t)n * sizeof(double));
+  if (!y) return -1;
+  for (int32_t i = 0; i < n; ++i) x[i] = 1.0 / sqrt((double)n);
+  for (int32_t t = 0; t < iters; ++t) {
+    pull_in(n, col_ptr, row_idx, x, y);
+    scale_unit(n, y);
+    for (int32_t i = 0; i < n; ++i) x[i] = y[i];
+  }
+  free(y);
   return 0;
 }

@@ -71,4 +71,23 @@ int64_t oracle_sample_in_rows(int32_t n, int64_t m_raw, const int32_t* src, cons
 int32_t oracle_sample_outdeg(int32_t n, int64_t m_raw, const int32_t* src, const int32_t* dst,
                              int32_t k, const int32_t* nodes, int32_t* outdeg_out);
 
+/* HITS (section 4 Table "snap_methods" names Hits among the centralities;
+ * the paper prints no formula).  Reading: Kleinberg's hubs and authorities on
+ * the directed graph, with A[u][v] = 1 for each edge u -> v:
+ *   h_0 = 1/sqrt(n) everywhere;  for t = 1..iters:
+ *     a_t = A^T h_{t-1} / ||A^T h_{t-1}||_2   (a_t[v] = sum over in-neighbours u of h[u])
+ *     h_t = A a_t       / ||A a_t||_2         (h_t[u] = sum over out-neighbours v of a[v])
+ * A vector whose norm is 0 stays 0.  iters = 0 gives a = h = 1/sqrt(n).
+ * Returns 0, or -1 on bad arguments. */
+int32_t oracle_hits(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t iters, double* hub,
+                    double* auth);
+
+/* Eigenvector centrality (section 4 Table "snap_methods": eigen-centrality;
+ * no formula printed).  Reading: the power iteration toward the Perron
+ * vector of A^T, x_0 = 1/sqrt(n), x_t = A^T x_{t-1} / ||A^T x_{t-1}||_2
+ * (a node is central when central nodes point to it); a vector whose norm
+ * is 0 stays 0.  Returns 0, or -1 on bad arguments. */
+int32_t oracle_eigen_centrality(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t iters,
+                                double* x);
+
 #endif /* GPR_ORACLE_H */

@@ -348,3 +348,154 @@ def test_pins_catch_planted_mistakes(mutation):
     # and the unmutated transcription passes the same pins
     x = _mutant_pagerank(g, 250, "none")
     assert abs(x[0] - 1.0 / (N + D)) < 1e-13 and abs(x.sum() - 1.0) <= 1e-12
+
+
+# ------------------------------------------- HITS and eigenvector centrality --
+# Pins: closed forms of bipartite and star graphs, the principal
+# eigenvectors of A^T A, A A^T and A^T from a dense eigen-decomposition,
+# unit norms and supports, and the zero-vector rule.
+
+def dense_adj(g):
+    """A[u, v] = 1 for each edge u -> v, from the CSC."""
+    A = np.zeros((g.n, g.n))
+    for v in range(g.n):
+        for u in g.row_idx[g.col_ptr[v]:g.col_ptr[v + 1]]:
+            A[u, v] = 1.0
+    return A
+
+
+@pytest.mark.parametrize("p,q", [(1, 1), (2, 5), (7, 3)])
+def test_hits_complete_bipartite_closed_form(p, q):
+    # every source points to every sink: one step reaches the fixed point
+    edges = [(u, p + v) for u in range(p) for v in range(q)]
+    g = csc_from_edges(p + q, edges)
+    for k in (1, 2, 30):
+        hub, auth = oracle.hits(g, k)
+        assert np.allclose(hub[:p], 1 / np.sqrt(p), atol=1e-15, rtol=0) and (hub[p:] == 0).all()
+        assert np.allclose(auth[p:], 1 / np.sqrt(q), atol=1e-15, rtol=0) and (auth[:p] == 0).all()
+
+
+@pytest.mark.parametrize("N", [2, 5, 40])
+def test_hits_stars(N):
+    out_star = csc_from_edges(N, [(0, i) for i in range(1, N)])
+    hub, auth = oracle.hits(out_star, 5)
+    assert abs(hub[0] - 1) < 1e-15 and (hub[1:] == 0).all()
+    assert auth[0] == 0 and np.allclose(auth[1:], 1 / np.sqrt(N - 1), atol=1e-15, rtol=0)
+    in_star = csc_from_edges(N, [(i, 0) for i in range(1, N)])
+    hub, auth = oracle.hits(in_star, 5)
+    assert abs(auth[0] - 1) < 1e-15 and (auth[1:] == 0).all()
+    assert hub[0] == 0 and np.allclose(hub[1:], 1 / np.sqrt(N - 1), atol=1e-15, rtol=0)
+
+
+def test_hits_zero_steps_and_no_edges():
+    g = csc_from_edges(9, [(0, 1), (3, 2)])
+    hub, auth = oracle.hits(g, 0)
+    assert np.allclose(hub, 1 / 3) and np.allclose(auth, 1 / 3)
+    hub, auth = oracle.hits(csc_from_edges(4, []), 3)
+    assert (hub == 0).all() and (auth == 0).all()
+
+
+def principal(M):
+    """Principal eigenpair of a symmetric PSD matrix, vector made nonnegative."""
+    w, V = np.linalg.eigh(M)
+    v = V[:, -1]
+    v = v if v.sum() >= 0 else -v
+    return w, v
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_hits_matches_dense_principal_eigenvectors(seed):
+    rng = np.random.default_rng(300 + seed)
+    N = int(rng.integers(5, 40))
+    src, dst = rng.integers(0, N, N * 6), rng.integers(0, N, N * 6)
+    g = oracle.build_csc(N, src, dst)
+    A = dense_adj(g)
+    wa, va = principal(A.T @ A)
+    wh, vh = principal(A @ A.T)
+    if wa[-1] <= 0 or wa[-2] / wa[-1] > 0.9:  # need a spectral gap for 400 steps to settle
+        pytest.skip("no spectral gap")
+    hub, auth = oracle.hits(g, 400)
+    assert np.abs(auth - va).max() < 1e-9
+    assert np.abs(hub - vh).max() < 1e-9
+    # unit norms, nonnegative, supported on nodes with in- / out-edges
+    assert abs(np.linalg.norm(auth) - 1) < 1e-12 and abs(np.linalg.norm(hub) - 1) < 1e-12
+    assert (auth >= 0).all() and (hub >= 0).all()
+    assert (auth[A.sum(0) == 0] == 0).all() and (hub[A.sum(1) == 0] == 0).all()
+
+
+def test_hits_finite_steps_match_dense_products():
+    rng = np.random.default_rng(7)
+    g = oracle.build_csc(30, rng.integers(0, 30, 150), rng.integers(0, 30, 150))
+    A = dense_adj(g)
+    h = np.full(30, 1 / np.sqrt(30))
+    for _ in range(6):
+        a = A.T @ h
+        a /= np.linalg.norm(a)
+        h = A @ a
+        h /= np.linalg.norm(h)
+    hub, auth = oracle.hits(g, 6)
+    assert np.abs(hub - h).max() < 1e-14 and np.abs(auth - a).max() < 1e-14
+
+
+@pytest.mark.parametrize("N", [3, 17])
+def test_eigen_centrality_cycle_and_complete_uniform(N):
+    cyc = csc_from_edges(N, [(i, (i + 1) % N) for i in range(N)])
+    comp = csc_from_edges(N, [(u, v) for u in range(N) for v in range(N) if u != v])
+    for g in (cyc, comp):
+        for k in (1, 7, 50):
+            assert np.allclose(oracle.eigen_centrality(g, k), 1 / np.sqrt(N), atol=1e-15, rtol=0)
+
+
+def test_eigen_centrality_in_star_and_zero_rule():
+    # leaves -> hub 0: one step puts everything on the hub; the hub points
+    # nowhere, so the next product is 0 and stays 0
+    g = csc_from_edges(6, [(i, 0) for i in range(1, 6)])
+    x1 = oracle.eigen_centrality(g, 1)
+    assert abs(x1[0] - 1) < 1e-15 and (x1[1:] == 0).all()
+    assert (oracle.eigen_centrality(g, 2) == 0).all()
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_eigen_centrality_matches_perron_vector(seed):
+    rng = np.random.default_rng(500 + seed)
+    N = int(rng.integers(6, 40))
+    g = oracle.build_csc(N, rng.integers(0, N, N * 8), rng.integers(0, N, N * 8))
+    A = dense_adj(g)
+    w, V = np.linalg.eig(A.T)
+    order = np.argsort(-np.abs(w))
+    lead, second = w[order[0]], w[order[1]]
+    if abs(lead.imag) > 1e-12 or abs(second) / abs(lead) > 0.9:
+        pytest.skip("no dominant real eigenvalue with a gap")
+    v = np.real(V[:, order[0]])
+    v = v / np.linalg.norm(v)
+    v = v if v.sum() >= 0 else -v
+    x = oracle.eigen_centrality(g, 600)
+    assert np.abs(x - v).max() < 1e-9
+    # and it is an eigenvector of A^T: A^T x = lambda x
+    assert np.abs(A.T @ x - np.real(lead) * x).max() < 1e-8
+
+
+def _mutant_hits(g, iters, mutation):
+    """HITS written out with one deliberate slip."""
+    A = dense_adj(g)
+    h = np.full(g.n, 1 / np.sqrt(g.n))
+    a = h.copy()
+    for _ in range(iters):
+        a = (A @ h) if mutation == "authority_from_out_edges" else (A.T @ h)
+        a /= np.linalg.norm(a) or 1.0
+        h = (A.T @ a) if mutation == "hub_from_in_edges" else (A @ a)
+        if mutation != "no_hub_norm":
+            h /= np.linalg.norm(h) or 1.0
+    return h, a
+
+
+@pytest.mark.parametrize("mutation", ["authority_from_out_edges", "hub_from_in_edges", "no_hub_norm"])
+def test_hits_pins_catch_planted_mistakes(mutation):
+    p, q = 2, 5
+    g = csc_from_edges(p + q, [(u, p + v) for u in range(p) for v in range(q)])
+    hub, auth = _mutant_hits(g, 3, mutation)
+    ok = (np.allclose(hub[:p], 1 / np.sqrt(p)) and np.allclose(auth[p:], 1 / np.sqrt(q))
+          and (hub[p:] == 0).all() and (auth[:p] == 0).all())
+    assert not ok
+    hub, auth = _mutant_hits(g, 3, "none")
+    assert np.allclose(hub[:p], 1 / np.sqrt(p)) and np.allclose(auth[p:], 1 / np.sqrt(q))
