@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpr", "reference"], default="gpr")
-    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve"], default="rmat25")
+    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits"], default="rmat25")
     ap.add_argument("--graphs", type=int, default=4096, help="batched: number of graphs")
     ap.add_argument("--dtypes", default="fp32,bf16,fp16", help="batched: contribution storage types")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -675,6 +675,83 @@ def run_serve(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_hits(args, world, rank, local):
+    """HITS on the R-MAT scale-25 graph (edge factor 32): each step is one
+    `hits` call of 20 iterations (authorities from the in-edges, hubs from the
+    out-edges, both L2-normalised) on a graph built before the timed region
+    (its out-adjacency is built by the first, untimed call).  GTEPS counts 2m
+    edge traversals per iteration."""
+    import torch
+
+    import gen
+    import oracle
+    import paper_1606_07550_gb300 as gpr
+
+    iters = 20
+    torch.cuda.set_device(local)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s = 1 << args.cpu_sample_scale
+        s_h, d_h = gen.rmat_coo(n_s, 32 * n_s, seed=3)
+        gs = oracle.build_csc(n_s, s_h, d_h)
+        t0 = time.perf_counter()
+        oracle.hits(gs, iters)
+        dt = time.perf_counter() - t0
+        cpu = (2 * gs.m * iters / dt / 1e9, dt,
+               f"R-MAT scale {args.cpu_sample_scale}, edge factor 32 (m={gs.m}); {iters} HITS iterations, "
+               "single-threaded FP64 oracle")
+    spec = workload("rmat25")
+    src, dst = make_coo_device(torch, spec)
+    g = gpr.graph_build(src, dst, spec.n)
+    del src, dst
+    torch.cuda.empty_cache()
+    m, n = g.info().m, spec.n
+    stream = torch.cuda.current_stream()
+    hub = torch.empty(n, device="cuda")
+    auth = torch.empty(n, device="cuda")
+    for _ in range(args.warmup):
+        gpr.hits(g, hub, auth, iters=iters, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    launches0 = gpr.lib().gpr_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            gpr.hits(g, hub, auth, iters=iters, stream=stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = gpr.lib().gpr_kernel_launches() - launches0
+    t = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    t = max_over_ranks(world, t)
+    value = sum_over_ranks(world, float(m)) * 2 * iters / (t * 1e-3) / 1e9
+    bytes_iter = 2 * (8 * m + 12 * n + 4)
+    achieved = bytes_iter * iters / (t * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    if rank != 0:
+        return
+    line = {
+        "metric": "HITS GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "hits-rmat-s25-ef32", "n": n, "m": m, "iters": iters,
+                   "step": "one hits call: 20 iterations (two pull products each) + L2 output",
+                   "value_counts": "2 m iters / time", "l2": "inputs larger than L2 (CSC 4 GiB x 2)"},
+        "roofline": {"kernel": "HITS iteration (bucketed pull SpMV on the CSC and its transpose + fold)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_kind, "bytes_model": "2 x (8m + 12n + 4) per iteration", "traffic": None},
+        "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": cpu[2],
+                                "seconds": cpu[1]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -684,6 +761,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "serve":
         run_serve(args, world, rank, local)
+    elif args.workload == "hits":
+        run_hits(args, world, rank, local)
     else:
         run_gpr(args, world, rank, local)
     if world > 1:

@@ -151,6 +151,21 @@ typedef struct {
 gpr_status pagerank_tune(const gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out,
                          void* stream);
 
+/* ---- HITS and eigenvector centrality -----------------------------------------
+ * Section 4 Table "snap_methods" names HITS and eigen-centrality among the
+ * library's centralities; the paper prints no formula.  With A[u][v] = 1 for
+ * each edge u -> v (the simple graph g holds) and h_0 = x_0 uniform:
+ *   hits:             a_t = A^T h_{t-1} / ||A^T h_{t-1}||_2,  h_t = A a_t / ||A a_t||_2
+ *   eigen_centrality: x_t = A^T x_{t-1} / ||A^T x_{t-1}||_2
+ * for `iters` >= 0 steps; a vector whose norm is 0 stays 0.  Outputs are n
+ * floats each, unit L2 norm, indexed by node id; device memory, or host
+ * memory with GPR_PTR_HOST (then the call is synchronous).  FP32 products,
+ * FP64 norms.  hits builds the graph's out-adjacency on its first call and
+ * keeps it with the graph.  Calls on one graph must not overlap in time (they
+ * share the graph's workspace with pagerank). */
+gpr_status hits(const gpr_graph* g, int32_t iters, float* hub_out, float* auth_out, int flags, void* stream);
+gpr_status eigen_centrality(const gpr_graph* g, int32_t iters, float* x_out, int flags, void* stream);
+
 /* ---- batched personalised PageRank ---------------------------------------
  * Personalised PageRank (section 4 Table "snap_methods"; section 4,
  * "Fast Random Walk Algorithms": scores from the point of view of a given

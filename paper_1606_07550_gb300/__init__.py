@@ -132,6 +132,8 @@ def lib():
         L.graph_export.argtypes = [_VP, _VP, _VP, _VP]
         L.pagerank.argtypes = [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int, ctypes.c_int, _VP,
                                ctypes.POINTER(Stats), _VP]
+        L.hits.argtypes = [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int, _VP]
+        L.eigen_centrality.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int, _VP]
         L.pagerank_tune.argtypes = [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult), _VP]
         L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                 ctypes.c_int, _VP]
@@ -148,7 +150,8 @@ def lib():
         L.serve_destroy.argtypes = [_VP]
         L.pagerank_csc_noalloc.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _VP, _VP]
         L.pagerank_csc_noalloc.restype = ctypes.c_int
-        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "pagerank_tune", "ppr_batch",
+        for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "pagerank_tune", "hits",
+                     "eigen_centrality", "ppr_batch",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
                      "serve_destroy", "serve_completed"):
             getattr(L, name).restype = ctypes.c_int
@@ -253,6 +256,22 @@ def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int =
     _check(lib().pagerank(g.handle, damping, iters, dtype, flags, po,
                           ctypes.byref(st) if st is not None else None, _stream_ptr(stream)))
     return st
+
+
+def hits(g: Graph, hub_out, auth_out, iters: int = 50, stream=None):
+    """HITS hubs and authorities (unit L2 norm, by node id) into two CUDA
+    tensors, or host arrays / CPU tensors."""
+    ph, host = _ptr_and_flag(hub_out)
+    pa, host2 = _ptr_and_flag(auth_out)
+    if host != host2:
+        raise ValueError("hub_out and auth_out must both be on the device or both on the host")
+    _check(lib().hits(g.handle, iters, ph, pa, PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
+
+
+def eigen_centrality(g: Graph, out, iters: int = 50, stream=None):
+    """Eigenvector centrality (unit L2 norm, by node id) into `out`."""
+    po, host = _ptr_and_flag(out)
+    _check(lib().eigen_centrality(g.handle, iters, po, PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
 
 
 def pagerank_tune(g: Graph, dtype: int = FP32, trial_steps: int = 5, stream=None) -> TuneResult:

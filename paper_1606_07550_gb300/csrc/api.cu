@@ -10,11 +10,18 @@ gpr_status build_graph(const int32_t* src, const int32_t* dst, int64_t m_raw, in
 gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype dt, int flags, float* x_out,
                         gpr_stats* st, cudaStream_t s);
 gpr_status run_pagerank_tune(gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out, cudaStream_t s);
+gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, float* out_hub, int flags,
+                          cudaStream_t s);
 gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
                          cudaStream_t s);
 
 void graph_free_device(gpr_graph* g, cudaStream_t s) {
   if (!g) return;
+  if (g->transposed) {
+    graph_free_device(g->transposed, s);
+    delete g->transposed;
+    g->transposed = nullptr;
+  }
   if (g->work) {
     pagerank_work_free(g->work);
     g->work = nullptr;
@@ -155,6 +162,44 @@ gpr_status pagerank_tune(const gpr_graph* g, gpr_dtype dt, int32_t trial_steps, 
     return GPR_EINVAL;
   }
   return run_pagerank_tune(const_cast<gpr_graph*>(g), dt, trial_steps, out, (cudaStream_t)stream);
+}
+
+static gpr_status check_centrality(const char* what, const gpr_graph* g, int32_t iters, int flags) {
+  if (!g) {
+    set_error("%s: NULL graph", what);
+    return GPR_EINVAL;
+  }
+  if (iters < 0 || iters > (1 << 20)) {
+    set_error("%s: iters %d outside [0, 2^20]", what, (int)iters);
+    return GPR_EINVAL;
+  }
+  if (flags & ~GPR_PTR_HOST) {
+    set_error("%s: unknown flags 0x%x", what, flags);
+    return GPR_EINVAL;
+  }
+  return GPR_OK;
+}
+
+gpr_status hits(const gpr_graph* g, int32_t iters, float* hub_out, float* auth_out, int flags, void* stream) {
+  clear_error();
+  gpr_status st = check_centrality("hits", g, iters, flags);
+  if (st != GPR_OK) return st;
+  if (!hub_out || !auth_out) {
+    set_error("hits: NULL output");
+    return GPR_EINVAL;
+  }
+  return run_centrality(const_cast<gpr_graph*>(g), 1, iters, auth_out, hub_out, flags, (cudaStream_t)stream);
+}
+
+gpr_status eigen_centrality(const gpr_graph* g, int32_t iters, float* x_out, int flags, void* stream) {
+  clear_error();
+  gpr_status st = check_centrality("eigen_centrality", g, iters, flags);
+  if (st != GPR_OK) return st;
+  if (!x_out) {
+    set_error("eigen_centrality: NULL output");
+    return GPR_EINVAL;
+  }
+  return run_centrality(const_cast<gpr_graph*>(g), 0, iters, x_out, nullptr, flags, (cudaStream_t)stream);
 }
 
 gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,

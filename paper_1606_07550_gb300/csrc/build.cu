@@ -554,6 +554,18 @@ static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b,
   return m;
 }
 
+// Keys (src << b | dst) of every edge of a CSC, in CSC order: one warp per row.
+__global__ void transpose_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                                      int32_t n, int b, uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < n; p += nwarps) {
+    const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+    for (int32_t e = e0 + lane; e < e1; e += 32) keys[e] = ((uint64_t)(uint32_t)row_idx[e] << b) | (uint64_t)p;
+  }
+}
+
 void graph_free_device(gpr_graph* g, cudaStream_t s);
 void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
 
@@ -671,6 +683,54 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     delete g;
     set_error("graph_build: %s failed: %s", f.what, cudaGetErrorString(f.err));
     return GPR_ECUDA;
+  }
+}
+
+// The out-adjacency of g as a CSC over the same relabelled ids: the keys
+// (src, dst) of g's edges sorted and laid out like a build's, with its own
+// execution plan.  Its `outdeg` counts in-degrees of g.
+gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s) {
+  gpr_graph* t = new gpr_graph();
+  t->n = g->n;
+  t->m_raw = g->m;
+  t->id_bits = g->id_bits;
+  t->device = g->device;
+  Temps tmp{s, {}};
+  const int32_t n = g->n;
+  const int b = g->id_bits;
+  try {
+    int* derr = (int*)tmp.get(sizeof(int) * 2);
+    GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
+    t->col_ptr = (int32_t*)dalloc(((size_t)n + 1) * 4, s);
+    t->outdeg = (int32_t*)dalloc((size_t)n * 4, s);
+    t->row_idx = (int32_t*)dalloc((size_t)std::max<int64_t>(g->m, 1) * 4, s);
+    int64_t m = 0;
+    if (g->m > 0) {
+      uint64_t* keys = (uint64_t*)tmp.get((size_t)g->m * 8);
+      uint64_t* alt = (uint64_t*)tmp.get((size_t)g->m * 8);
+      transpose_keys_kernel<<<grid_for(n), kThreads, 0, s>>>(g->col_ptr, g->row_idx, n, b, keys);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      m = keys_to_csc(keys, alt, g->m, b, n, nullptr, t->col_ptr, t->row_idx, t->outdeg, derr, tmp, s);
+    } else {
+      GPR_CUDA(cudaMemsetAsync(t->col_ptr, 0, ((size_t)n + 1) * 4, s));
+      GPR_CUDA(cudaMemsetAsync(t->outdeg, 0, (size_t)n * 4, s));
+    }
+    t->m = m;
+    plan_build(t, s, derr);
+    int herr = 0;
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    tmp.release();
+    if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "transposed graph: a device-side wait timed out"};
+    if (m != g->m) throw StatusFail{GPR_ECUDA, "transposed graph: edge count differs from the graph's"};
+    return t;
+  } catch (...) {
+    tmp.release();
+    graph_free_device(t, s);
+    cudaStreamSynchronize(s);
+    delete t;
+    throw;
   }
 }
 

@@ -129,12 +129,18 @@ struct gpr_graph {
   int32_t* outdeg = nullptr;   // n
   gpr::Plan plan;
   int64_t device_bytes = 0;
-  std::mutex mu;                    // guards `work`
+  std::mutex mu;                    // guards `work` and `transposed`
   gpr::PagerankWork* work = nullptr;  // lazily made by pagerank()
+  // the out-adjacency as a CSC over the same relabelled ids (row u lists the
+  // destinations of u, ascending), made by the first call that needs it
+  gpr_graph* transposed = nullptr;
 };
 
 namespace gpr {
 void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
+// The transposed graph of g (throws StatusFail / CudaFail).
+gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s);
+void graph_free_device(gpr_graph* g, cudaStream_t s);
 gpr_status export_graph(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg);
 void plan_free(Plan& p, cudaStream_t s);
 void pagerank_work_free(PagerankWork* w);

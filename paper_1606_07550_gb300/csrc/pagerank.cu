@@ -307,6 +307,7 @@ struct PagerankWork {
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kMaxBuckets] = {};
   Blocked* blk = nullptr;  // the blocked schedule's edge layout, made on first use
+  float* ones = nullptr;   // n ones: unit weights for the centralities
   bool tuned = false;      // `choice` was measured on this graph
   Choice choice;
   cudaGraphExec_t exec = nullptr;
@@ -326,6 +327,7 @@ void pagerank_work_free(PagerankWork* w) {
     dfree(w->c[i], s);
   }
   dfree(w->out_tmp, s);
+  dfree(w->ones, s);
   dfree(w->y_hot, s);
   dfree(w->partials, s);
   dfree(w->chunk_sum, s);
@@ -387,7 +389,7 @@ static int grid_for_bucket(const Bucket& b, int32_t nchunks) {
 template <typename T>
 static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_graph* g, const float* y_hot,
                           const T* c_in, const float* x_in, float* x_out, T* c_out, float* chunk_sum,
-                          const StepParams* prm, double* part) {
+                          const StepParams* prm, double* part, const float* inv_deg) {
   const Plan& P = g->plan;
   // only warp-per-row rows are split; narrower buckets read their whole rows
   const bool split_rows = P.hot_H > 0 && b.lanes == 32;
@@ -395,7 +397,7 @@ static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_g
   if (!split_rows) y_hot = nullptr;
 #define GPR_ROWS(GL)                                                                                            \
   rows_kernel<GL, T><<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, P.rows, b.row_begin, b.row_end, split, y_hot, \
-                                          c_in, x_in, P.inv_deg, x_out, c_out, prm, part)
+                                          c_in, x_in, inv_deg, x_out, c_out, prm, part)
   switch (b.lanes) {
     case 1: GPR_ROWS(1); break;
     case 2: GPR_ROWS(2); break;
@@ -451,7 +453,7 @@ static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, int 
     for (int bi = 0; bi < P.nbuckets; ++bi) {
       GPR_CUDA(cudaStreamWaitEvent(w->side[bi], w->ev_fork, 0));
       launch_bucket<T>(P.bucket[bi], w->shape[bi].grid, w->side[bi], g, hot ? w->y_hot : nullptr, c[a], x[a], x[b],
-                       c[b], w->chunk_sum, w->prm, w->partials + 3 * (int64_t)w->shape[bi].partial_off);
+                       c[b], w->chunk_sum, w->prm, w->partials + 3 * (int64_t)w->shape[bi].partial_off, P.inv_deg);
       GPR_CUDA(cudaEventRecord(w->ev_join[bi], w->side[bi]));
       GPR_CUDA(cudaStreamWaitEvent(s, w->ev_join[bi], 0));
     }
@@ -771,6 +773,182 @@ gpr_status run_pagerank_tune(gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gp
   } catch (const CudaFail& f) {
     cudaGetLastError();
     set_error("pagerank_tune: %s failed: %s", f.what, cudaGetErrorString(f.err));
+    return GPR_ECUDA;
+  }
+}
+
+// ---- HITS and eigenvector centrality ------------------------------------------
+// (section 4 Table "snap_methods" names both).  The power iterations
+//   authorities a = A^T h,  hubs h = A a   (HITS)
+//   x = A^T x                              (eigenvector centrality)
+// run on the pull kernels of the PageRank step with unit weights (an
+// inverse-degree vector of ones) and d = 1: each step's fold leaves
+// coefA = 1 / ||previous vector||_1, so every product starts from the L1-
+// normalised previous vector.  Scaling does not change a direction, so the
+// vectors match the L2-normalised iteration; the output is scaled to unit L2
+// norm once, at the end.  A^T x pulls over g's CSC; A x pulls over the CSC of
+// the transposed graph (same relabelled ids), built on first use.
+
+__global__ void fill_kernel(float* __restrict__ p, float v, int32_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// Block partials of sum x^2 (FP32 per thread, FP64 across warps).
+__global__ void sumsq_kernel(const float* __restrict__ x, int32_t n, double* __restrict__ partials) {
+  float a = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a = fmaf(x[i], x[i], a);
+  block_partials3(a, 0.f, 0.f, partials + 3 * (int64_t)blockIdx.x);
+}
+
+// out[v] = x[old2new[v]] / ||x||_2, the norm folded from the partials in
+// index order by every block (0 stays 0).
+__global__ void l2_output_kernel(const float* __restrict__ x, const int32_t* __restrict__ old2new, int32_t n,
+                                 const double* __restrict__ partials, int32_t np, float* __restrict__ out) {
+  __shared__ float s_inv;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int32_t i = 0; i < np; ++i) t += partials[3 * (int64_t)i];
+    s_inv = t > 0.0 ? (float)(1.0 / sqrt(t)) : 0.f;
+  }
+  __syncthreads();
+  const float inv = s_inv;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = x[old2new[v]] * inv;
+}
+
+// One pull step of g's kernels on stream s: x_out = coefA * (A-pull of c_in),
+// c_out = x_out * inv_deg, partials folded into prm and log_row.
+static void launch_pull_step(gpr_graph* g, PagerankWork* w, cudaStream_t s, const float* c_in, const float* x_in,
+                             float* x_out, float* c_out, const float* inv_deg, StepParams* prm, double* log_row) {
+  const Plan& P = g->plan;
+  if (w->hot_grid > 0) {
+    HotLayout hl{};
+    hl.nb = P.nbuckets;
+    for (int k = 0; k < P.nbuckets; ++k) {
+      hl.lanes[k] = P.bucket[k].lanes == 32 ? 32 : 0;
+      hl.begin[k] = P.bucket[k].row_begin;
+      hl.end[k] = P.bucket[k].row_end;
+    }
+    hot_kernel<float><<<w->hot_grid, 1024, w->hot_smem32, s>>>(g->col_ptr, g->row_idx, P.rows, hl, P.split, c_in,
+                                                              P.hot_H, P.chunk_begin, P.chunk_end, P.n_hot_chunks,
+                                                              w->y_hot, w->chunk_sum);
+    count_launches(1);
+  }
+  GPR_CUDA(cudaEventRecord(w->ev_fork, s));
+  for (int bi = 0; bi < P.nbuckets; ++bi) {
+    GPR_CUDA(cudaStreamWaitEvent(w->side[bi], w->ev_fork, 0));
+    launch_bucket<float>(P.bucket[bi], w->shape[bi].grid, w->side[bi], g, w->hot_grid > 0 ? w->y_hot : nullptr, c_in,
+                         x_in, x_out, c_out, w->chunk_sum, prm, w->partials + 3 * (int64_t)w->shape[bi].partial_off,
+                         inv_deg);
+    GPR_CUDA(cudaEventRecord(w->ev_join[bi], w->side[bi]));
+    GPR_CUDA(cudaStreamWaitEvent(s, w->ev_join[bi], 0));
+  }
+  finish_kernel<float><<<w->finish_grid, 256, 0, s>>>(x_in, inv_deg, x_out, c_out, P.split_row, P.split_hbeg,
+                                                      P.split_hend, P.split_cbeg, P.split_cend, P.nsplit,
+                                                      w->chunk_sum, w->partials, w->npartials, prm, log_row,
+                                                      w->arrive);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(P.nbuckets + 1);
+}
+
+static void ensure_log(PagerankWork* w, int32_t rows, cudaStream_t s) {
+  if (w->log_cap >= rows) return;
+  drop_exec(w);  // the captured PageRank loop writes into the old log
+  dfree(w->log, s);
+  w->log = nullptr;
+  w->log_cap = 0;
+  const int32_t cap = std::max(rows, 128);
+  w->log = (double*)dalloc((size_t)cap * 3 * sizeof(double), s);
+  w->log_cap = cap;
+}
+
+// out (device or, with GPR_PTR_HOST, host) = x / ||x||_2 by caller id.
+static void write_l2_output(gpr_graph* g, PagerankWork* w, const float* x, float* out, int flags, cudaStream_t s) {
+  const int32_t n = g->n;
+  float* dst = out;
+  if (flags & GPR_PTR_HOST) {
+    if (!w->out_tmp) w->out_tmp = (float*)dalloc((size_t)n * 4, s);
+    dst = w->out_tmp;
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)w->npartials));
+  sumsq_kernel<<<grid, 256, 0, s>>>(x, n, w->partials);
+  l2_output_kernel<<<grid, 256, 0, s>>>(x, g->plan.old2new, n, w->partials, grid, dst);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(2);
+  if (flags & GPR_PTR_HOST) {
+    GPR_CUDA(cudaMemcpyAsync(out, dst, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+// kind 0: eigenvector centrality into out_x; kind 1: HITS into out_hub and out_auth.
+gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, float* out_hub, int flags,
+                          cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g->mu);
+  try {
+    if (!g->work) g->work = work_make(g, s);
+    PagerankWork* w = g->work;
+    const int32_t n = g->n;
+    if (!w->ones) {
+      w->ones = (float*)dalloc((size_t)n * 4, s);
+      fill_kernel<<<(int)std::min<int64_t>(((int64_t)n + 255) / 256, num_sms() * 8), 256, 0, s>>>(w->ones, 1.f, n);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+    }
+    gpr_graph* t = nullptr;
+    PagerankWork* wt = nullptr;
+    if (kind == 1) {
+      if (!g->transposed) g->transposed = build_transposed(g, s);
+      t = g->transposed;
+      if (!t->work) t->work = work_make(t, s);
+      wt = t->work;
+      // the authorities start uniform too (the output of 0 steps)
+      fill_kernel<<<(int)std::min<int64_t>(((int64_t)n + 255) / 256, num_sms() * 8), 256, 0, s>>>(w->x[0],
+                                                                                              1.f / (float)n, n);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+    }
+    ensure_log(w, 2 * iters + 2, s);
+    const StepParams hp{0.f, 0.f, 1.0, (double)n};  // d = 1: no teleport, coefA = 1 / mass
+    GPR_CUDA(cudaMemcpyAsync(w->prm, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    // the start vector: uniform (1/n; its direction is 1/sqrt(n)), its fold sets coefA = 1
+    float* x0 = kind == 1 ? wt->x[0] : w->x[0];
+    float* c0 = kind == 1 ? (float*)wt->c[0] : (float*)w->c[0];
+    init_kernel<float><<<w->init_grid, 256, 0, s>>>(x0, c0, w->ones, n, w->partials);
+    finish_kernel<float><<<1, 256, 0, s>>>(x0, w->ones, x0, c0, g->plan.split_row, g->plan.split_hbeg,
+                                          g->plan.split_hend, g->plan.split_cbeg, g->plan.split_cend, 0,
+                                          w->chunk_sum, w->partials, w->init_grid + 1, w->prm, w->log, w->arrive);
+    GPR_CUDA(cudaGetLastError());
+    count_launches(2);
+    if (kind == 0) {
+      for (int32_t it = 0; it < iters; ++it) {
+        const int a = it & 1, b = a ^ 1;
+        launch_pull_step(g, w, s, (const float*)w->c[a], w->x[a], w->x[b], (float*)w->c[b], w->ones, w->prm,
+                         w->log + 3 * (int64_t)(it + 1));
+      }
+      write_l2_output(g, w, w->x[iters & 1], out_x, flags, s);
+    } else {
+      // hubs in wt->x / wt->c[0], authorities in w->x / w->c[0]; one coefficient
+      // block, so each fold hands 1 / ||x||_1 to the other product
+      for (int32_t it = 0; it < iters; ++it) {
+        const int a = it & 1, b = a ^ 1;
+        launch_pull_step(g, w, s, (const float*)wt->c[0], w->x[a], w->x[b], (float*)w->c[0], w->ones, w->prm,
+                         w->log + 3 * (int64_t)(2 * it + 1));
+        launch_pull_step(t, wt, s, (const float*)w->c[0], wt->x[a], wt->x[b], (float*)wt->c[0], w->ones, w->prm,
+                         w->log + 3 * (int64_t)(2 * it + 2));
+      }
+      write_l2_output(g, w, wt->x[iters & 1], out_hub, flags, s);
+      write_l2_output(g, w, w->x[iters & 1], out_x, flags, s);
+    }
+    return GPR_OK;
+  } catch (const StatusFail& f) {
+    set_error("%s: %s", kind == 1 ? "hits" : "eigen_centrality", f.msg.c_str());
+    return f.st;
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    set_error("%s: %s failed: %s", kind == 1 ? "hits" : "eigen_centrality", f.what, cudaGetErrorString(f.err));
     return GPR_ECUDA;
   }
 }

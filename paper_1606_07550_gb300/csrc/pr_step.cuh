@@ -130,8 +130,10 @@ __device__ __forceinline__ void fold_step(const double* partials, int32_t nparti
     log_row[1] = dang;
     log_row[2] = res;
     const double d = prm->d, n = prm->n;
-    prm->coefA = (float)(d / mass);
-    prm->coefB = (float)((1.0 - d) / n + d * dang / (n * mass));
+    // (mass is positive for PageRank; a zero vector, possible for the
+    // centralities that share these kernels, stays zero)
+    prm->coefA = mass > 0.0 ? (float)(d / mass) : 0.f;
+    prm->coefB = (float)((1.0 - d) / n + (mass > 0.0 ? d * dang / (n * mass) : 0.0));
   }
 }
 
