@@ -59,6 +59,8 @@ def _L():
         lib.oracle_hits.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _f64p, _f64p]
         lib.oracle_eigen_centrality.restype = ctypes.c_int32
         lib.oracle_eigen_centrality.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _f64p]
+        lib.oracle_wcc.restype = ctypes.c_int32
+        lib.oracle_wcc.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
         _lib = lib
     return _lib
 
@@ -201,3 +203,14 @@ def eigen_centrality(g: CSC, iters: int = 50):
     if _L().oracle_eigen_centrality(g.n, ptrs[0], ptrs[1], iters, x.ctypes.data_as(_f64p)) < 0:
         raise ValueError("oracle_eigen_centrality: invalid arguments")
     return x
+
+
+def wcc(g: CSC):
+    """Weakly connected components: (labels, count), labels[v] = the smallest
+    node id of v's component (oracle_wcc in oracle/oracle.h)."""
+    keep, ptrs = _csc_ptrs(g)
+    labels = np.empty(g.n, np.int32)
+    k = _L().oracle_wcc(g.n, ptrs[0], ptrs[1], labels.ctypes.data_as(_i32p))
+    if k < 0:
+        raise ValueError("oracle_wcc: invalid arguments")
+    return labels, int(k)

@@ -312,3 +312,38 @@ int32_t oracle_eigen_centrality(int32_t n, const int32_t* col_ptr, const int32_t
   free(y);
   return 0;
 }
+
+/* ---- weakly connected components -----------------------------------------
+ * Union-find with path halving; each union keeps the smaller root, so a
+ * root is the smallest id of its set and labels are the roots. */
+
+static int32_t uf_find(int32_t* parent, int32_t v) {
+  while (parent[v] != v) {
+    parent[v] = parent[parent[v]];
+    v = parent[v];
+  }
+  return v;
+}
+
+int32_t oracle_wcc(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t* labels) {
+  if (n <= 0 || !col_ptr || !row_idx || !labels) return -1;
+  int32_t* parent = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  if (!parent) return -1;
+  for (int32_t v = 0; v < n; ++v) parent[v] = v;
+  for (int32_t v = 0; v < n; ++v) {
+    for (int32_t e = col_ptr[v]; e < col_ptr[v + 1]; ++e) {
+      const int32_t a = uf_find(parent, row_idx[e]), b = uf_find(parent, v);
+      if (a < b)
+        parent[b] = a;
+      else if (b < a)
+        parent[a] = b;
+    }
+  }
+  int32_t count = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    labels[v] = uf_find(parent, v);
+    if (labels[v] == v) ++count;
+  }
+  free(parent);
+  return count;
+}

@@ -90,4 +90,12 @@ int32_t oracle_hits(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, i
 int32_t oracle_eigen_centrality(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t iters,
                                 double* x);
 
+/* Weakly connected components (section 4 Table "snap_methods": connected
+ * components; section 6 Table "exp_algs" times WCC).  Reading: nodes u and v
+ * are in one component when a path joins them with edge directions ignored;
+ * labels[v] = the smallest node id of v's component (isolated nodes are
+ * their own component).  Union-find over every edge of the CSC.  Returns the
+ * number of components, or -1 on bad arguments / allocation failure. */
+int32_t oracle_wcc(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t* labels);
+
 #endif /* GPR_ORACLE_H */

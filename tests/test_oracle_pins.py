@@ -499,3 +499,65 @@ def test_hits_pins_catch_planted_mistakes(mutation):
     assert not ok
     hub, auth = _mutant_hits(g, 3, "none")
     assert np.allclose(hub[:p], 1 / np.sqrt(p)) and np.allclose(auth[p:], 1 / np.sqrt(q))
+
+
+# ------------------------------------------ weakly connected components --
+# Pins: brute-force search over the undirected edge set, scipy's weak
+# components (compared as partitions), closed forms and invariants.
+
+def brute_wcc(n, src, dst):
+    adj = [set() for _ in range(n)]
+    for u, v in zip(src, dst):
+        if u != v:
+            adj[int(u)].add(int(v))
+            adj[int(v)].add(int(u))
+    lab = [-1] * n
+    for s in range(n):
+        if lab[s] >= 0:
+            continue
+        lab[s] = s
+        stack = [s]
+        while stack:
+            u = stack.pop()
+            for w in adj[u]:
+                if lab[w] < 0:
+                    lab[w] = s
+                    stack.append(w)
+    return np.array(lab, np.int32)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_wcc_matches_brute_force_and_scipy(seed):
+    import scipy.sparse
+    import scipy.sparse.csgraph
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(1, 300))
+    m_raw = int(rng.integers(0, 2 * n))
+    src, dst = random_coo(rng, n, m_raw)
+    g = oracle.build_csc(n, src, dst)
+    lab, k = oracle.wcc(g)
+    ref = brute_wcc(n, src, dst)
+    assert (lab == ref).all()
+    A = scipy.sparse.csr_matrix((np.ones(len(src)), (src, dst)), shape=(n, n))
+    k2, sl = scipy.sparse.csgraph.connected_components(A, directed=True, connection="weak")
+    assert k == k2
+    # the same partition: equal scipy labels <=> equal oracle labels
+    pairs = set(zip(sl.tolist(), lab.tolist()))
+    assert len(pairs) == k
+    # invariants: a label is the smallest id of its component and labels itself
+    assert (lab <= np.arange(n)).all() and (lab[lab] == lab).all()
+
+
+def test_wcc_closed_forms():
+    N = 50
+    path = csc_from_edges(N, [(i + 1, i) if i % 2 else (i, i + 1) for i in range(N - 1)])
+    lab, k = oracle.wcc(path)
+    assert k == 1 and (lab == 0).all()
+    lab, k = oracle.wcc(csc_from_edges(N, []))
+    assert k == N and (lab == np.arange(N)).all()
+    # two stars joined by nothing, hub ids larger than their leaves
+    edges = [(10, i) for i in range(5)] + [(i, 30) for i in range(20, 25)]
+    lab, k = oracle.wcc(csc_from_edges(40, edges))
+    assert k == 40 - 5 - 5
+    assert (lab[[0, 1, 2, 3, 4, 10]] == 0).all() and (lab[[20, 21, 22, 23, 24, 30]] == 20).all()
+    assert lab[39] == 39
