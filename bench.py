@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpr", "reference"], default="gpr")
-    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits"], default="rmat25")
+    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits", "wcc"],
+                    default="rmat25")
     ap.add_argument("--graphs", type=int, default=4096, help="batched: number of graphs")
     ap.add_argument("--dtypes", default="fp32,bf16,fp16", help="batched: contribution storage types")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -752,6 +753,88 @@ def run_hits(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_wcc(args, world, rank, local):
+    """Weakly connected components of the R-MAT scale-25 graph (edge factor
+    32), built before the timed region; each step is one `wcc` call.  GTEPS
+    counts m edges per call.  Also times a binary save and load of the same
+    graph through a temporary file (the paper's save/load measurement)."""
+    import tempfile
+
+    import torch
+
+    import gen
+    import oracle
+    import paper_1606_07550_gb300 as gpr
+
+    torch.cuda.set_device(local)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s = 1 << args.cpu_sample_scale
+        s_h, d_h = gen.rmat_coo(n_s, 32 * n_s, seed=3)
+        gs = oracle.build_csc(n_s, s_h, d_h)
+        t0 = time.perf_counter()
+        oracle.wcc(gs)
+        dt = time.perf_counter() - t0
+        cpu = (gs.m / dt / 1e9, dt, f"R-MAT scale {args.cpu_sample_scale}, edge factor 32 (m={gs.m}); union-find, "
+                                    "single-threaded oracle")
+    spec = workload("rmat25")
+    src, dst = make_coo_device(torch, spec)
+    g = gpr.graph_build(src, dst, spec.n)
+    del src, dst
+    torch.cuda.empty_cache()
+    m, n = g.info().m, spec.n
+    stream = torch.cuda.current_stream()
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        k = gpr.wcc(g, labels, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    launches0 = gpr.lib().gpr_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            k = gpr.wcc(g, labels, stream=stream)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = gpr.lib().gpr_kernel_launches() - launches0
+    t = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in evs) / args.steps)
+    value = sum_over_ranks(world, float(m)) / (t * 1e-3) / 1e9
+    io = None
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "g.bin")
+        t0 = time.perf_counter()
+        g.save(path)
+        t_save = time.perf_counter() - t0
+        size = os.path.getsize(path)
+        t0 = time.perf_counter()
+        h = gpr.graph_load(path)
+        torch.cuda.synchronize()
+        t_load = time.perf_counter() - t0
+        h.free()
+        io = {"file_bytes": size, "save_s": t_save, "load_s": t_load, "save_gb_per_s": size / t_save / 1e9,
+              "load_gb_per_s": size / t_load / 1e9}
+    if rank != 0:
+        return
+    line = {
+        "metric": "WCC GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "wcc-rmat-s25-ef32", "n": n, "m": m, "components": k,
+                   "step": "one wcc call: hook/compress rounds to convergence + labels by caller id",
+                   "value_counts": "m / time"},
+        "clocks": clk.summary(), "gpu_launches": launches, "save_load": io,
+    }
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": cpu[2],
+                                "seconds": cpu[1]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -763,6 +846,8 @@ def main():
         run_serve(args, world, rank, local)
     elif args.workload == "hits":
         run_hits(args, world, rank, local)
+    elif args.workload == "wcc":
+        run_wcc(args, world, rank, local)
     else:
         run_gpr(args, world, rank, local)
     if world > 1:

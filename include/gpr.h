@@ -113,6 +113,18 @@ gpr_status graph_info(const gpr_graph* g, gpr_graph_info* info);
  * outdeg (n); any pointer may be NULL to skip it.  Synchronous. */
 gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg);
 
+/* Binary save and load (section 3, Table "exp_basic": graphs are saved to
+ * and loaded from a binary format).  graph_save writes the graph as the
+ * library holds it (relabelled CSC and its permutation, little-endian) to
+ * `path`; synchronous, GPR_EINVAL if the file cannot be written.  graph_load
+ * reads such a file, checks it (header, sizes, offsets, sorted in-range
+ * sources without self-loops, the permutation) and builds the graph with no
+ * sort; GPR_ENOTFOUND if the file cannot be opened, GPR_EINVAL if it is not
+ * a well-formed graph file.  A loaded graph is bit-identical to the saved one:
+ * graph_export and every computation on it give the same bits. */
+gpr_status graph_save(const gpr_graph* g, const char* path);
+gpr_status graph_load(const char* path, void* stream, gpr_graph** out);
+
 /* ---- PageRank ------------------------------------------------------------
  * pagerank: `iters` steps of PageRank power iteration (section 4 Table
  * "snap_methods"; the fixed iteration count follows section 6 Table
@@ -165,6 +177,17 @@ gpr_status pagerank_tune(const gpr_graph* g, gpr_dtype dt, int32_t trial_steps, 
  * share the graph's workspace with pagerank). */
 gpr_status hits(const gpr_graph* g, int32_t iters, float* hub_out, float* auth_out, int flags, void* stream);
 gpr_status eigen_centrality(const gpr_graph* g, int32_t iters, float* x_out, int flags, void* stream);
+
+/* ---- weakly connected components ------------------------------------------
+ * wcc: the components of g with edge directions ignored (section 4 Table
+ * "snap_methods": connected components; section 6 Table "exp_algs" times
+ * WCC).  labels_out (n int32, by node id; device memory, or host memory with
+ * GPR_PTR_HOST) receives for each node the smallest node id of its
+ * component, so the output does not depend on scheduling; num_components
+ * (host, nullable) receives the number of components (isolated nodes count).
+ * Synchronous.  GPR_ETIMEOUT if the hook rounds do not converge (not
+ * expected: a bound that turns a fault into an error). */
+gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components, int flags, void* stream);
 
 /* ---- batched personalised PageRank ---------------------------------------
  * Personalised PageRank (section 4 Table "snap_methods"; section 4,

@@ -134,6 +134,9 @@ def lib():
                                ctypes.POINTER(Stats), _VP]
         L.hits.argtypes = [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int, _VP]
         L.eigen_centrality.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int, _VP]
+        L.graph_save.argtypes = [_VP, ctypes.c_char_p]
+        L.graph_load.argtypes = [ctypes.c_char_p, _VP, ctypes.POINTER(_VP)]
+        L.wcc.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, _VP]
         L.pagerank_tune.argtypes = [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult), _VP]
         L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                 ctypes.c_int, _VP]
@@ -151,7 +154,7 @@ def lib():
         L.pagerank_csc_noalloc.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _VP, _VP]
         L.pagerank_csc_noalloc.restype = ctypes.c_int
         for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "pagerank_tune", "hits",
-                     "eigen_centrality", "ppr_batch",
+                     "eigen_centrality", "wcc", "graph_save", "graph_load", "ppr_batch",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
                      "serve_destroy", "serve_completed"):
             getattr(L, name).restype = ctypes.c_int
@@ -216,6 +219,10 @@ class Graph:
         _check(lib().graph_export(self.handle, cp.ctypes.data, ri.ctypes.data, od.ctypes.data))
         return cp, ri[: inf.m], od
 
+    def save(self, path: str):
+        """Binary save (see graph_save in include/gpr.h)."""
+        _check(lib().graph_save(self.handle, os.fsencode(path)))
+
     def free(self):
         if self._h:
             h, self._h = self._h, None
@@ -242,6 +249,13 @@ def graph_build(src, dst, n: int, stream=None) -> Graph:
     h = _VP()
     _check(lib().graph_build(ps, pd, len(src), n, PTR_HOST if hs else PTR_DEVICE, _stream_ptr(stream),
                              ctypes.byref(h)))
+    return Graph(h.value)
+
+
+def graph_load(path: str, stream=None) -> Graph:
+    """A graph saved by Graph.save (see graph_load in include/gpr.h)."""
+    h = _VP()
+    _check(lib().graph_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(h)))
     return Graph(h.value)
 
 
@@ -272,6 +286,16 @@ def eigen_centrality(g: Graph, out, iters: int = 50, stream=None):
     """Eigenvector centrality (unit L2 norm, by node id) into `out`."""
     po, host = _ptr_and_flag(out)
     _check(lib().eigen_centrality(g.handle, iters, po, PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
+
+
+def wcc(g: Graph, out, stream=None) -> int:
+    """Weakly connected components: out[v] (int32, by node id; CUDA tensor or
+    host array) = the smallest node id of v's component.  Returns the number
+    of components."""
+    po, host = _ptr_and_flag(out)
+    k = ctypes.c_int32(0)
+    _check(lib().wcc(g.handle, po, ctypes.byref(k), PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
+    return int(k.value)
 
 
 def pagerank_tune(g: Graph, dtype: int = FP32, trial_steps: int = 5, stream=None) -> TuneResult:

@@ -12,6 +12,9 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
 gpr_status run_pagerank_tune(gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out, cudaStream_t s);
 gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, float* out_hub, int flags,
                           cudaStream_t s);
+gpr_status run_wcc(gpr_graph* g, int32_t* labels_out, int32_t* num_components, int flags, cudaStream_t s);
+gpr_status save_graph(const gpr_graph* g, const char* path);
+gpr_status load_graph(const char* path, cudaStream_t s, gpr_graph** out);
 gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
                          cudaStream_t s);
 
@@ -92,6 +95,27 @@ gpr_status graph_free(gpr_graph* g) {
     return GPR_ECUDA;
   }
   return GPR_OK;
+}
+
+gpr_status graph_save(const gpr_graph* g, const char* path) {
+  clear_error();
+  if (!g || !path) {
+    set_error("graph_save: NULL graph or path");
+    return GPR_EINVAL;
+  }
+  return save_graph(g, path);
+}
+
+gpr_status graph_load(const char* path, void* stream, gpr_graph** out) {
+  clear_error();
+  if (!path || !out) {
+    set_error("graph_load: NULL path or out");
+    return GPR_EINVAL;
+  }
+  *out = nullptr;
+  gpr_status st = load_graph(path, (cudaStream_t)stream, out);
+  if (st == GPR_OK) (*out)->device_bytes = graph_bytes(*out);
+  return st;
 }
 
 gpr_status graph_info(const gpr_graph* g, gpr_graph_info* info) {
@@ -200,6 +224,19 @@ gpr_status eigen_centrality(const gpr_graph* g, int32_t iters, float* x_out, int
     return GPR_EINVAL;
   }
   return run_centrality(const_cast<gpr_graph*>(g), 0, iters, x_out, nullptr, flags, (cudaStream_t)stream);
+}
+
+gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components, int flags, void* stream) {
+  clear_error();
+  if (!g || !labels_out) {
+    set_error("wcc: NULL graph or output");
+    return GPR_EINVAL;
+  }
+  if (flags & ~GPR_PTR_HOST) {
+    set_error("wcc: unknown flags 0x%x", flags);
+    return GPR_EINVAL;
+  }
+  return run_wcc(const_cast<gpr_graph*>(g), labels_out, num_components, flags, (cudaStream_t)stream);
 }
 
 gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
