@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpr", "reference"], default="gpr")
-    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits", "wcc"],
+    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits", "wcc", "dynamic"],
                     default="rmat25")
     ap.add_argument("--graphs", type=int, default=4096, help="batched: number of graphs")
     ap.add_argument("--dtypes", default="fp32,bf16,fp16", help="batched: contribution storage types")
@@ -835,6 +835,78 @@ def run_wcc(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_dynamic(args, world, rank, local):
+    """Dynamic graph (the paper's section 5 theme; Table "exp_del" times
+    deletions): the R-MAT scale-25 graph (edge factor 32) takes, per step, one
+    graph_update of 2^20 random insertions and 2^20 deletions of existing
+    edges, then a 10-step PageRank warm-started from the previous ranks.
+    value = updated edges per second of graph_update; the warm PageRank is
+    reported beside it."""
+    import torch
+
+    import paper_1606_07550_gb300 as gpr
+
+    torch.cuda.set_device(local)
+    spec = workload("rmat25")
+    src, dst = make_coo_device(torch, spec)
+    g = gpr.graph_build(src, dst, spec.n)
+    n = spec.n
+    k = 1 << 20
+    gen_ = torch.Generator(device="cuda")
+    gen_.manual_seed(11)
+    x = torch.empty(n, device="cuda")
+    gpr.pagerank(g, x, iters=30)
+    stream = torch.cuda.current_stream()
+
+    def batch():
+        pick = torch.randint(0, src.numel(), (k,), device="cuda", generator=gen_)
+        ins_s = torch.randint(0, n, (k,), device="cuda", dtype=torch.int32, generator=gen_)
+        ins_d = torch.randint(0, n, (k,), device="cuda", dtype=torch.int32, generator=gen_)
+        return (ins_s, ins_d), (src[pick].contiguous(), dst[pick].contiguous())
+
+    for _ in range(args.warmup):
+        ins, dels = batch()
+        gpr.graph_update(g, ins, dels, stream=stream)
+        gpr.pagerank(g, x, iters=10, warm_start=True, stream=stream)
+    torch.cuda.synchronize()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    launches0 = gpr.lib().gpr_kernel_launches()
+    t_upd, t_pr = [], []
+    barrier(world)
+    with ClockSampler(gpu_index) as clk:
+        for _ in range(args.steps):
+            ins, dels = batch()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            c = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gpr.graph_update(g, ins, dels, stream=stream)
+            b.record(stream)
+            gpr.pagerank(g, x, iters=10, warm_start=True, stream=stream)
+            c.record(stream)
+            torch.cuda.synchronize()
+            t_upd.append(a.elapsed_time(b))
+            t_pr.append(b.elapsed_time(c))
+    barrier(world)
+    launches = gpr.lib().gpr_kernel_launches() - launches0
+    tu = max_over_ranks(world, sum(t_upd) / len(t_upd))
+    tp = sum(t_pr) / len(t_pr)
+    value = sum_over_ranks(world, 2.0 * k) / (tu * 1e-3)
+    if rank != 0:
+        return
+    line = {
+        "metric": "edge updates/s", "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tu, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "dynamic-rmat-s25-ef32", "n": n, "m_after": g.info().m, "insertions": k,
+                   "deletions": k, "step": "graph_update (2^20 inserts + 2^20 deletes), then 10 warm PageRank steps"},
+        "warm_pagerank_ms": tp, "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -848,6 +920,8 @@ def main():
         run_hits(args, world, rank, local)
     elif args.workload == "wcc":
         run_wcc(args, world, rank, local)
+    elif args.workload == "dynamic":
+        run_dynamic(args, world, rank, local)
     else:
         run_gpr(args, world, rank, local)
     if world > 1:

@@ -58,6 +58,9 @@ typedef enum { GPR_FP32 = 0, GPR_BF16 = 1, GPR_FP16 = 2 } gpr_dtype;
 /* Schedule of the PageRank step (pagerank only; neither: the library's choice) */
 #define GPR_SPMV_PULL 0x10    /* one gather per edge, rows by in-degree bucket */
 #define GPR_SPMV_BLOCKED 0x20 /* two streaming phases over a bin-major edge copy */
+/* pagerank only: start from the vector in x_out (n floats by node id, e.g. the
+ * result before a graph_update) instead of the uniform vector */
+#define GPR_WARM_START 0x40
 
 /* A directed simple graph resident in device memory: the CSC (in-adjacency,
  * sources ascending within each destination), out-degrees, and an execution
@@ -122,6 +125,18 @@ gpr_status graph_export(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, 
  * sort; GPR_ENOTFOUND if the file cannot be opened, GPR_EINVAL if it is not
  * a well-formed graph file.  A loaded graph is bit-identical to the saved one:
  * graph_export and every computation on it give the same bits. */
+/* graph_update: edge insertions and deletions in place (section 5: SNAP's
+ * graphs are dynamic; section 6 Table "exp_del" times deletions).  The new
+ * edge set is E' = (E \ D) u I, with D the pairs (del_src[i], del_dst[i])
+ * and I the pairs (ins_src[i], ins_dst[i]) (node ids in [0, n); n stays;
+ * self-loops in I are dropped, deleting a missing edge does nothing, repeats
+ * count once).  Arrays are device memory, or host memory with GPR_PTR_HOST;
+ * either batch may be empty (count 0, NULL arrays).  The graph keeps its
+ * internal numbering; its workspaces are dropped and rebuilt on next use.
+ * Synchronous.  GPR_EINVAL (graph unchanged) if an id is out of range. */
+gpr_status graph_update(gpr_graph* g, const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins,
+                        const int32_t* del_src, const int32_t* del_dst, int64_t n_del, int flags, void* stream);
+
 gpr_status graph_save(const gpr_graph* g, const char* path);
 gpr_status graph_load(const char* path, void* stream, gpr_graph** out);
 

@@ -30,6 +30,7 @@ _NAMES = ["GPR_OK", "GPR_EINVAL", "GPR_ENOMEM", "GPR_ECUDA", "GPR_ETIMEOUT", "GP
 FP32, BF16, FP16 = 0, 1, 2
 PTR_DEVICE, PTR_HOST = 0, 1
 SPMV_PULL, SPMV_BLOCKED = 0x10, 0x20
+WARM_START = 0x40
 _SPMV = {"auto": 0, "pull": SPMV_PULL, "blocked": SPMV_BLOCKED}
 
 
@@ -134,6 +135,7 @@ def lib():
                                ctypes.POINTER(Stats), _VP]
         L.hits.argtypes = [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int, _VP]
         L.eigen_centrality.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int, _VP]
+        L.graph_update.argtypes = [_VP, _VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP]
         L.graph_save.argtypes = [_VP, ctypes.c_char_p]
         L.graph_load.argtypes = [ctypes.c_char_p, _VP, ctypes.POINTER(_VP)]
         L.wcc.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, _VP]
@@ -154,7 +156,7 @@ def lib():
         L.pagerank_csc_noalloc.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _VP, _VP]
         L.pagerank_csc_noalloc.restype = ctypes.c_int
         for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "pagerank_tune", "hits",
-                     "eigen_centrality", "wcc", "graph_save", "graph_load", "ppr_batch",
+                     "eigen_centrality", "wcc", "graph_save", "graph_load", "graph_update", "ppr_batch",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
                      "serve_destroy", "serve_completed"):
             getattr(L, name).restype = ctypes.c_int
@@ -252,6 +254,30 @@ def graph_build(src, dst, n: int, stream=None) -> Graph:
     return Graph(h.value)
 
 
+def graph_update(g: Graph, ins=None, dels=None, stream=None):
+    """Insert the (src, dst) pairs `ins` and delete the pairs `dels` (each a
+    pair of equal-length int32 arrays, CUDA tensors or host arrays; None for
+    none): E' = (E minus dels) plus ins (see graph_update in include/gpr.h)."""
+    def pair(p):
+        if p is None or len(p[0]) == 0:
+            return None, None, 0, None
+        s_, d_ = p
+        if len(s_) != len(d_):
+            raise ValueError("src and dst differ in length")
+        ps, hs = _ptr_and_flag(s_)
+        pd, hd = _ptr_and_flag(d_)
+        if hs != hd:
+            raise ValueError("src and dst must both be host or both be device arrays")
+        return ps, pd, len(s_), hs
+    a, b, k1, h1 = pair(ins)
+    c, d, k2, h2 = pair(dels)
+    hosts = {h for h in (h1, h2) if h is not None}
+    if len(hosts) > 1:
+        raise ValueError("insertions and deletions must both be host or both be device arrays")
+    host = hosts.pop() if hosts else False
+    _check(lib().graph_update(g.handle, a, b, k1, c, d, k2, PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
+
+
 def graph_load(path: str, stream=None) -> Graph:
     """A graph saved by Graph.save (see graph_load in include/gpr.h)."""
     h = _VP()
@@ -260,13 +286,14 @@ def graph_load(path: str, stream=None) -> Graph:
 
 
 def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int = FP32, stream=None,
-             stats: bool = False, spmv: str = "auto"):
+             stats: bool = False, spmv: str = "auto", warm_start: bool = False):
     """Writes PageRank (n floats, by node id) into `out` (a CUDA tensor, or a
     host array / CPU tensor).  Returns a Stats if stats=True.  spmv picks the
-    step's schedule: "pull", "blocked", or "auto" (the library's choice)."""
+    step's schedule: "pull", "blocked", or "auto" (the library's choice).
+    warm_start: start from the vector `out` holds instead of uniform."""
     po, host = _ptr_and_flag(out)
     st = Stats() if stats else None
-    flags = (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv]
+    flags = (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv] | (WARM_START if warm_start else 0)
     _check(lib().pagerank(g.handle, damping, iters, dtype, flags, po,
                           ctypes.byref(st) if st is not None else None, _stream_ptr(stream)))
     return st

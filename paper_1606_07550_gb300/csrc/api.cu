@@ -15,6 +15,8 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
 gpr_status run_wcc(gpr_graph* g, int32_t* labels_out, int32_t* num_components, int flags, cudaStream_t s);
 gpr_status save_graph(const gpr_graph* g, const char* path);
 gpr_status load_graph(const char* path, cudaStream_t s, gpr_graph** out);
+gpr_status update_graph(gpr_graph* g, const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins,
+                        const int32_t* del_src, const int32_t* del_dst, int64_t n_del, int flags, cudaStream_t s);
 gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
                          cudaStream_t s);
 
@@ -97,6 +99,27 @@ gpr_status graph_free(gpr_graph* g) {
   return GPR_OK;
 }
 
+gpr_status graph_update(gpr_graph* g, const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins,
+                        const int32_t* del_src, const int32_t* del_dst, int64_t n_del, int flags, void* stream) {
+  clear_error();
+  if (!g) {
+    set_error("graph_update: NULL graph");
+    return GPR_EINVAL;
+  }
+  if (n_ins < 0 || n_del < 0 || n_ins >= ((int64_t)1 << 31) || n_del >= ((int64_t)1 << 31) ||
+      (n_ins > 0 && (!ins_src || !ins_dst)) || (n_del > 0 && (!del_src || !del_dst))) {
+    set_error("graph_update: bad batch sizes or NULL arrays");
+    return GPR_EINVAL;
+  }
+  if (flags & ~GPR_PTR_HOST) {
+    set_error("graph_update: unknown flags 0x%x", flags);
+    return GPR_EINVAL;
+  }
+  gpr_status st = update_graph(g, ins_src, ins_dst, n_ins, del_src, del_dst, n_del, flags, (cudaStream_t)stream);
+  if (st == GPR_OK) g->device_bytes = graph_bytes(g);
+  return st;
+}
+
 gpr_status graph_save(const gpr_graph* g, const char* path) {
   clear_error();
   if (!g || !path) {
@@ -162,7 +185,7 @@ gpr_status pagerank(const gpr_graph* g, double damping, int32_t iters, gpr_dtype
     set_error("pagerank: unknown dtype %d", (int)dt);
     return GPR_EINVAL;
   }
-  if ((flags & ~(GPR_PTR_HOST | GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) ||
+  if ((flags & ~(GPR_PTR_HOST | GPR_SPMV_PULL | GPR_SPMV_BLOCKED | GPR_WARM_START)) ||
       (flags & (GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) == (GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) {
     set_error("pagerank: unknown or conflicting flags 0x%x", flags);
     return GPR_EINVAL;

@@ -523,11 +523,11 @@ static int grid_for(int64_t items, int per_sm = 8) {
 // Sorted unique-or-not keys (length m_keys) -> CSC arrays; returns m.
 static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b, int32_t n, uint32_t* hist,
                            int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg, int* derr, Temps& tmp,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool presorted = false) {
   GPR_CUDA(cudaMemsetAsync(col_ptr, 0, ((size_t)n + 1) * 4, s));
   GPR_CUDA(cudaMemsetAsync(outdeg, 0, (size_t)n * 4, s));
   if (m_keys == 0) return 0;
-  uint64_t* sorted = radix_sort_u64(keys, alt, m_keys, 2 * b, s, derr, hist);
+  uint64_t* sorted = presorted ? keys : radix_sort_u64(keys, alt, m_keys, 2 * b, s, derr, hist);
   const int64_t tiles = (m_keys + kTile - 1) / kTile;
   uint64_t* status = (uint64_t*)tmp.get((size_t)tiles * 8);
   uint32_t* ctr = (uint32_t*)tmp.get(8);
@@ -731,6 +731,304 @@ gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s) {
     cudaStreamSynchronize(s);
     delete t;
     throw;
+  }
+}
+
+// ---- in-place edge updates ---------------------------------------------------
+// E' = (E \ D) u I for a batch of deletions D and insertions I (caller ids;
+// self-loops in I are dropped, deleting a missing edge does nothing).  The
+// graph's keys (row << b | source, relabelled ids) are already sorted: the
+// kept ones are compacted by a prefix scan and the sorted insert keys are
+// placed among them by rank (an insert goes before an equal kept key, so the
+// de-duplication keeps one copy), and the merged keys go through the build's
+// de-duplication and offset pass without a sort.  The node numbering stays.
+
+__global__ void check_ids_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                                 int32_t n, int* __restrict__ derr) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= (uint32_t)src[i] >= (uint32_t)n || (uint32_t)dst[i] >= (uint32_t)n;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(derr, DERR_BAD_ID);
+}
+
+// key = row << b | source for every edge of a CSC, in CSC (= key) order.
+__global__ void own_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
+                                int b, uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < n; p += nwarps)
+    for (int32_t e = col_ptr[p] + lane; e < col_ptr[p + 1]; e += 32)
+      keys[e] = ((uint64_t)p << b) | (uint64_t)(uint32_t)row_idx[e];
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (a[mid] < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t upper_bound_u64(const uint64_t* a, int64_t n, uint64_t key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (a[mid] <= key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// keep[i] = 1 unless keys[i] is among the sorted deletion keys
+__global__ void keep_kernel(const uint64_t* __restrict__ keys, int64_t m, const uint64_t* __restrict__ del,
+                            int64_t nd, int32_t* __restrict__ keep) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = lower_bound_u64(del, nd, keys[i]);
+    keep[i] = (j < nd && del[j] == keys[i]) ? 0 : 1;
+  }
+}
+
+// Exclusive scan of int32 flags in tiles of kScanTile: tile sums, one block
+// scanning the tile sums, then each tile's own scan.
+constexpr int kScanTile = 4096;
+__global__ void tile_sums_kernel(const int32_t* __restrict__ v, int64_t m, int64_t* __restrict__ sums) {
+  __shared__ int64_t s[kThreads / 32];
+  const int64_t t0 = blockIdx.x * (int64_t)kScanTile;
+  int64_t a = 0;
+  for (int64_t i = t0 + threadIdx.x; i < min(m, t0 + kScanTile); i += blockDim.x) a += v[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    sums[blockIdx.x] = t;
+  }
+}
+__global__ void scan_sums_kernel(int64_t* __restrict__ sums, int64_t nt, int64_t* __restrict__ total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t run = 0;
+  for (int64_t i = 0; i < nt; ++i) {
+    const int64_t v = sums[i];
+    sums[i] = run;
+    run += v;
+  }
+  *total = run;
+}
+__global__ void tile_scan_kernel(const int32_t* __restrict__ v, int64_t m, const int64_t* __restrict__ offs,
+                                 int32_t* __restrict__ out) {
+  __shared__ int32_t s_w[kThreads / 32];
+  const int64_t t0 = blockIdx.x * (int64_t)kScanTile;
+  constexpr int kPer = kScanTile / kThreads;  // consecutive items per thread
+  const int64_t i0 = t0 + (int64_t)threadIdx.x * kPer;
+  int32_t loc[kPer];
+  int32_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    loc[j] = i0 + j < m ? v[i0 + j] : 0;
+    sum += loc[j];
+  }
+  int32_t inc = sum;  // inclusive scan of the per-thread sums across the block
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  int32_t wo = 0;
+  for (int ww = 0; ww < w; ++ww) wo += s_w[ww];
+  int64_t run = offs[blockIdx.x] + wo + inc - sum;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    if (i0 + j < m) out[i0 + j] = (int32_t)run;
+    run += loc[j];
+  }
+}
+
+// merged[kpos[i] + #(inserts <= key)] = key for every kept old key
+__global__ void place_kept_kernel(const uint64_t* __restrict__ keys, int64_t m, const int32_t* __restrict__ keep,
+                                  const int32_t* __restrict__ kpos, const uint64_t* __restrict__ ins, int64_t ni,
+                                  uint64_t* __restrict__ merged) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    if (keep[i]) merged[(int64_t)kpos[i] + upper_bound_u64(ins, ni, keys[i])] = keys[i];
+}
+
+// merged[j + #(kept old keys < ins[j])] = ins[j]
+__global__ void place_ins_kernel(const uint64_t* __restrict__ ins, int64_t ni, const uint64_t* __restrict__ keys,
+                                 int64_t m, const int32_t* __restrict__ kpos, const int32_t* __restrict__ keep,
+                                 uint64_t* __restrict__ merged) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ni; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lb = lower_bound_u64(keys, m, ins[j]);
+    const int64_t before = lb < m ? (int64_t)kpos[lb] : (m > 0 ? (int64_t)kpos[m - 1] + keep[m - 1] : 0);
+    merged[j + before] = ins[j];
+  }
+}
+
+// Index of the first sentinel in sorted keys (the count of real keys).
+__global__ void count_real_kernel(const uint64_t* __restrict__ keys, int64_t n, int64_t* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = lower_bound_u64(keys, n, kSentinel);
+}
+
+// Sorted keys of a batch of caller-id pairs (self-loops sort last as
+// sentinels); returns the number of real keys.  Ids already checked.
+static int64_t batch_keys(const gpr_graph* g, const int32_t* src, const int32_t* dst, int64_t k, Temps& tmp,
+                          int* derr, uint64_t** out, cudaStream_t s) {
+  *out = nullptr;
+  if (k <= 0) return 0;
+  uint64_t* keys = (uint64_t*)tmp.get((size_t)k * 8);
+  uint64_t* alt = (uint64_t*)tmp.get((size_t)k * 8);
+  pack_kernel<<<grid_for(k), kThreads, 0, s>>>(src, dst, k, g->n, g->id_bits, g->plan.old2new, 0, keys, nullptr);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(1);
+  uint64_t* sorted = radix_sort_u64(keys, alt, k, 64, s, derr, nullptr);  // sentinels need every bit
+  int64_t* cnt = (int64_t*)tmp.get(8);
+  count_real_kernel<<<1, 32, 0, s>>>(sorted, k, cnt);
+  count_launches(1);
+  int64_t real = 0;
+  GPR_CUDA(cudaMemcpyAsync(&real, cnt, 8, cudaMemcpyDeviceToHost, s));
+  GPR_CUDA(cudaStreamSynchronize(s));
+  *out = sorted;
+  return real;
+}
+
+gpr_status update_graph(gpr_graph* g, const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins,
+                        const int32_t* del_src, const int32_t* del_dst, int64_t n_del, int flags, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g->mu);
+  Temps tmp{s, {}};
+  const int32_t n = g->n;
+  const int b = g->id_bits;
+  int32_t* new_col_ptr = nullptr;
+  int32_t* new_row_idx = nullptr;
+  int32_t* new_outdeg = nullptr;
+  try {
+    int* derr = (int*)tmp.get(sizeof(int) * 2);
+    GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
+    // the batches on the device, ids checked before anything changes
+    auto to_dev = [&](const int32_t* p, int64_t k) -> const int32_t* {
+      if (!(flags & GPR_PTR_HOST) || k <= 0) return p;
+      int32_t* d = (int32_t*)tmp.get((size_t)k * 4);
+      GPR_CUDA(cudaMemcpyAsync(d, p, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+      return d;
+    };
+    const int32_t* is = to_dev(ins_src, n_ins);
+    const int32_t* id = to_dev(ins_dst, n_ins);
+    const int32_t* ds = to_dev(del_src, n_del);
+    const int32_t* dd = to_dev(del_dst, n_del);
+    if (n_ins > 0) check_ids_kernel<<<grid_for(n_ins), kThreads, 0, s>>>(is, id, n_ins, n, derr);
+    if (n_del > 0) check_ids_kernel<<<grid_for(n_del), kThreads, 0, s>>>(ds, dd, n_del, n, derr);
+    GPR_CUDA(cudaGetLastError());
+    int herr = 0;
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    if (herr & DERR_BAD_ID) throw StatusFail{GPR_EINVAL, "graph_update: an edge id is outside [0, n)"};
+    uint64_t* ins = nullptr;
+    uint64_t* del = nullptr;
+    const int64_t ni = batch_keys(g, is, id, n_ins, tmp, derr, &ins, s);
+    const int64_t nd = batch_keys(g, ds, dd, n_del, tmp, derr, &del, s);
+    const int64_t m = g->m;
+    // kept old keys and their compacted positions
+    uint64_t* keys = (uint64_t*)tmp.get((size_t)std::max<int64_t>(m, 1) * 8);
+    int32_t* keep = (int32_t*)tmp.get((size_t)std::max<int64_t>(m, 1) * 4);
+    int32_t* kpos = (int32_t*)tmp.get((size_t)std::max<int64_t>(m, 1) * 4);
+    int64_t kept = 0;
+    if (m > 0) {
+      own_keys_kernel<<<grid_for(n), kThreads, 0, s>>>(g->col_ptr, g->row_idx, n, b, keys);
+      keep_kernel<<<grid_for(m), kThreads, 0, s>>>(keys, m, del, nd, keep);
+      const int64_t nt = (m + kScanTile - 1) / kScanTile;
+      int64_t* sums = (int64_t*)tmp.get((size_t)nt * 8 + 8);
+      tile_sums_kernel<<<(unsigned)nt, kThreads, 0, s>>>(keep, m, sums);
+      scan_sums_kernel<<<1, 32, 0, s>>>(sums, nt, sums + nt);
+      tile_scan_kernel<<<(unsigned)nt, kThreads, 0, s>>>(keep, m, sums, kpos);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(5);
+      GPR_CUDA(cudaMemcpyAsync(&kept, sums + nt, 8, cudaMemcpyDeviceToHost, s));
+      GPR_CUDA(cudaStreamSynchronize(s));
+    }
+    const int64_t total = kept + ni;
+    if (total >= ((int64_t)1 << 31)) throw StatusFail{GPR_EINVAL, "graph_update: more than 2^31 - 1 edges"};
+    uint64_t* merged = (uint64_t*)tmp.get((size_t)std::max<int64_t>(total, 1) * 8);
+    if (m > 0) {
+      place_kept_kernel<<<grid_for(m), kThreads, 0, s>>>(keys, m, keep, kpos, ins, ni, merged);
+      count_launches(1);
+    }
+    if (ni > 0) {
+      place_ins_kernel<<<grid_for(ni), kThreads, 0, s>>>(ins, ni, keys, m, kpos, keep, merged);
+      count_launches(1);
+    }
+    GPR_CUDA(cudaGetLastError());
+    new_col_ptr = (int32_t*)dalloc(((size_t)n + 1) * 4, s);
+    new_outdeg = (int32_t*)dalloc((size_t)n * 4, s);
+    int32_t* row_full = (int32_t*)tmp.get((size_t)std::max<int64_t>(total, 1) * 4);
+    const int64_t m2 = keys_to_csc(merged, nullptr, total, b, n, nullptr, new_col_ptr, row_full, new_outdeg, derr, tmp,
+                                   s, /*presorted=*/true);
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_update: a device-side wait timed out"};
+    new_row_idx = (int32_t*)dalloc((size_t)std::max<int64_t>(m2, 1) * 4, s);
+    if (m2 > 0) GPR_CUDA(cudaMemcpyAsync(new_row_idx, row_full, (size_t)m2 * 4, cudaMemcpyDeviceToDevice, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    tmp.release();
+    // swap in the new CSC; everything derived from the old one goes
+    GPR_CUDA(cudaDeviceSynchronize());  // work queued on other streams may still read the graph
+    if (g->work) {
+      pagerank_work_free(g->work);
+      g->work = nullptr;
+    }
+    if (g->transposed) {
+      graph_free_device(g->transposed, s);
+      delete g->transposed;
+      g->transposed = nullptr;
+    }
+    int32_t* n2o = g->plan.new2old;
+    int32_t* o2n = g->plan.old2new;
+    g->plan.new2old = g->plan.old2new = nullptr;
+    plan_free(g->plan, s);
+    g->plan.new2old = n2o;
+    g->plan.old2new = o2n;
+    dfree(g->col_ptr, s);
+    dfree(g->row_idx, s);
+    dfree(g->outdeg, s);
+    g->col_ptr = new_col_ptr;
+    g->row_idx = new_row_idx;
+    g->outdeg = new_outdeg;
+    new_col_ptr = new_row_idx = new_outdeg = nullptr;
+    g->m = m2;
+    g->m_raw = m2;
+    int* derr2 = (int*)dalloc(8, s);
+    GPR_CUDA(cudaMemsetAsync(derr2, 0, 8, s));
+    try {
+      plan_build(g, s, derr2);
+    } catch (...) {
+      dfree(derr2, s);
+      throw;
+    }
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr2, 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    dfree(derr2, s);
+    if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_update: a device-side wait timed out"};
+    return GPR_OK;
+  } catch (const StatusFail& f) {
+    tmp.release();
+    dfree(new_col_ptr, s);
+    dfree(new_row_idx, s);
+    dfree(new_outdeg, s);
+    set_error("%s", f.msg.c_str());
+    return f.st;
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    tmp.release();
+    dfree(new_col_ptr, s);
+    dfree(new_row_idx, s);
+    dfree(new_outdeg, s);
+    set_error("graph_update: %s failed: %s", f.what, cudaGetErrorString(f.err));
+    return GPR_ECUDA;
   }
 }
 

@@ -214,18 +214,19 @@ __global__ void __launch_bounds__(1024, 1) hot_kernel(const int32_t* __restrict_
   }
 }
 
-// x_0 = 1/N, c_0 = x_0 * inv_outdeg.
+// x_0 = 1/N (or the warm-start vector), c_0 = x_0 * inv_outdeg.
 template <typename T>
 __global__ void init_kernel(float* __restrict__ x, T* __restrict__ c, const float* __restrict__ inv_deg, int32_t n,
-                            double* __restrict__ partials) {
+                            double* __restrict__ partials, const float* __restrict__ x_start) {
   float mass = 0.f, dang = 0.f;
   const float x0 = 1.0f / (float)n;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const float idg = inv_deg[v];
-    x[v] = x0;
-    store_rank(c, v, x0 * idg);
-    mass += x0;
-    if (idg == 0.0f) dang += x0;
+    const float xv = x_start ? x_start[v] : x0;  // a warm start, else uniform
+    x[v] = xv;
+    store_rank(c, v, xv * idg);
+    mass += xv;
+    if (idg == 0.0f) dang += xv;
   }
   block_partials3(mass, dang, 0.f, partials + 3 * (int64_t)blockIdx.x);
 }
@@ -261,6 +262,13 @@ __global__ void __launch_bounds__(256) finish_kernel(
   __threadfence();
   fold_step(partials, npartials, prm, log_row);
   if (threadIdx.x == 0) *arrive = 0;  // ready for the next step
+}
+
+// x_start[p] = x[new2old[p]]: a caller-ordered vector in relabelled order.
+__global__ void start_kernel(const float* __restrict__ x, const int32_t* __restrict__ new2old, int32_t n,
+                             float* __restrict__ x_start) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    x_start[p] = x[new2old[p]];
 }
 
 __global__ void output_kernel(const float* __restrict__ x, const int32_t* __restrict__ old2new, int32_t n,
@@ -308,12 +316,14 @@ struct PagerankWork {
   cudaEvent_t ev_join[kMaxBuckets] = {};
   Blocked* blk = nullptr;  // the blocked schedule's edge layout, made on first use
   float* ones = nullptr;   // n ones: unit weights for the centralities
+  float* x_start = nullptr;  // n: a warm start's vector in relabelled order
   bool tuned = false;      // `choice` was measured on this graph
   Choice choice;
   cudaGraphExec_t exec = nullptr;
   int32_t exec_iters = -1;
   int exec_dt = -1;
   int exec_sched = -1;
+  bool exec_warm = false;
   int64_t exec_kernels = 0;  // kernel nodes in `exec`
 };
 
@@ -328,6 +338,7 @@ void pagerank_work_free(PagerankWork* w) {
   }
   dfree(w->out_tmp, s);
   dfree(w->ones, s);
+  dfree(w->x_start, s);
   dfree(w->y_hot, s);
   dfree(w->partials, s);
   dfree(w->chunk_sum, s);
@@ -417,7 +428,7 @@ static void launch_bucket(const Bucket& b, int grid, cudaStream_t s, const gpr_g
 // hot pass, then the cold-pass bucket kernels forked onto side streams, joined
 // before the finish kernel.
 template <typename T>
-static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, int sched) {
+static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, int sched, bool warm) {
   const Plan& P = g->plan;
   cudaStream_t s = w->cap;
   float* x[2] = {w->x[0], w->x[1]};
@@ -431,7 +442,7 @@ static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, int 
     hl.begin[k] = P.bucket[k].row_begin;
     hl.end[k] = P.bucket[k].row_end;
   }
-  init_kernel<T><<<w->init_grid, 256, 0, s>>>(x[0], c[0], P.inv_deg, g->n, w->partials);
+  init_kernel<T><<<w->init_grid, 256, 0, s>>>(x[0], c[0], P.inv_deg, g->n, w->partials, warm ? w->x_start : nullptr);
   finish_kernel<T><<<1, 256, 0, s>>>(x[0], P.inv_deg, x[0], c[0], P.split_row, P.split_hbeg, P.split_hend,
                                     P.split_cbeg, P.split_cend, 0, w->chunk_sum, w->partials, w->init_grid + 1,
                                     w->prm, w->log, w->arrive);
@@ -574,7 +585,8 @@ static void ensure_layout(gpr_graph* g, PagerankWork* w, const Choice& c, cudaSt
 }
 
 // The iteration loop of `iters` steps with schedule `sched`, as a CUDA graph.
-static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype dt, int sched, cudaStream_t s) {
+static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype dt, int sched, bool warm,
+                        cudaStream_t s) {
   if (w->log_cap < iters + 1) {
     dfree(w->log, s);
     w->log = nullptr;
@@ -584,7 +596,8 @@ static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype 
     w->log_cap = cap;
     drop_exec(w);
   }
-  if (w->exec && w->exec_iters == iters && w->exec_dt == (int)dt && w->exec_sched == sched) return;
+  if (w->exec && w->exec_iters == iters && w->exec_dt == (int)dt && w->exec_sched == sched && w->exec_warm == warm)
+    return;
   drop_exec(w);
   // the capture stream must see the allocations made on `s`
   GPR_CUDA(cudaStreamSynchronize(s));
@@ -592,9 +605,9 @@ static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype 
   GPR_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
   try {
     if (dt == GPR_BF16)
-      record_iterations<__nv_bfloat16>(g, w, iters, sched);
+      record_iterations<__nv_bfloat16>(g, w, iters, sched, warm);
     else
-      record_iterations<float>(g, w, iters, sched);
+      record_iterations<float>(g, w, iters, sched, warm);
   } catch (...) {
     cudaGraph_t junk = nullptr;
     cudaStreamEndCapture(w->cap, &junk);
@@ -612,6 +625,7 @@ static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype 
   w->exec_iters = iters;
   w->exec_dt = (int)dt;
   w->exec_sched = sched;
+  w->exec_warm = warm;
   w->exec_kernels = sched == kSchedBlocked ? 2 + (int64_t)iters * 2
                                            : 2 + (int64_t)iters * (g->plan.nbuckets + 1 + (w->hot_grid > 0 ? 1 : 0));
 }
@@ -620,7 +634,7 @@ static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype 
 static double time_choice(gpr_graph* g, PagerankWork* w, const Choice& c, int32_t iters, gpr_dtype dt,
                           cudaStream_t s) {
   if (c.sched == kSchedBlocked) ensure_layout(g, w, c, s);
-  ensure_exec(g, w, iters, dt, c.sched, s);
+  ensure_exec(g, w, iters, dt, c.sched, false, s);
   const StepParams hp{0.f, 0.f, 0.85, (double)g->n};
   float best = 0.f;
   for (int rep = 0; rep < 2; ++rep) {
@@ -711,7 +725,22 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
     const Choice ch = pick(g, w, flags, dt, s);
     const int sched = ch.sched;
     if (sched == kSchedBlocked) ensure_layout(g, w, ch, s);
-    ensure_exec(g, w, iters, dt, sched, s);
+    const bool warm = (flags & GPR_WARM_START) != 0;
+    if (warm) {
+      // the caller's start vector (x_out, caller ids) into relabelled order
+      if (!w->x_start) w->x_start = (float*)dalloc((size_t)g->n * 4, s);
+      const float* src = x_out;
+      if (flags & GPR_PTR_HOST) {
+        if (!w->out_tmp) w->out_tmp = (float*)dalloc((size_t)g->n * 4, s);
+        GPR_CUDA(cudaMemcpyAsync(w->out_tmp, x_out, (size_t)g->n * 4, cudaMemcpyHostToDevice, s));
+        src = w->out_tmp;
+      }
+      const int og = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, num_sms() * 8));
+      start_kernel<<<og, 256, 0, s>>>(src, g->plan.new2old, g->n, w->x_start);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+    }
+    ensure_exec(g, w, iters, dt, sched, warm, s);
     StepParams hp{0.f, 0.f, damping, (double)g->n};
     GPR_CUDA(cudaMemcpyAsync(w->prm, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
     const double t_setup =
@@ -916,7 +945,7 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
     // the start vector: uniform (1/n; its direction is 1/sqrt(n)), its fold sets coefA = 1
     float* x0 = kind == 1 ? wt->x[0] : w->x[0];
     float* c0 = kind == 1 ? (float*)wt->c[0] : (float*)w->c[0];
-    init_kernel<float><<<w->init_grid, 256, 0, s>>>(x0, c0, w->ones, n, w->partials);
+    init_kernel<float><<<w->init_grid, 256, 0, s>>>(x0, c0, w->ones, n, w->partials, nullptr);
     finish_kernel<float><<<1, 256, 0, s>>>(x0, w->ones, x0, c0, g->plan.split_row, g->plan.split_hbeg,
                                           g->plan.split_hend, g->plan.split_cbeg, g->plan.split_cend, 0,
                                           w->chunk_sum, w->partials, w->init_grid + 1, w->prm, w->log, w->arrive);
