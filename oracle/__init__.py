@@ -61,6 +61,16 @@ def _L():
         lib.oracle_eigen_centrality.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _f64p]
         lib.oracle_wcc.restype = ctypes.c_int32
         lib.oracle_wcc.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+        lib.oracle_reverse_push.restype = ctypes.c_int64
+        lib.oracle_reverse_push.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_double,
+                                            ctypes.c_double, _f64p, _f64p]
+        lib.oracle_ppr_contrib.restype = ctypes.c_int32
+        lib.oracle_ppr_contrib.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_int32, _f64p]
+        lib.oracle_ppr_target.restype = ctypes.c_int32
+        lib.oracle_ppr_target.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double, _i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                          _f64p]
         _lib = lib
     return _lib
 
@@ -214,3 +224,35 @@ def wcc(g: CSC):
     if k < 0:
         raise ValueError("oracle_wcc: invalid arguments")
     return labels, int(k)
+
+
+def reverse_push(g: CSC, target: int, d: float = DAMPING, r_max: float = 1e-4):
+    """Reverse push from `target` (oracle_reverse_push): (p, r, pushes)."""
+    keep, ptrs = _csc_ptrs(g)
+    p = np.empty(g.n, np.float64)
+    r = np.empty(g.n, np.float64)
+    k = _L().oracle_reverse_push(g.n, *ptrs, target, d, r_max, p.ctypes.data_as(_f64p), r.ctypes.data_as(_f64p))
+    if k < 0:
+        raise ValueError("oracle_reverse_push: invalid arguments")
+    return p, r, int(k)
+
+
+def ppr_contrib(g: CSC, target: int, d: float = DAMPING, iters: int = 250):
+    """q(s) = Q_s(target) for every s: the absorbing walk's chance to stop at target."""
+    keep, ptrs = _csc_ptrs(g)
+    q = np.empty(g.n, np.float64)
+    if _L().oracle_ppr_contrib(g.n, *ptrs, target, d, iters, q.ctypes.data_as(_f64p)) < 0:
+        raise ValueError("oracle_ppr_contrib: invalid arguments")
+    return q
+
+
+def ppr_target(g: CSC, target: int, sources, d: float = DAMPING, r_max: float = 1e-4, walks: int = 1000,
+               seed: int = 1):
+    """Bidirectional estimates of pi_s(target) for each source (oracle_ppr_target)."""
+    keep, ptrs = _csc_ptrs(g)
+    src, ps = _i32(sources)
+    out = np.empty(len(src), np.float64)
+    if _L().oracle_ppr_target(g.n, *ptrs, target, d, r_max, ps, len(src), walks, seed,
+                              out.ctypes.data_as(_f64p)) < 0:
+        raise ValueError("oracle_ppr_target: invalid arguments")
+    return out

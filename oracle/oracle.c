@@ -347,3 +347,125 @@ int32_t oracle_wcc(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, in
   free(parent);
   return count;
 }
+
+/* ---- single-target personalised PageRank (bidirectional) ------------------ */
+
+int64_t oracle_reverse_push(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
+                            int32_t target, double d, double r_max, double* p, double* r) {
+  if (n <= 0 || target < 0 || target >= n || !(d > 0.0 && d < 1.0) || !(r_max > 0.0) || !col_ptr || !row_idx ||
+      !outdeg || !p || !r)
+    return -1;
+  const double a = 1.0 - d;
+  int32_t* queue = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  char* queued = (char*)calloc((size_t)n, 1);
+  if (!queue || !queued) {
+    free(queue);
+    free(queued);
+    return -1;
+  }
+  for (int32_t v = 0; v < n; ++v) p[v] = r[v] = 0.0;
+  r[target] = 1.0;
+  int64_t head = 0, size = 0, pushes = 0; /* ring buffer of n entries: each node at most once */
+  queue[0] = target;
+  queued[target] = 1;
+  size = 1;
+  while (size > 0) {
+    const int32_t v = queue[head];
+    head = (head + 1) % n;
+    --size;
+    queued[v] = 0;
+    if (!(r[v] > r_max)) continue;
+    const double amt = r[v];
+    r[v] = 0.0;
+    p[v] += a * amt;
+    ++pushes;
+    for (int32_t e = col_ptr[v]; e < col_ptr[v + 1]; ++e) {
+      const int32_t u = row_idx[e];
+      r[u] += (1.0 - a) * amt / outdeg[u];
+      if (r[u] > r_max && !queued[u]) {
+        queue[(head + size) % n] = u;
+        ++size;
+        queued[u] = 1;
+      }
+    }
+  }
+  free(queue);
+  free(queued);
+  return pushes;
+}
+
+int32_t oracle_ppr_contrib(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
+                           int32_t target, double d, int32_t iters, double* q) {
+  if (n <= 0 || target < 0 || target >= n || !(d > 0.0 && d < 1.0) || iters < 0 || !q) return -1;
+  const double a = 1.0 - d;
+  double* acc = (double*)malloc((size_t)n * sizeof(double));
+  if (!acc) return -1;
+  for (int32_t v = 0; v < n; ++v) q[v] = 0.0;
+  for (int32_t k = 0; k < iters; ++k) {
+    for (int32_t u = 0; u < n; ++u) acc[u] = 0.0;
+    for (int32_t v = 0; v < n; ++v) /* edge u -> v: u's mean includes q(v) */
+      for (int32_t e = col_ptr[v]; e < col_ptr[v + 1]; ++e) acc[row_idx[e]] += q[v];
+    for (int32_t u = 0; u < n; ++u) q[u] = (u == target ? a : 0.0) + (outdeg[u] > 0 ? d * acc[u] / outdeg[u] : 0.0);
+  }
+  free(acc);
+  return 0;
+}
+
+/* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", 2014): state += golden gamma, then the mix. */
+static uint64_t sm64_next(uint64_t* state) {
+  uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static double sm64_unit(uint64_t* state) { return (double)(sm64_next(state) >> 11) * 0x1p-53; }
+
+int32_t oracle_ppr_target(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
+                          int32_t target, double d, double r_max, const int32_t* sources, int32_t k,
+                          int32_t walks, uint64_t seed, double* out) {
+  if (k < 0 || walks < 1 || (k > 0 && (!sources || !out))) return -1;
+  double* p = (double*)malloc((size_t)n * sizeof(double));
+  double* r = (double*)malloc((size_t)n * sizeof(double));
+  int64_t* optr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  const int64_t m = n > 0 ? col_ptr[n] : 0;
+  int32_t* olist = (int32_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+  int64_t* fill = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  if (!p || !r || !optr || !olist || !fill || oracle_reverse_push(n, col_ptr, row_idx, outdeg, target, d, r_max, p, r) < 0) {
+    free(p); free(r); free(optr); free(olist); free(fill);
+    return -1;
+  }
+  /* out-adjacency, each list ascending: destinations v visited in order */
+  for (int32_t u = 0; u < n; ++u) optr[u + 1] = optr[u] + outdeg[u];
+  for (int32_t u = 0; u < n; ++u) fill[u] = optr[u];
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t e = col_ptr[v]; e < col_ptr[v + 1]; ++e) olist[fill[row_idx[e]]++] = v;
+  const double a = 1.0 - d;
+  for (int32_t i = 0; i < k; ++i) {
+    const int32_t s = sources[i];
+    if (s < 0 || s >= n) {
+      free(p); free(r); free(optr); free(olist); free(fill);
+      return -1;
+    }
+    double sum_r = 0.0;
+    int64_t at_dangling = 0;
+    for (int32_t w = 0; w < walks; ++w) {
+      uint64_t st = seed ^ (((uint64_t)(uint32_t)i << 32) | (uint32_t)w) * 0xD6E8FEB86659FD93ull;
+      int32_t u = s;
+      for (int32_t step = 0; step < (1 << 20); ++step) {
+        if (sm64_unit(&st) < a) break;
+        if (outdeg[u] == 0) {
+          u = s; /* dangling: the walk's mass goes back to the seed */
+          continue;
+        }
+        const int64_t j = (int64_t)(sm64_unit(&st) * outdeg[u]);
+        u = olist[optr[u] + (j < outdeg[u] ? j : outdeg[u] - 1)];
+      }
+      sum_r += r[u];
+      at_dangling += outdeg[u] == 0;
+    }
+    out[i] = p[s] * (1.0 + (d / a) * ((double)at_dangling / walks)) + sum_r / walks;
+  }
+  free(p); free(r); free(optr); free(olist); free(fill);
+  return 0;
+}

@@ -98,4 +98,46 @@ int32_t oracle_eigen_centrality(int32_t n, const int32_t* col_ptr, const int32_t
  * number of components, or -1 on bad arguments / allocation failure. */
 int32_t oracle_wcc(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, int32_t* labels);
 
+/* Single-target personalised PageRank, bidirectional (section 4.3 "Fast
+ * Random Walk Algorithms": work backwards from the target to a set of
+ * intermediate nodes, then walk forwards from the sources).  Reading, for
+ * the personalised PageRank pi_s of oracle_ppr (restart a = 1 - d, dangling
+ * mass back to the seed s):
+ *   Q_s(t): the chance that an excursion from s (stop with probability a at
+ *   each node; absorbed at a dangling node when it does not stop) stops at t;
+ *   Q_s = a e_s + d Q_s P, P[u][v] = 1/outdeg(u) for u -> v, 0 rows at
+ *   dangling nodes.  pi_s solves pi_s = c_s e_s + d pi_s P with
+ *   c_s = a + d pi_s(dangling set), so pi_s = (c_s / a) Q_s.
+ *   Reverse push from t (threshold r_max): p = 0, r = e_t; while some v has
+ *   r(v) > r_max: p(v) += a r(v), r(u) += d r(v) / outdeg(u) for each
+ *   in-neighbour u of v, r(v) = 0.  Each push keeps
+ *     Q_s(t) = p(s) + sum_v Q_s(v) r(v)   and   pi_s(t) = (c_s / a) p(s) + sum_v pi_s(v) r(v).
+ *   Estimate: W walks of the PageRank process from s (stop with probability
+ *   a; from a dangling node go back to s; else to a uniform out-neighbour,
+ *   out-neighbours in ascending id order), ending at V_1..V_W:
+ *     pi^_s(t) = p(s) (1 + (d / a) #{i : V_i dangling} / W) + sum_i r(V_i) / W,
+ *   an unbiased estimate (E[1{V dangling}] = pi_s(dangling set)).
+ * oracle_reverse_push: p and r (n doubles each); returns the number of
+ * pushes, or -1 on bad arguments.  Pushes in FIFO order. */
+int64_t oracle_reverse_push(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
+                            int32_t target, double d, double r_max, double* p, double* r);
+
+/* oracle_ppr_contrib: q(s) = Q_s(target) for every s, by iterating
+ * q <- a e_target + (1 - a) P q  (P q)(s) = mean of q over the out-neighbours
+ * of s, 0 at a dangling s; `iters` steps from q = 0 (error <= (1 - a)^iters).
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int32_t oracle_ppr_contrib(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
+                           int32_t target, double d, int32_t iters, double* q);
+
+/* oracle_ppr_target: estimates for k sources (ids) into out (k doubles).
+ * Walk w of source i draws from the SplitMix64 stream whose state starts at
+ * seed ^ ((i << 32 | w) * 0xD6E8FEB86659FD93); each step takes one draw
+ * u = (x >> 11) 2^-53 and stops if u < a; otherwise, at a node of out-degree
+ * k > 0, a second draw picks out-neighbour min(floor(u k), k - 1).  A walk is
+ * cut (ending where it is) after 2^20 steps.  Returns 0, or -1 on bad
+ * arguments / allocation failure. */
+int32_t oracle_ppr_target(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
+                          int32_t target, double d, double r_max, const int32_t* sources, int32_t k,
+                          int32_t walks, uint64_t seed, double* out);
+
 #endif /* GPR_ORACLE_H */
