@@ -458,8 +458,10 @@ int32_t oracle_ppr_target(int32_t n, const int32_t* col_ptr, const int32_t* row_
           u = s; /* dangling: the walk's mass goes back to the seed */
           continue;
         }
-        const int64_t j = (int64_t)(sm64_unit(&st) * outdeg[u]);
-        u = olist[optr[u] + (j < outdeg[u] ? j : outdeg[u] - 1)];
+        /* uniform index: floor(X k / 2^53) for the draw's top 53 bits X (exact) */
+        const uint64_t x53 = sm64_next(&st) >> 11;
+        const int64_t j = (int64_t)(((unsigned __int128)x53 * (uint64_t)outdeg[u]) >> 53);
+        u = olist[optr[u] + j];
       }
       sum_r += r[u];
       at_dangling += outdeg[u] == 0;

@@ -133,8 +133,9 @@ int32_t oracle_ppr_contrib(int32_t n, const int32_t* col_ptr, const int32_t* row
  * Walk w of source i draws from the SplitMix64 stream whose state starts at
  * seed ^ ((i << 32 | w) * 0xD6E8FEB86659FD93); each step takes one draw
  * u = (x >> 11) 2^-53 and stops if u < a; otherwise, at a node of out-degree
- * k > 0, a second draw picks out-neighbour min(floor(u k), k - 1).  A walk is
- * cut (ending where it is) after 2^20 steps.  Returns 0, or -1 on bad
+ * k > 0, a second draw x' picks out-neighbour floor((x' >> 11) k / 2^53)
+ * (exact integer arithmetic).  A walk is cut (ending where it is) after 2^20
+ * steps.  Returns 0, or -1 on bad
  * arguments / allocation failure. */
 int32_t oracle_ppr_target(int32_t n, const int32_t* col_ptr, const int32_t* row_idx, const int32_t* outdeg,
                           int32_t target, double d, double r_max, const int32_t* sources, int32_t k,
