@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpr", "reference"], default="gpr")
-    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits", "wcc", "dynamic"],
+    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits", "wcc", "dynamic",
+                                           "target"],
                     default="rmat25")
     ap.add_argument("--graphs", type=int, default=4096, help="batched: number of graphs")
     ap.add_argument("--dtypes", default="fp32,bf16,fp16", help="batched: contribution storage types")
@@ -57,6 +58,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--spmv", choices=["auto", "pull", "blocked"], default="auto",
                     help="schedule of the PageRank step (auto: the library's choice)")
+    ap.add_argument("--target-sources", type=int, default=1024, help="target: sources per query")
+    ap.add_argument("--target-walks", type=int, default=2048, help="target: walks per source")
+    ap.add_argument("--target-rmax", type=float, default=1e-6, help="target: reverse-push threshold")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-scale", type=int, default=19)
     return ap.parse_args()
@@ -907,6 +911,103 @@ def run_dynamic(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_target(args, world, rank, local):
+    """Single-target personalised PageRank (section 4.3, bidirectional): on the
+    R-MAT scale-25 graph (edge factor 32), each step answers one query: a
+    random target, `--target-sources` random sources, reverse push to
+    `--target-rmax`, then `--target-walks` walks per source.  value = (source,
+    target) estimates per second.  The push alone is timed beside it."""
+    import numpy as np
+    import torch
+
+    import gen
+    import oracle
+    import paper_1606_07550_gb300 as gpr
+
+    torch.cuda.set_device(local)
+    k, W, r_max = args.target_sources, args.target_walks, args.target_rmax
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s = 1 << args.cpu_sample_scale
+        s_h, d_h = gen.rmat_coo(n_s, 32 * n_s, seed=3)
+        gs = oracle.build_csc(n_s, s_h, d_h)
+        rng = np.random.default_rng(5)
+        ks = 8
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < 10.0 and done < 64:
+            t = int(rng.integers(0, n_s))
+            oracle.ppr_target(gs, t, rng.integers(0, n_s, ks).astype(np.int32), 0.85, r_max, W, seed=done)
+            done += ks
+        dt = time.perf_counter() - t0
+        cpu = (done / dt, dt, f"R-MAT scale {args.cpu_sample_scale}, edge factor 32; {done // ks} targets x {ks} "
+                              f"sources, r_max {r_max:g}, {W} walks; single-threaded oracle")
+    spec = workload("rmat25")
+    src, dst = make_coo_device(torch, spec)
+    g = gpr.graph_build(src, dst, spec.n)
+    del src, dst
+    torch.cuda.empty_cache()
+    n = spec.n
+    stream = torch.cuda.current_stream()
+    gen_ = torch.Generator(device="cpu")
+    gen_.manual_seed(17 + rank)
+    queries = [(int(torch.randint(0, n, (1,), generator=gen_)),
+                torch.randint(0, n, (k,), generator=gen_, dtype=torch.int32).cuda())
+               for _ in range(args.warmup + args.steps)]
+    est = torch.empty(k, dtype=torch.float64, device="cuda")
+    p = torch.empty(n, dtype=torch.float64, device="cuda")
+    for i in range(args.warmup):
+        t, srcs = queries[i]
+        gpr.ppr_target(g, t, srcs, est, r_max, W, seed=i, stream=stream)
+    torch.cuda.synchronize()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    launches0 = gpr.lib().gpr_kernel_launches()
+    times, pushes = [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        for i in range(args.warmup, args.warmup + args.steps):
+            t, srcs = queries[i]
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gpr.ppr_target(g, t, srcs, est, r_max, W, seed=i, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+    barrier(world)
+    launches = gpr.lib().gpr_kernel_launches() - launches0
+    # the backward phase alone, same targets (outside the timed region)
+    t_push = []
+    for i in range(args.warmup, args.warmup + args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pushes.append(gpr.ppr_reverse_push(g, queries[i][0], r_max, p, None, stream=stream))
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_push.append(a.elapsed_time(b))
+    tq = max_over_ranks(world, sum(times) / len(times))
+    value = sum_over_ranks(world, float(k)) / (tq * 1e-3)
+    if rank != 0:
+        return
+    line = {
+        "metric": "single-target PPR estimates/s", "value": value, "unit": "estimates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tq, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ppr-target-rmat-s25-ef32", "n": n, "m": g.info().m, "sources": k, "walks": W,
+                   "r_max": r_max, "damping": 0.85,
+                   "step": "one ppr_target call: reverse push from a random target + walks from k random sources"},
+        "push_ms": sum(t_push) / len(t_push), "pushes_mean": sum(pushes) / len(pushes),
+        "query_ms_each": times, "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": "estimates/s", "cores": 1, "kind": "oracle",
+                                "sample": cpu[2], "seconds": cpu[1]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -922,6 +1023,8 @@ def main():
         run_wcc(args, world, rank, local)
     elif args.workload == "dynamic":
         run_dynamic(args, world, rank, local)
+    elif args.workload == "target":
+        run_target(args, world, rank, local)
     else:
         run_gpr(args, world, rank, local)
     if world > 1:

@@ -204,6 +204,51 @@ gpr_status eigen_centrality(const gpr_graph* g, int32_t iters, float* x_out, int
  * expected: a bound that turns a fault into an error). */
 gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components, int flags, void* stream);
 
+/* ---- single-target personalised PageRank (bidirectional) --------------------
+ * Section 4.3, "Fast Random Walk Algorithms": the personalised PageRank from
+ * sources to one target t, found by working backwards from t to the nodes
+ * near it and then walking forwards from the sources.  pi_s is the
+ * personalised PageRank of ppr_batch (restart a = 1 - d to s, dangling mass
+ * back to s).
+ *
+ * ppr_reverse_push: the backward phase.  From p = 0, r = e_t, pushes every
+ * node v with r(v) > r_max: p(v) += a r(v); r(u) += d r(v) / outdeg(u) for
+ * each in-neighbour u of v; r(v) = 0; until every r(v) <= r_max.  Then for
+ * every s, Q_s(t) = p(s) + sum_v Q_s(v) r(v), where Q_s(v) is the chance
+ * that a walk from s, stopping with probability a at each node and absorbed
+ * at a dangling node, stops at v; so 0 <= Q_s(t) - p(s) <= r_max.  Nodes are
+ * pushed in rounds (all nodes above r_max at once), so p and r depend on the
+ * schedule in their last digits and in which nodes ended below r_max; the
+ * invariant and the bound do not.
+ *   target  : node id in [0, n).   damping : d in (0, 1).   r_max : > 0.
+ *   p_out, r_out : n doubles each by node id (either may be NULL); device
+ *             memory, or host memory with GPR_PTR_HOST.
+ *   pushes  : host, nullable: the number of pushes taken.
+ * Synchronous.  GPR_EINVAL for a bad argument, GPR_ETIMEOUT if the push
+ * needs more than 65536 rounds.
+ *
+ * ppr_target: estimates pi_s(t) for k sources.  After the backward phase,
+ * `walks` PageRank walks from each source s (stop with probability a; from a
+ * dangling node go back to s; else to a uniform out-neighbour) end at
+ * V_1..V_W, and
+ *   est[i] = p(s) (1 + (d/a) #{V_j dangling} / W) + sum_j r(V_j) / W,
+ * an unbiased estimate of pi_s(t) whose terms lie in [0, p(s) d/a + r_max].
+ * The walks are reproducible: walk w of sources[i] draws from the SplitMix64
+ * stream with state seed ^ ((i << 32 | w) * 0xD6E8FEB86659FD93); a step stops
+ * when the draw's top 53 bits X satisfy X 2^-53 < a, else moves to
+ * out-neighbour floor(X' k / 2^53) (next draw X', out-degree k, neighbours by
+ * ascending id).  A walk is cut after 2^20 steps.
+ *   sources : k node ids; est_out : k doubles (device memory, or host memory
+ *             with GPR_PTR_HOST for both).  k >= 0, walks >= 1, k *
+ *             ceil(walks / 256) < 2^31.
+ * The first call on a graph builds the out-adjacency in node-id order and
+ * keeps it with the graph.  Synchronous.  GPR_EINVAL for a bad argument
+ * (including a source id out of range), GPR_ETIMEOUT as above. */
+gpr_status ppr_reverse_push(const gpr_graph* g, int32_t target, double damping, double r_max, double* p_out,
+                            double* r_out, int64_t* pushes, int flags, void* stream);
+gpr_status ppr_target(const gpr_graph* g, int32_t target, double damping, double r_max, const int32_t* sources,
+                      int32_t k, int32_t walks, uint64_t seed, double* est_out, int flags, void* stream);
+
 /* ---- batched personalised PageRank ---------------------------------------
  * Personalised PageRank (section 4 Table "snap_methods"; section 4,
  * "Fast Random Walk Algorithms": scores from the point of view of a given

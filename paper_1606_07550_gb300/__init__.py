@@ -139,6 +139,10 @@ def lib():
         L.graph_save.argtypes = [_VP, ctypes.c_char_p]
         L.graph_load.argtypes = [ctypes.c_char_p, _VP, ctypes.POINTER(_VP)]
         L.wcc.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, _VP]
+        L.ppr_reverse_push.argtypes = [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _VP, _VP,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _VP]
+        L.ppr_target.argtypes = [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _VP, ctypes.c_int32,
+                                 ctypes.c_int32, ctypes.c_uint64, _VP, ctypes.c_int, _VP]
         L.pagerank_tune.argtypes = [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult), _VP]
         L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                 ctypes.c_int, _VP]
@@ -157,6 +161,7 @@ def lib():
         L.pagerank_csc_noalloc.restype = ctypes.c_int
         for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "pagerank_tune", "hits",
                      "eigen_centrality", "wcc", "graph_save", "graph_load", "graph_update", "ppr_batch",
+                     "ppr_reverse_push", "ppr_target",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
                      "serve_destroy", "serve_completed"):
             getattr(L, name).restype = ctypes.c_int
@@ -323,6 +328,51 @@ def wcc(g: Graph, out, stream=None) -> int:
     k = ctypes.c_int32(0)
     _check(lib().wcc(g.handle, po, ctypes.byref(k), PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
     return int(k.value)
+
+
+def _dtype_name(a):
+    return str(a.dtype).replace("torch.", "")
+
+
+def ppr_reverse_push(g: Graph, target: int, r_max: float, p_out=None, r_out=None, damping: float = 0.85,
+                     stream=None) -> int:
+    """Reverse push from `target` (section 4.3): p and r (float64, by node id)
+    into CUDA tensors or host arrays, either may be None.  Returns the number
+    of pushes.  Q_s(target) = p(s) + sum_v Q_s(v) r(v) afterwards."""
+    host = None
+    ptrs = []
+    for a in (p_out, r_out):
+        if a is None:
+            ptrs.append(None)
+            continue
+        if _dtype_name(a) != "float64":
+            raise ValueError("p_out and r_out must be float64")
+        pa, h = _ptr_and_flag(a)
+        if host is not None and h != host:
+            raise ValueError("p_out and r_out must both be on the device or both on the host")
+        host = h
+        ptrs.append(pa)
+    k = ctypes.c_int64(0)
+    _check(lib().ppr_reverse_push(g.handle, int(target), damping, r_max, ptrs[0], ptrs[1], ctypes.byref(k),
+                                  PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
+    return int(k.value)
+
+
+def ppr_target(g: Graph, target: int, sources, out, r_max: float, walks: int, seed: int = 1,
+               damping: float = 0.85, stream=None):
+    """Bidirectional estimates of pi_s(target) (section 4.3) for each source:
+    `sources` (int32) and `out` (float64, same length) both CUDA tensors or
+    both host arrays."""
+    if _dtype_name(sources) != "int32" or _dtype_name(out) != "float64":
+        raise ValueError("sources must be int32 and out float64")
+    if len(sources) != len(out):
+        raise ValueError("sources and out differ in length")
+    ps, h1 = _ptr_and_flag(sources)
+    po, h2 = _ptr_and_flag(out)
+    if h1 != h2:
+        raise ValueError("sources and out must both be on the device or both on the host")
+    _check(lib().ppr_target(g.handle, int(target), damping, r_max, ps, len(sources), int(walks),
+                            int(seed) & (2 ** 64 - 1), po, PTR_HOST if h1 else PTR_DEVICE, _stream_ptr(stream)))
 
 
 def pagerank_tune(g: Graph, dtype: int = FP32, trial_steps: int = 5, stream=None) -> TuneResult:

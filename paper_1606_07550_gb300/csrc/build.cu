@@ -734,6 +734,61 @@ gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s) {
   }
 }
 
+// Keys (caller src << b | caller dst) of every edge: one warp per row.
+__global__ void caller_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                                   const int32_t* __restrict__ new2old, int32_t n, int b,
+                                   uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < n; p += nwarps) {
+    const uint64_t dst = (uint32_t)new2old[p];
+    const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+    for (int32_t e = e0 + lane; e < e1; e += 32) keys[e] = ((uint64_t)(uint32_t)new2old[row_idx[e]] << b) | dst;
+  }
+}
+
+// The out-adjacency in the caller's ids: out_ptr[u] .. out_ptr[u + 1] indexes
+// out_adj, the destinations of u in ascending order.
+void build_caller_out_adjacency(const gpr_graph* g, cudaStream_t s, int32_t** out_ptr, int32_t** out_adj) {
+  Temps tmp{s, {}};
+  const int32_t n = g->n;
+  const int b = g->id_bits;
+  int32_t* ptr = nullptr;
+  int32_t* adj = nullptr;
+  try {
+    int* derr = (int*)tmp.get(sizeof(int) * 2);
+    GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
+    ptr = (int32_t*)dalloc(((size_t)n + 1) * 4, s);
+    adj = (int32_t*)dalloc((size_t)std::max<int64_t>(g->m, 1) * 4, s);
+    int32_t* indeg = (int32_t*)tmp.get((size_t)n * 4);
+    int64_t m = 0;
+    if (g->m > 0) {
+      uint64_t* keys = (uint64_t*)tmp.get((size_t)g->m * 8);
+      uint64_t* alt = (uint64_t*)tmp.get((size_t)g->m * 8);
+      caller_keys_kernel<<<grid_for(n), kThreads, 0, s>>>(g->col_ptr, g->row_idx, g->plan.new2old, n, b, keys);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      m = keys_to_csc(keys, alt, g->m, b, n, nullptr, ptr, adj, indeg, derr, tmp, s);
+    } else {
+      GPR_CUDA(cudaMemsetAsync(ptr, 0, ((size_t)n + 1) * 4, s));
+    }
+    int herr = 0;
+    GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+    tmp.release();
+    if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "out-adjacency: a device-side wait timed out"};
+    if (m != g->m) throw StatusFail{GPR_ECUDA, "out-adjacency: edge count differs from the graph's"};
+    *out_ptr = ptr;
+    *out_adj = adj;
+  } catch (...) {
+    tmp.release();
+    dfree(ptr, s);
+    dfree(adj, s);
+    throw;
+  }
+}
+
 // ---- in-place edge updates ---------------------------------------------------
 // E' = (E \ D) u I for a batch of deletions D and insertions I (caller ids;
 // self-loops in I are dropped, deleting a missing edge does nothing).  The
@@ -986,6 +1041,9 @@ gpr_status update_graph(gpr_graph* g, const int32_t* ins_src, const int32_t* ins
       delete g->transposed;
       g->transposed = nullptr;
     }
+    dfree(g->walk_ptr, s);
+    dfree(g->walk_adj, s);
+    g->walk_ptr = g->walk_adj = nullptr;
     int32_t* n2o = g->plan.new2old;
     int32_t* o2n = g->plan.old2new;
     g->plan.new2old = g->plan.old2new = nullptr;

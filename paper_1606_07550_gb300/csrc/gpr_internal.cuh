@@ -129,17 +129,23 @@ struct gpr_graph {
   int32_t* outdeg = nullptr;   // n
   gpr::Plan plan;
   int64_t device_bytes = 0;
-  std::mutex mu;                    // guards `work` and `transposed`
+  std::mutex mu;                    // guards `work`, `transposed` and the walk arrays
   gpr::PagerankWork* work = nullptr;  // lazily made by pagerank()
   // the out-adjacency as a CSC over the same relabelled ids (row u lists the
   // destinations of u, ascending), made by the first call that needs it
   gpr_graph* transposed = nullptr;
+  // the out-adjacency in the caller's ids (walk_ptr: n + 1, walk_adj: m; the
+  // destinations of u ascending), made by the first random-walk call
+  int32_t* walk_ptr = nullptr;
+  int32_t* walk_adj = nullptr;
 };
 
 namespace gpr {
 void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
 // The transposed graph of g (throws StatusFail / CudaFail).
 gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s);
+// The caller-id out-adjacency of g into two new device arrays (throws).
+void build_caller_out_adjacency(const gpr_graph* g, cudaStream_t s, int32_t** out_ptr, int32_t** out_adj);
 void graph_free_device(gpr_graph* g, cudaStream_t s);
 gpr_status export_graph(const gpr_graph* g, int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg);
 void plan_free(Plan& p, cudaStream_t s);
