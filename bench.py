@@ -59,8 +59,9 @@ def parse_args():
     ap.add_argument("--spmv", choices=["auto", "pull", "blocked"], default="auto",
                     help="schedule of the PageRank step (auto: the library's choice)")
     ap.add_argument("--target-sources", type=int, default=1024, help="target: sources per query")
-    ap.add_argument("--target-walks", type=int, default=2048, help="target: walks per source")
-    ap.add_argument("--target-rmax", type=float, default=1e-6, help="target: reverse-push threshold")
+    ap.add_argument("--target-walks", type=int, default=8192, help="target: walks per source")
+    ap.add_argument("--target-rmax", type=float, default=1e-5, help="target: reverse-push threshold")
+    ap.add_argument("--target-scale", type=int, default=25, help="target: R-MAT scale (edge factor 32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-scale", type=int, default=19)
     return ap.parse_args()
@@ -942,7 +943,12 @@ def run_target(args, world, rank, local):
         dt = time.perf_counter() - t0
         cpu = (done / dt, dt, f"R-MAT scale {args.cpu_sample_scale}, edge factor 32; {done // ks} targets x {ks} "
                               f"sources, r_max {r_max:g}, {W} walks; single-threaded oracle")
-    spec = workload("rmat25")
+    if args.target_scale == 25:
+        spec = workload("rmat25")
+    else:
+        from gen.workloads import GraphSpec
+        spec = GraphSpec(f"rmat-s{args.target_scale}-ef32", "rmat", 1 << args.target_scale,
+                         1 << (args.target_scale + 5), seed=3)
     src, dst = make_coo_device(torch, spec)
     g = gpr.graph_build(src, dst, spec.n)
     del src, dst
@@ -955,7 +961,6 @@ def run_target(args, world, rank, local):
                 torch.randint(0, n, (k,), generator=gen_, dtype=torch.int32).cuda())
                for _ in range(args.warmup + args.steps)]
     est = torch.empty(k, dtype=torch.float64, device="cuda")
-    p = torch.empty(n, dtype=torch.float64, device="cuda")
     for i in range(args.warmup):
         t, srcs = queries[i]
         gpr.ppr_target(g, t, srcs, est, r_max, W, seed=i, stream=stream)
@@ -963,7 +968,7 @@ def run_target(args, world, rank, local):
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
         "CUDA_VISIBLE_DEVICES") else str(local)
     launches0 = gpr.lib().gpr_kernel_launches()
-    times, pushes = [], []
+    times, stats = [], []
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(gpu_index) as clk:
@@ -972,34 +977,58 @@ def run_target(args, world, rank, local):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            gpr.ppr_target(g, t, srcs, est, r_max, W, seed=i, stream=stream)
+            stats.append(gpr.ppr_target(g, t, srcs, est, r_max, W, seed=i, stream=stream))
             b.record(stream)
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
     barrier(world)
     launches = gpr.lib().gpr_kernel_launches() - launches0
-    # the backward phase alone, same targets (outside the timed region)
-    t_push = []
-    for i in range(args.warmup, args.warmup + args.steps):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pushes.append(gpr.ppr_reverse_push(g, queries[i][0], r_max, p, None, stream=stream))
-        b.record(stream)
-        torch.cuda.synchronize()
-        t_push.append(a.elapsed_time(b))
     tq = max_over_ranks(world, sum(times) / len(times))
     value = sum_over_ranks(world, float(k)) / (tq * 1e-3)
+    # end to end: sources from pinned host memory, estimates back to the host
+    h_src = [queries[i][1].cpu().pin_memory() for i in range(args.warmup, args.warmup + args.steps)]
+    h_est = torch.empty(k, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for q, i in enumerate(range(args.warmup, args.warmup + args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gpr.ppr_target(g, queries[i][0], h_src[q].numpy(), h_est.numpy(), r_max, W, seed=i, stream=stream)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = max_over_ranks(world, 1e3 * sum(e2e_t) / len(e2e_t))
     if rank != 0:
         return
+    mean = lambda f: sum(f(x) for x in stats) / len(stats)
+    walk_ms, push_ms = mean(lambda x: x.walk_ms), mean(lambda x: x.push_ms)
+    # algorithmic bytes: a walk step reads the out-offsets of its node (8 B)
+    # and one out-neighbour (4 B); each walk also reads its start offsets and
+    # writes its endpoint (12 B).  A push scans its in-edges (source id 4 B,
+    # its out-degree 4 B, the residual's atomic read and write 16 B per edge)
+    # and takes its own residual, p, amount and offsets (72 B).
+    walk_bytes = mean(lambda x: 12.0 * x.walk_steps + 12.0 * k * W)
+    push_bytes = mean(lambda x: 24.0 * x.edges + 72.0 * x.pushes)
+    peak = measured_peak()
+    phases = {
+        "walk": {"ms": walk_ms, "bytes": walk_bytes, "gbs": walk_bytes / (walk_ms * 1e6)},
+        "push": {"ms": push_ms, "bytes": push_bytes, "gbs": push_bytes / (push_ms * 1e6),
+                 "pushes": mean(lambda x: x.pushes), "edges": mean(lambda x: x.edges),
+                 "rounds": mean(lambda x: x.rounds)},
+    }
+    top = "walk" if walk_ms >= push_ms else "push"
     line = {
         "metric": "single-target PPR estimates/s", "value": value, "unit": "estimates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tq, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "ppr-target-rmat-s25-ef32", "n": n, "m": g.info().m, "sources": k, "walks": W,
+        "config": {"workload": f"ppr-target-rmat-s{spec.scale}-ef32", "n": n, "m": g.info().m, "sources": k, "walks": W,
                    "r_max": r_max, "damping": 0.85,
-                   "step": "one ppr_target call: reverse push from a random target + walks from k random sources"},
-        "push_ms": sum(t_push) / len(t_push), "pushes_mean": sum(pushes) / len(pushes),
+                   "step": "one ppr_target call: reverse push from a random target beside walks from k random "
+                           "sources, then the estimates",
+                   "l2": "graph 4.3 GB + walk adjacency 4.3 GB >> L2; each query a new target and sources"},
+        "roofline": {"bound": "hbm", "kernel": "walk_kernel" if top == "walk" else "push_take+push_scatter",
+                     "achieved": phases[top]["gbs"], "peak": peak[0], "unit": "GB/s",
+                     "frac": phases[top]["gbs"] / peak[0], "traffic": None, "peak_source": peak[1]},
+        "phases": phases, "walk_steps_mean": mean(lambda x: x.walk_steps),
+        "e2e": {"value": k / (e2e_ms * 1e-3), "unit": "estimates/s", "h2d_bytes_per_step": 4 * k,
+                "d2h_bytes_per_step": 8 * k},
         "query_ms_each": times, "clocks": clk.summary(), "gpu_launches": launches,
     }
     if cpu:

@@ -223,7 +223,7 @@ gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components,
  *   target  : node id in [0, n).   damping : d in (0, 1).   r_max : > 0.
  *   p_out, r_out : n doubles each by node id (either may be NULL); device
  *             memory, or host memory with GPR_PTR_HOST.
- *   pushes  : host, nullable: the number of pushes taken.
+ *   stats   : host, nullable: pushes, edges scanned, rounds, device time.
  * Synchronous.  GPR_EINVAL for a bad argument, GPR_ETIMEOUT if the push
  * needs more than 65536 rounds.
  *
@@ -239,15 +239,29 @@ gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components,
  * out-neighbour floor(X' k / 2^53) (next draw X', out-degree k, neighbours by
  * ascending id).  A walk is cut after 2^20 steps.
  *   sources : k node ids; est_out : k doubles (device memory, or host memory
- *             with GPR_PTR_HOST for both).  k >= 0, walks >= 1, k *
- *             ceil(walks / 256) < 2^31.
+ *             with GPR_PTR_HOST for both).  k >= 0, walks >= 1,
+ *             k * walks < 2^31.   stats : host, nullable.
+ * The walks run on `stream` beside the push, which takes a high-priority
+ * stream of the library's and joins `stream` before the estimates; the sum
+ * over each source's walks is taken in a fixed order, so a call's result
+ * depends only on its arguments and the push's rounding. 
  * The first call on a graph builds the out-adjacency in node-id order and
  * keeps it with the graph.  Synchronous.  GPR_EINVAL for a bad argument
  * (including a source id out of range), GPR_ETIMEOUT as above. */
+typedef struct {
+  int64_t pushes;     /* pushes taken by the backward phase */
+  int64_t edges;      /* in-edges those pushes scanned */
+  int32_t rounds;     /* push rounds with a non-empty frontier */
+  int64_t walk_steps; /* steps of all walks (ppr_target; 0 for ppr_reverse_push) */
+  double push_ms;     /* device time of the backward phase (CUDA events) */
+  double walk_ms;     /* device time of the walks (ppr_target: they run beside the push) */
+  double total_ms;    /* device time of the whole call after its argument checks */
+} gpr_target_stats;
 gpr_status ppr_reverse_push(const gpr_graph* g, int32_t target, double damping, double r_max, double* p_out,
-                            double* r_out, int64_t* pushes, int flags, void* stream);
+                            double* r_out, gpr_target_stats* stats, int flags, void* stream);
 gpr_status ppr_target(const gpr_graph* g, int32_t target, double damping, double r_max, const int32_t* sources,
-                      int32_t k, int32_t walks, uint64_t seed, double* est_out, int flags, void* stream);
+                      int32_t k, int32_t walks, uint64_t seed, double* est_out, gpr_target_stats* stats, int flags,
+                      void* stream);
 
 /* ---- batched personalised PageRank ---------------------------------------
  * Personalised PageRank (section 4 Table "snap_methods"; section 4,

@@ -102,6 +102,13 @@ class ServerStats(ctypes.Structure):
                                                "device_bytes_in_use")]
 
 
+class TargetStats(ctypes.Structure):
+    """gpr_target_stats: counters and device times of ppr_reverse_push / ppr_target."""
+    _fields_ = [("pushes", ctypes.c_int64), ("edges", ctypes.c_int64), ("rounds", ctypes.c_int32),
+                ("walk_steps", ctypes.c_int64), ("push_ms", ctypes.c_double), ("walk_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("sb_bits", ctypes.c_int32), ("w_bits", ctypes.c_int32),
                 ("unit_edges", ctypes.c_int64), ("ms_per_step", ctypes.c_double),
@@ -140,9 +147,9 @@ def lib():
         L.graph_load.argtypes = [ctypes.c_char_p, _VP, ctypes.POINTER(_VP)]
         L.wcc.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, _VP]
         L.ppr_reverse_push.argtypes = [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _VP, _VP,
-                                       ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _VP]
+                                       ctypes.POINTER(TargetStats), ctypes.c_int, _VP]
         L.ppr_target.argtypes = [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _VP, ctypes.c_int32,
-                                 ctypes.c_int32, ctypes.c_uint64, _VP, ctypes.c_int, _VP]
+                                 ctypes.c_int32, ctypes.c_uint64, _VP, ctypes.POINTER(TargetStats), ctypes.c_int, _VP]
         L.pagerank_tune.argtypes = [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult), _VP]
         L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                 ctypes.c_int, _VP]
@@ -335,10 +342,11 @@ def _dtype_name(a):
 
 
 def ppr_reverse_push(g: Graph, target: int, r_max: float, p_out=None, r_out=None, damping: float = 0.85,
-                     stream=None) -> int:
+                     stream=None) -> "TargetStats":
     """Reverse push from `target` (section 4.3): p and r (float64, by node id)
-    into CUDA tensors or host arrays, either may be None.  Returns the number
-    of pushes.  Q_s(target) = p(s) + sum_v Q_s(v) r(v) afterwards."""
+    into CUDA tensors or host arrays, either may be None.  Returns the push's
+    counters (pushes, edges, rounds, push_ms).  Q_s(target) = p(s) +
+    sum_v Q_s(v) r(v) afterwards."""
     host = None
     ptrs = []
     for a in (p_out, r_out):
@@ -352,17 +360,17 @@ def ppr_reverse_push(g: Graph, target: int, r_max: float, p_out=None, r_out=None
             raise ValueError("p_out and r_out must both be on the device or both on the host")
         host = h
         ptrs.append(pa)
-    k = ctypes.c_int64(0)
-    _check(lib().ppr_reverse_push(g.handle, int(target), damping, r_max, ptrs[0], ptrs[1], ctypes.byref(k),
+    st = TargetStats()
+    _check(lib().ppr_reverse_push(g.handle, int(target), damping, r_max, ptrs[0], ptrs[1], ctypes.byref(st),
                                   PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
-    return int(k.value)
+    return st
 
 
 def ppr_target(g: Graph, target: int, sources, out, r_max: float, walks: int, seed: int = 1,
-               damping: float = 0.85, stream=None):
+               damping: float = 0.85, stream=None) -> "TargetStats":
     """Bidirectional estimates of pi_s(target) (section 4.3) for each source:
     `sources` (int32) and `out` (float64, same length) both CUDA tensors or
-    both host arrays."""
+    both host arrays.  Returns the call's counters and phase times."""
     if _dtype_name(sources) != "int32" or _dtype_name(out) != "float64":
         raise ValueError("sources must be int32 and out float64")
     if len(sources) != len(out):
@@ -371,8 +379,11 @@ def ppr_target(g: Graph, target: int, sources, out, r_max: float, walks: int, se
     po, h2 = _ptr_and_flag(out)
     if h1 != h2:
         raise ValueError("sources and out must both be on the device or both on the host")
+    st = TargetStats()
     _check(lib().ppr_target(g.handle, int(target), damping, r_max, ps, len(sources), int(walks),
-                            int(seed) & (2 ** 64 - 1), po, PTR_HOST if h1 else PTR_DEVICE, _stream_ptr(stream)))
+                            int(seed) & (2 ** 64 - 1), po, ctypes.byref(st), PTR_HOST if h1 else PTR_DEVICE,
+                            _stream_ptr(stream)))
+    return st
 
 
 def pagerank_tune(g: Graph, dtype: int = FP32, trial_steps: int = 5, stream=None) -> TuneResult:

@@ -21,9 +21,10 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
                          cudaStream_t s);
 
 gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max, double* p_out, double* r_out,
-                            int64_t* pushes, int flags, cudaStream_t s);
+                            gpr_target_stats* st, int flags, cudaStream_t s);
 gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, const int32_t* sources, int32_t k,
-                          int32_t walks, uint64_t seed, double* est_out, int flags, cudaStream_t s);
+                          int32_t walks, uint64_t seed, double* est_out, gpr_target_stats* st, int flags,
+                          cudaStream_t s);
 
 void graph_free_device(gpr_graph* g, cudaStream_t s) {
   if (!g) return;
@@ -34,7 +35,9 @@ void graph_free_device(gpr_graph* g, cudaStream_t s) {
   }
   dfree(g->walk_ptr, s);
   dfree(g->walk_adj, s);
+  dfree(g->walk_nbr, s);
   g->walk_ptr = g->walk_adj = nullptr;
+  g->walk_nbr = nullptr;
   if (g->work) {
     pagerank_work_free(g->work);
     g->work = nullptr;
@@ -271,7 +274,7 @@ gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components,
 }
 
 gpr_status ppr_reverse_push(const gpr_graph* g, int32_t target, double damping, double r_max, double* p_out,
-                            double* r_out, int64_t* pushes, int flags, void* stream) {
+                            double* r_out, gpr_target_stats* stats, int flags, void* stream) {
   clear_error();
   if (!g) {
     set_error("ppr_reverse_push: NULL graph");
@@ -281,12 +284,13 @@ gpr_status ppr_reverse_push(const gpr_graph* g, int32_t target, double damping, 
     set_error("ppr_reverse_push: unknown flags 0x%x", flags);
     return GPR_EINVAL;
   }
-  return run_reverse_push(const_cast<gpr_graph*>(g), target, damping, r_max, p_out, r_out, pushes, flags,
+  return run_reverse_push(const_cast<gpr_graph*>(g), target, damping, r_max, p_out, r_out, stats, flags,
                           (cudaStream_t)stream);
 }
 
 gpr_status ppr_target(const gpr_graph* g, int32_t target, double damping, double r_max, const int32_t* sources,
-                      int32_t k, int32_t walks, uint64_t seed, double* est_out, int flags, void* stream) {
+                      int32_t k, int32_t walks, uint64_t seed, double* est_out, gpr_target_stats* stats, int flags,
+                      void* stream) {
   clear_error();
   if (!g || (k > 0 && (!sources || !est_out))) {
     set_error("ppr_target: NULL graph, sources or output");
@@ -296,8 +300,8 @@ gpr_status ppr_target(const gpr_graph* g, int32_t target, double damping, double
     set_error("ppr_target: unknown flags 0x%x", flags);
     return GPR_EINVAL;
   }
-  return run_ppr_target(const_cast<gpr_graph*>(g), target, damping, r_max, sources, k, walks, seed, est_out, flags,
-                        (cudaStream_t)stream);
+  return run_ppr_target(const_cast<gpr_graph*>(g), target, damping, r_max, sources, k, walks, seed, est_out, stats,
+                        flags, (cudaStream_t)stream);
 }
 
 gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,

@@ -37,6 +37,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "gpr_internal.cuh"
 
@@ -48,7 +50,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kItemEdges = 16;           // in-edges of one frontier node per work item
-constexpr int kRoundsPerCheck = 8;       // rounds launched between host reads of the frontier size
+constexpr int kRoundsPerCheck = 8;       // rounds launched between host reads of the frontier size (4 at first)
 constexpr int32_t kMaxRounds = 1 << 16;  // a push that needs more is reported as an error
 constexpr int kMaxWalkSteps = 1 << 20;
 
@@ -56,8 +58,9 @@ struct PushCtl {
   uint32_t fcount[2];  // frontier sizes by round parity
   uint32_t icount[2];  // work items by round parity
   unsigned long long pushes;
+  unsigned long long edges;  // in-edges scanned
+  uint32_t rounds;           // rounds with a non-empty frontier
   int32_t overflow;
-  int32_t pad;
 };
 
 __device__ __forceinline__ double take_double(double* p) {
@@ -79,18 +82,20 @@ __global__ void __launch_bounds__(kBlock) push_take_kernel(const int32_t* __rest
     ctl->icount[nxt] = 0;
   }
   const uint32_t F = min(ctl->fcount[cur], (uint32_t)n);  // a frontier holds each node at most once
+  if (blockIdx.x == 0 && threadIdx.x == 0 && F > 0) ctl->rounds += 1;
   const int lane = threadIdx.x & 31;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < F; i0 += stride) {
     const uint32_t i = i0 + lane;
-    int32_t nit = 0, e0 = 0;
+    int32_t nit = 0, e0 = 0, deg = 0;
     if (i < F) {
       const int32_t v = frontier[i];
       const double amt = take_double(r + v);
       p[v] += a * amt;
       famt[i] = d * amt;
       e0 = col_ptr[v];
-      nit = (col_ptr[v + 1] - e0 + kItemEdges - 1) / kItemEdges;
+      deg = col_ptr[v + 1] - e0;
+      nit = (deg + kItemEdges - 1) / kItemEdges;
     }
     int32_t incl = nit;
     for (int o = 1; o < 32; o <<= 1) {
@@ -116,7 +121,11 @@ __global__ void __launch_bounds__(kBlock) push_take_kernel(const int32_t* __rest
       }
     }
     const unsigned took = __ballot_sync(0xffffffffu, i < F);
-    if (lane == 0) atomicAdd(&ctl->pushes, (unsigned long long)__popc(took));
+    for (int o = 16; o > 0; o >>= 1) deg += __shfl_xor_sync(0xffffffffu, deg, o);
+    if (lane == 0) {
+      atomicAdd(&ctl->pushes, (unsigned long long)__popc(took));
+      atomicAdd(&ctl->edges, (unsigned long long)(uint32_t)deg);
+    }
   }
 }
 
@@ -133,19 +142,27 @@ __global__ void __launch_bounds__(kBlock) push_scatter_kernel(
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < I; j += stride) {
     const int32_t f = item_f[j];
     const int32_t e0 = item_e[j];
-    const int32_t e1 = min(e0 + kItemEdges, col_ptr[frontier[f] + 1]);
+    const int32_t cnt = min(kItemEdges, col_ptr[frontier[f] + 1] - e0);
     const double amt = famt[f];
-    for (int32_t e = e0; e < e1; ++e) {
-      const int32_t u = row_idx[e];
-      const double inc = amt / (double)outdeg[u];
-      const double old = atomicAdd(r + u, inc);
-      if (old <= r_max && old + inc > r_max) {
+    // all of the item's loads and atomics in flight at once; the crossing
+    // tests only after every add has returned
+    int32_t u[kItemEdges];
+    double inc[kItemEdges], old[kItemEdges];
+#pragma unroll
+    for (int q = 0; q < kItemEdges; ++q) u[q] = q < cnt ? row_idx[e0 + q] : -1;
+#pragma unroll
+    for (int q = 0; q < kItemEdges; ++q) inc[q] = u[q] >= 0 ? amt / (double)outdeg[u[q]] : 0.0;
+#pragma unroll
+    for (int q = 0; q < kItemEdges; ++q) old[q] = u[q] >= 0 ? atomicAdd(r + u[q], inc[q]) : 0.0;
+#pragma unroll
+    for (int q = 0; q < kItemEdges; ++q) {
+      if (u[q] >= 0 && old[q] <= r_max && old[q] + inc[q] > r_max) {
         cg::coalesced_group grp = cg::coalesced_threads();
         uint32_t pos = 0;
         if (grp.thread_rank() == 0) pos = atomicAdd(&ctl->fcount[nxt], grp.size());
         pos = grp.shfl(pos, 0) + grp.thread_rank();
         if (pos < (uint32_t)n)
-          next[pos] = u;
+          next[pos] = u[q];
         else
           ctl->overflow = 1;  // not expected: a node crosses at most once per round
       }
@@ -179,70 +196,152 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t& state) {
   return z ^ (z >> 31);
 }
 
-// One thread per walk; blocks of `bps` per source.  Per source: the sum of
-// r at the endpoints (relabelled r, looked up through old2new) and the count
-// of dangling endpoints.
+// Each adjacency entry's target with its own out-list: nbr[e] = (offset,
+// out-degree) of adj[e], so that a walk step is one 8-byte load; then the
+// entry itself becomes the target's relabelled id, the index of the push's
+// residuals (the order of each list, by caller id, stays).
+__global__ void walk_nbr_kernel(const int32_t* __restrict__ wptr, int32_t* __restrict__ wadj,
+                                const int32_t* __restrict__ old2new, int64_t m, int2* __restrict__ nbr) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = wadj[e];
+    const int32_t b = wptr[v];
+    nbr[e] = make_int2(b, wptr[v + 1] - b);
+    wadj[e] = old2new[v];
+  }
+}
+
+// Walks of the flattened (source index i, walk w) order, idx = i W + w.  A
+// warp owns the range [w0, w0 + per_warp); each lane runs one walk, and a
+// lane whose walk ends takes the next index of the range, so the lanes stay
+// busy although walk lengths are geometric.  The state of a walk is the
+// (offset, out-degree) of its node and the last edge taken; its endpoint is
+// written as the relabelled id, with bit 31 set when that node is dangling.
 __global__ void __launch_bounds__(kBlock) walk_kernel(const int32_t* __restrict__ wptr,
+                                                      const int2* __restrict__ wnbr,
                                                       const int32_t* __restrict__ wadj,
                                                       const int32_t* __restrict__ old2new,
-                                                      const double* __restrict__ r,
-                                                      const int32_t* __restrict__ sources, int32_t walks, int32_t bps,
-                                                      uint64_t seed, uint64_t stop_below,
-                                                      double* __restrict__ sum_r,
-                                                      unsigned long long* __restrict__ n_dang) {
-  const int32_t i = blockIdx.x / bps;
-  const int32_t w = (blockIdx.x % bps) * kBlock + threadIdx.x;
-  double val = 0.0;
-  unsigned dang = 0;
-  if (w < walks) {
-    const int32_t s = sources[i];
-    uint64_t st = seed ^ ((((uint64_t)(uint32_t)i << 32) | (uint32_t)w) * 0xD6E8FEB86659FD93ull);
-    int32_t u = s;
-    int32_t b = wptr[u], k = wptr[u + 1] - b;
-    for (int step = 0; step < kMaxWalkSteps; ++step) {
-      if ((splitmix64(st) >> 11) < stop_below) break;
-      if (k == 0) {
-        u = s;
+                                                      const int32_t* __restrict__ sources, int32_t walks,
+                                                      int64_t total, int32_t per_warp, uint64_t seed,
+                                                      uint64_t stop_below, int32_t* __restrict__ end,
+                                                      unsigned long long* __restrict__ steps_total) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * per_warp;
+  const int64_t w1 = min(w0 + per_warp, total);
+  if (w0 >= w1) return;  // warp-uniform
+  int64_t next = w0 + 32;
+  int64_t idx = w0 + lane < w1 ? w0 + lane : -1;
+  uint64_t st = 0;
+  int32_t src = 0, s_new = 0, s_off = 0, s_deg = 0, off = 0, deg = 0, last_e = -1, moves = 0;
+  unsigned long long steps = 0;
+  auto start = [&]() {
+    const uint32_t i = (uint32_t)idx / (uint32_t)walks;  // idx < 2^31
+    const uint32_t w = (uint32_t)idx - i * (uint32_t)walks;
+    st = seed ^ ((((uint64_t)i << 32) | w) * 0xD6E8FEB86659FD93ull);
+    src = sources[i];
+    s_new = old2new[src];
+    s_off = wptr[src];
+    s_deg = wptr[src + 1] - s_off;
+    off = s_off;
+    deg = s_deg;
+    last_e = -1;
+    moves = 0;
+  };
+  if (idx >= 0) start();
+  for (;;) {
+    bool done = false;
+    if (idx >= 0) {
+      if (moves == kMaxWalkSteps || (splitmix64(st) >> 11) < stop_below) {
+        done = true;
       } else {
-        const uint64_t j = __umul64hi(splitmix64(st) & ~0x7FFull, (uint64_t)k);
-        u = wadj[b + (int32_t)j];
+        ++moves;
+        if (deg == 0) {  // dangling: back to the source
+          off = s_off;
+          deg = s_deg;
+          last_e = -1;
+        } else {
+          last_e = off + (int32_t)__umul64hi(splitmix64(st) & ~0x7FFull, (uint64_t)deg);
+          const int2 nb = __ldg(wnbr + last_e);
+          off = nb.x;
+          deg = nb.y;
+        }
       }
-      b = wptr[u];
-      k = wptr[u + 1] - b;
     }
-    val = r[old2new[u]];
-    dang = k == 0;
+    if (done) {
+      const int32_t id = last_e < 0 ? s_new : wadj[last_e];
+      end[idx] = (int32_t)((uint32_t)id | (deg == 0 ? 0x80000000u : 0u));
+      steps += (unsigned long long)moves;
+    }
+    const unsigned dm = __ballot_sync(0xffffffffu, done);
+    if (dm) {
+      if (done) {
+        const int64_t q = next + __popc(dm & ((1u << lane) - 1u));
+        idx = q < w1 ? q : -1;
+        if (idx >= 0) start();
+      }
+      next += __popc(dm);
+    }
+    if (!__any_sync(0xffffffffu, idx >= 0)) break;
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+  if (lane == 0 && steps) atomicAdd(steps_total, steps);
+}
+
+// One block per source: the estimate from its W endpoints (relabelled ids,
+// bit 31 = dangling), summed in a fixed
+// order (so the result does not depend on the schedule):
+//   p(s) (1 + (d/a) #dangling / W) + sum r(V) / W.
+__global__ void __launch_bounds__(kBlock) estimate_kernel(const double* __restrict__ p,
+                                                          const double* __restrict__ r,
+                                                          const int32_t* __restrict__ old2new,
+                                                          const int32_t* __restrict__ sources,
+                                                          const int32_t* __restrict__ end, int32_t walks,
+                                                          double coef, double* __restrict__ out) {
+  const int32_t i = blockIdx.x;
+  const int32_t* e = end + (int64_t)i * walks;
+  double val = 0.0;
+  uint32_t dang = 0;
+  for (int32_t w = threadIdx.x; w < walks; w += kBlock) {
+    const uint32_t u = (uint32_t)e[w];
+    val += r[u & 0x7FFFFFFFu];
+    dang += u >> 31;
   }
   for (int o = 16; o > 0; o >>= 1) {
     val += __shfl_xor_sync(0xffffffffu, val, o);
     dang += __shfl_xor_sync(0xffffffffu, dang, o);
   }
   __shared__ double s_val[kBlock / 32];
-  __shared__ unsigned s_dang[kBlock / 32];
-  const int wid = threadIdx.x >> 5;
+  __shared__ uint32_t s_dang[kBlock / 32];
   if ((threadIdx.x & 31) == 0) {
-    s_val[wid] = val;
-    s_dang[wid] = dang;
+    s_val[threadIdx.x >> 5] = val;
+    s_dang[threadIdx.x >> 5] = dang;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double tv = 0.0;
-    unsigned td = 0;
+    uint32_t td = 0;
     for (int q = 0; q < kBlock / 32; ++q) {
       tv += s_val[q];
       td += s_dang[q];
     }
-    if (tv != 0.0) atomicAdd(sum_r + i, tv);
-    if (td) atomicAdd(n_dang + i, (unsigned long long)td);
+    out[i] = p[old2new[sources[i]]] * (1.0 + coef * ((double)td / walks)) + tv / walks;
   }
 }
 
-__global__ void estimate_kernel(const double* __restrict__ p, const int32_t* __restrict__ old2new,
-                                const int32_t* __restrict__ sources, int32_t k, int32_t walks, double coef,
-                                const double* __restrict__ sum_r, const unsigned long long* __restrict__ n_dang,
-                                double* __restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = p[old2new[sources[i]]] * (1.0 + coef * ((double)n_dang[i] / walks)) + sum_r[i] / walks;
+// A high-priority stream per device for the push, so that its short rounds
+// get SMs ahead of the walks running beside them on the caller's stream.
+cudaStream_t push_stream() {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  std::lock_guard<std::mutex> lock(mu);
+  const int dev = device_ordinal();
+  auto it = streams.find(dev);
+  if (it != streams.end()) return it->second;
+  int lo = 0, hi = 0;
+  GPR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  cudaStream_t st = nullptr;
+  GPR_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi));
+  streams[dev] = st;
+  return st;
 }
 
 int grid_items(int64_t items, int per_sm = 8) {
@@ -262,17 +361,41 @@ struct Buffers {
   }
 };
 
-// Reverse push from relabelled node tn into p, r (relabelled, n each).
-// Returns the number of pushes.
-int64_t reverse_push(const gpr_graph* g, int32_t tn, double d, double r_max, double* p, double* r, Buffers& buf,
-                     cudaStream_t s) {
+// Device buffers of one reverse push (allocated before any fork, so that a
+// second stream may use them).
+struct PushBufs {
+  int64_t item_cap = 0;
+  int32_t* front[2] = {nullptr, nullptr};
+  double* famt = nullptr;
+  int32_t* item_f = nullptr;
+  int32_t* item_e = nullptr;
+  PushCtl* ctl = nullptr;
+};
+
+PushBufs push_bufs(const gpr_graph* g, Buffers& buf) {
+  PushBufs b;
   const int32_t n = g->n;
-  const int64_t item_cap = (int64_t)n + g->m / kItemEdges + 32;
-  int32_t* front[2] = {(int32_t*)buf.get((size_t)n * 4), (int32_t*)buf.get((size_t)n * 4)};
-  double* famt = (double*)buf.get((size_t)n * 8);
-  int32_t* item_f = (int32_t*)buf.get((size_t)item_cap * 4);
-  int32_t* item_e = (int32_t*)buf.get((size_t)item_cap * 4);
-  PushCtl* ctl = (PushCtl*)buf.get(sizeof(PushCtl));
+  b.item_cap = (int64_t)n + g->m / kItemEdges + 32;
+  b.front[0] = (int32_t*)buf.get((size_t)n * 4);
+  b.front[1] = (int32_t*)buf.get((size_t)n * 4);
+  b.famt = (double*)buf.get((size_t)n * 8);
+  b.item_f = (int32_t*)buf.get((size_t)b.item_cap * 4);
+  b.item_e = (int32_t*)buf.get((size_t)b.item_cap * 4);
+  b.ctl = (PushCtl*)buf.get(sizeof(PushCtl));
+  return b;
+}
+
+// Reverse push from relabelled node tn into p, r (relabelled, n each) on
+// stream s; its counters into st (pushes, edges, rounds).
+void reverse_push(const gpr_graph* g, int32_t tn, double d, double r_max, double* p, double* r, const PushBufs& B,
+                  cudaStream_t s, gpr_target_stats* st) {
+  const int32_t n = g->n;
+  const int64_t item_cap = B.item_cap;
+  int32_t* const* front = B.front;
+  double* famt = B.famt;
+  int32_t* item_f = B.item_f;
+  int32_t* item_e = B.item_e;
+  PushCtl* ctl = B.ctl;
   GPR_CUDA(cudaMemsetAsync(p, 0, (size_t)n * 8, s));
   GPR_CUDA(cudaMemsetAsync(r, 0, (size_t)n * 8, s));
   GPR_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PushCtl), s));
@@ -283,8 +406,8 @@ int64_t reverse_push(const gpr_graph* g, int32_t tn, double d, double r_max, dou
   const int gt = grid_items(n), gs = grid_items(item_cap);
   int32_t round = 0;
   PushCtl h{};
-  for (;;) {
-    for (int q = 0; q < kRoundsPerCheck; ++q, ++round) {
+  for (int batch = kRoundsPerCheck / 2;; batch = kRoundsPerCheck) {
+    for (int q = 0; q < batch; ++q, ++round) {
       const int cur = round & 1;
       push_take_kernel<<<gt, kBlock, 0, s>>>(g->col_ptr, front[cur], ctl, cur, a, d, p, r, famt, item_f, item_e, n,
                                              (uint32_t)item_cap);
@@ -292,15 +415,33 @@ int64_t reverse_push(const gpr_graph* g, int32_t tn, double d, double r_max, dou
                                                 ctl, cur, r_max, r, front[cur ^ 1], n, (uint32_t)item_cap);
     }
     GPR_CUDA(cudaGetLastError());
-    count_launches(2 * kRoundsPerCheck);
+    count_launches(2 * batch);
     GPR_CUDA(cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
     if (h.overflow) throw StatusFail{GPR_ECUDA, "reverse push: frontier or work list overflow"};
     if (h.fcount[round & 1] == 0) break;
     if (round >= kMaxRounds) throw StatusFail{GPR_ETIMEOUT, "reverse push: no end after 65536 rounds"};
   }
-  return (int64_t)h.pushes;
+  st->pushes = (int64_t)h.pushes;
+  st->edges = (int64_t)h.edges;
+  st->rounds = (int32_t)h.rounds;
 }
+
+struct Events {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  Events() {
+    for (auto& x : e) GPR_CUDA(cudaEventCreate(&x));
+  }
+  ~Events() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  double ms(int a, int b) const {
+    float t = 0.f;
+    GPR_CUDA(cudaEventElapsedTime(&t, e[a], e[b]));
+    return t;
+  }
+};
 
 void check_args(const gpr_graph* g, int32_t target, double d, double r_max) {
   if (target < 0 || target >= g->n) throw StatusFail{GPR_EINVAL, "target out of range"};
@@ -318,14 +459,19 @@ int32_t relabelled(const gpr_graph* g, int32_t v, cudaStream_t s) {
 }  // namespace
 
 gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max, double* p_out, double* r_out,
-                            int64_t* pushes, int flags, cudaStream_t s) {
+                            gpr_target_stats* stats, int flags, cudaStream_t s) {
   try {
     check_args(g, target, d, r_max);
     const int32_t n = g->n;
     Buffers buf{s, {}};
+    Events ev;
+    gpr_target_stats st{};
     double* p = (double*)buf.get((size_t)n * 8);
     double* r = (double*)buf.get((size_t)n * 8);
-    const int64_t k = reverse_push(g, relabelled(g, target, s), d, r_max, p, r, buf, s);
+    const int32_t tn = relabelled(g, target, s);
+    GPR_CUDA(cudaEventRecord(ev.e[0], s));
+    reverse_push(g, tn, d, r_max, p, r, push_bufs(g, buf), s, &st);
+    GPR_CUDA(cudaEventRecord(ev.e[1], s));
     double* outs[2] = {p_out, r_out};
     const double* ins[2] = {p, r};
     for (int q = 0; q < 2; ++q) {
@@ -337,7 +483,9 @@ gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max
       if (flags & GPR_PTR_HOST) GPR_CUDA(cudaMemcpyAsync(outs[q], dst, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
     }
     GPR_CUDA(cudaStreamSynchronize(s));
-    if (pushes) *pushes = k;
+    st.push_ms = ev.ms(0, 1);
+    st.total_ms = st.push_ms;
+    if (stats) *stats = st;
     return GPR_OK;
   } catch (const StatusFail& f) {
     set_error("ppr_reverse_push: %s", f.msg.c_str());
@@ -350,19 +498,31 @@ gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max
 }
 
 gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, const int32_t* sources, int32_t k,
-                          int32_t walks, uint64_t seed, double* est_out, int flags, cudaStream_t s) {
+                          int32_t walks, uint64_t seed, double* est_out, gpr_target_stats* stats, int flags,
+                          cudaStream_t s) {
   try {
     check_args(g, target, d, r_max);
     if (k < 0 || walks < 1) throw StatusFail{GPR_EINVAL, "need k >= 0 sources and walks >= 1"};
-    const int64_t bps = (walks + kBlock - 1) / kBlock;
-    if ((int64_t)k * bps > INT32_MAX) throw StatusFail{GPR_EINVAL, "too many walks in one call"};
-    if (k == 0) return GPR_OK;
+    if ((int64_t)k * walks > INT32_MAX) throw StatusFail{GPR_EINVAL, "k * walks must stay below 2^31"};
+    if (k == 0) {
+      if (stats) *stats = gpr_target_stats{};
+      return GPR_OK;
+    }
     const int32_t n = g->n;
     {
       std::lock_guard<std::mutex> lock(g->mu);
-      if (!g->walk_ptr) build_caller_out_adjacency(g, s, &g->walk_ptr, &g->walk_adj);
+      if (!g->walk_ptr) {
+        build_caller_out_adjacency(g, s, &g->walk_ptr, &g->walk_adj);
+        g->walk_nbr = (int2*)dalloc((size_t)std::max<int64_t>(g->m, 1) * sizeof(int2), s);
+        walk_nbr_kernel<<<grid_items(g->m), kBlock, 0, s>>>(g->walk_ptr, g->walk_adj, g->plan.old2new, g->m,
+                                                             g->walk_nbr);
+        GPR_CUDA(cudaGetLastError());
+        count_launches(1);
+      }
     }
     Buffers buf{s, {}};
+    Events ev;
+    gpr_target_stats st{};
     const int32_t* src = sources;
     if (flags & GPR_PTR_HOST) {
       int32_t* dsrc = (int32_t*)buf.get((size_t)k * 4);
@@ -376,27 +536,51 @@ gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, 
     count_launches(1);
     double* p = (double*)buf.get((size_t)n * 8);
     double* r = (double*)buf.get((size_t)n * 8);
+    const int64_t total = (int64_t)k * walks;
+    int32_t* end = (int32_t*)buf.get((size_t)total * 4);
+    unsigned long long* steps_dev = (unsigned long long*)buf.get(8);
+    const PushBufs pb = push_bufs(g, buf);
+    GPR_CUDA(cudaMemsetAsync(steps_dev, 0, 8, s));
     int32_t tn = 0;
     int herr = 0;
     GPR_CUDA(cudaMemcpyAsync(&tn, g->plan.old2new + target, 4, cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
     if (herr) throw StatusFail{GPR_EINVAL, "a source id is out of range"};
-    reverse_push(g, tn, d, r_max, p, r, buf, s);
-    double* sum_r = (double*)buf.get((size_t)k * 8);
-    unsigned long long* n_dang = (unsigned long long*)buf.get((size_t)k * 8);
-    GPR_CUDA(cudaMemsetAsync(sum_r, 0, (size_t)k * 8, s));
-    GPR_CUDA(cudaMemsetAsync(n_dang, 0, (size_t)k * 8, s));
+    // the push on a high-priority stream, the walks beside it on s; they meet
+    // at the estimate
+    cudaStream_t ps = push_stream();
+    GPR_CUDA(cudaEventRecord(ev.e[0], s));
+    GPR_CUDA(cudaStreamWaitEvent(ps, ev.e[0], 0));
+    // about two resident waves of warps, each with a pool of >= 64 walks
+    const int64_t resident_warps = (int64_t)num_sms() * 64;
+    const int32_t per_warp = (int32_t)std::max<int64_t>(64, std::min<int64_t>(4096, total / (2 * resident_warps)));
+    const int64_t warps = (total + per_warp - 1) / per_warp;
     const double a = 1.0 - d;
     const uint64_t stop_below = (uint64_t)std::ceil(std::ldexp(a, 53));
-    walk_kernel<<<(unsigned)(k * bps), kBlock, 0, s>>>(g->walk_ptr, g->walk_adj, g->plan.old2new, r, src,
-                                                       walks, (int32_t)bps, seed, stop_below, sum_r, n_dang);
-    double* out = (flags & GPR_PTR_HOST) ? (double*)buf.get((size_t)k * 8) : est_out;
-    estimate_kernel<<<grid_items(k), kBlock, 0, s>>>(p, g->plan.old2new, src, k, walks, d / a, sum_r, n_dang, out);
+    walk_kernel<<<(unsigned)((warps * 32 + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        g->walk_ptr, g->walk_nbr, g->walk_adj, g->plan.old2new, src, walks, total, per_warp, seed, stop_below, end,
+        steps_dev);
     GPR_CUDA(cudaGetLastError());
-    count_launches(2);
+    count_launches(1);
+    GPR_CUDA(cudaEventRecord(ev.e[2], s));
+    reverse_push(g, tn, d, r_max, p, r, pb, ps, &st);
+    GPR_CUDA(cudaEventRecord(ev.e[1], ps));
+    GPR_CUDA(cudaStreamWaitEvent(s, ev.e[1], 0));
+    double* out = (flags & GPR_PTR_HOST) ? (double*)buf.get((size_t)k * 8) : est_out;
+    estimate_kernel<<<k, kBlock, 0, s>>>(p, r, g->plan.old2new, src, end, walks, d / a, out);
+    GPR_CUDA(cudaGetLastError());
+    count_launches(1);
+    GPR_CUDA(cudaEventRecord(ev.e[3], s));
+    unsigned long long steps = 0;
+    GPR_CUDA(cudaMemcpyAsync(&steps, steps_dev, 8, cudaMemcpyDeviceToHost, s));
     if (flags & GPR_PTR_HOST) GPR_CUDA(cudaMemcpyAsync(est_out, out, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
+    st.walk_steps = (int64_t)steps;
+    st.push_ms = ev.ms(0, 1);
+    st.walk_ms = ev.ms(0, 2);
+    st.total_ms = ev.ms(0, 3);
+    if (stats) *stats = st;
     return GPR_OK;
   } catch (const StatusFail& f) {
     set_error("ppr_target: %s", f.msg.c_str());

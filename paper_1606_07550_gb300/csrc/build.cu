@@ -1043,7 +1043,9 @@ gpr_status update_graph(gpr_graph* g, const int32_t* ins_src, const int32_t* ins
     }
     dfree(g->walk_ptr, s);
     dfree(g->walk_adj, s);
+    dfree(g->walk_nbr, s);
     g->walk_ptr = g->walk_adj = nullptr;
+    g->walk_nbr = nullptr;
     int32_t* n2o = g->plan.new2old;
     int32_t* o2n = g->plan.old2new;
     g->plan.new2old = g->plan.old2new = nullptr;

@@ -134,10 +134,13 @@ struct gpr_graph {
   // the out-adjacency as a CSC over the same relabelled ids (row u lists the
   // destinations of u, ascending), made by the first call that needs it
   gpr_graph* transposed = nullptr;
-  // the out-adjacency in the caller's ids (walk_ptr: n + 1, walk_adj: m; the
-  // destinations of u ascending), made by the first random-walk call
-  int32_t* walk_ptr = nullptr;
-  int32_t* walk_adj = nullptr;
+  // the out-adjacency for random walks, made by the first call that walks:
+  // node u (caller id) lists its destinations in walk_ptr[u] ..
+  // walk_ptr[u + 1), by ascending caller id; walk_adj holds each
+  // destination's relabelled id and walk_nbr its (walk_ptr, out-degree)
+  int32_t* walk_ptr = nullptr;  // n + 1
+  int32_t* walk_adj = nullptr;  // m
+  int2* walk_nbr = nullptr;     // m
 };
 
 namespace gpr {

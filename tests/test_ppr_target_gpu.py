@@ -72,7 +72,8 @@ def test_push_bound_against_contributions(torch, graphs, name, r_max):
     for t in targets_of(ref, rng):
         p = torch.empty(n, dtype=torch.float64, device="cuda")
         r = torch.empty(n, dtype=torch.float64, device="cuda")
-        k = gpr.ppr_reverse_push(g, t, r_max, p, r)
+        st = gpr.ppr_reverse_push(g, t, r_max, p, r)
+        k = st.pushes
         p, r = p.cpu().numpy(), r.cpu().numpy()
         q = contrib(name, ref, t)
         assert (r >= 0).all() and r.max() <= r_max and (p >= 0).all()
@@ -82,6 +83,10 @@ def test_push_bound_against_contributions(torch, graphs, name, r_max):
         po, ro, ko = oracle.reverse_push(ref, t, D, r_max)
         assert np.abs(p - po).max() <= r_max + 1e-13
         assert k >= 1 and (k == 1) == (ko == 1)
+        # each push scans the in-edges of its node; at least one per round
+        assert st.rounds >= 1 and st.pushes >= st.rounds and st.edges >= 0 and st.push_ms > 0
+        if k == 1:
+            assert st.edges == np.diff(ref.col_ptr)[t] and st.rounds == 1
 
 
 def test_push_host_buffers_and_no_push(torch, graphs):
@@ -90,14 +95,15 @@ def test_push_host_buffers_and_no_push(torch, graphs):
     t = int(np.argmax(np.diff(ref.col_ptr)))
     p = np.empty(n)
     r = np.empty(n)
-    k = gpr.ppr_reverse_push(g, t, 1e-5, p, r)
+    k = gpr.ppr_reverse_push(g, t, 1e-5, p, r).pushes
     q = oracle.ppr_contrib(ref, t, D, 260)
     assert k > 1 and np.abs(q - p).max() <= 1e-5 + 1e-13 and r.max() <= 1e-5
     # r_max >= 1: nothing to push
-    k = gpr.ppr_reverse_push(g, t, 1.0, p, r)
-    assert k == 0 and p.max() == 0 and r[t] == 1 and r.sum() == 1
+    st = gpr.ppr_reverse_push(g, t, 1.0, p, r)
+    k = st.pushes
+    assert st.rounds == 0 and st.edges == 0 and k == 0 and p.max() == 0 and r[t] == 1 and r.sum() == 1
     # only one output wanted
-    k2 = gpr.ppr_reverse_push(g, t, 1e-5, p, None)
+    k2 = gpr.ppr_reverse_push(g, t, 1e-5, p, None).pushes
     assert k2 > 1 and np.abs(q - p).max() <= 1e-5 + 1e-13
 
 
@@ -113,8 +119,12 @@ def test_pure_walks_bit_exact(torch, graphs, name):
     for t in targets_of(ref, rng, 2):
         want = oracle.ppr_target(ref, t, sources, D, 1.0, W, seed=123)
         out = torch.empty(len(sources), dtype=torch.float64, device="cuda")
-        gpr.ppr_target(g, t, torch.from_numpy(sources).cuda(), out, 1.0, W, seed=123)
+        st = gpr.ppr_target(g, t, torch.from_numpy(sources).cuda(), out, 1.0, W, seed=123)
         assert (out.cpu().numpy() == want).all(), t
+        # a walk stops with probability a per step: about len * W * d / a steps
+        N = len(sources) * W
+        assert abs(st.walk_steps / N - D / A) < 6 * np.sqrt(D) / A / np.sqrt(N)
+        assert st.pushes == 0 and st.walk_ms > 0 and st.total_ms >= st.walk_ms
         # host buffers
         h = np.empty(len(sources))
         gpr.ppr_target(g, t, sources, h, 1.0, W, seed=123)
@@ -155,6 +165,31 @@ def test_estimates_within_sampling_bound(torch, graphs, name, r_max):
         # the same seeded walks on both sides: the estimates differ only
         # through the pushes, |dp(s)| <= r_max and |dr(V)| <= r_max
         assert abs(e - o) <= r_max * (2 + D / A) + 1e-13
+
+
+@pytest.mark.parametrize("W", [1, 31, 256, 1000])
+def test_walk_runs_split_across_sources(torch, graphs, W):
+    # a thread runs several consecutive walks, which may span sources; many
+    # sources and few walks each put those seams everywhere
+    g, ref = graphs["rmat5k"]
+    rng = np.random.default_rng(W)
+    k = 20_000 // W + 3
+    sources = rng.integers(0, ref.n, k).astype(np.int32)
+    t = int(np.argmax(np.diff(ref.col_ptr)))
+    want = oracle.ppr_target(ref, t, sources, D, 1.0, W, seed=5)
+    out = np.empty(k)
+    gpr.ppr_target(g, t, sources, out, 1.0, W, seed=5)
+    assert (out == want).all()
+
+
+def test_repeatable(torch, graphs):
+    g, ref = graphs["rmat40k"]
+    t = int(np.argmax(np.diff(ref.col_ptr)))
+    sources = np.arange(0, ref.n, 401, dtype=np.int32)
+    a, b = np.empty(len(sources)), np.empty(len(sources))
+    gpr.ppr_target(g, t, sources, a, 1e-6, 500, seed=3)
+    gpr.ppr_target(g, t, sources, b, 1e-6, 500, seed=3)
+    assert np.abs(a - b).max() <= 1e-12      # the push's atomics may round differently
 
 
 def test_errors_and_empty(torch, graphs):
