@@ -61,10 +61,19 @@ def parse_args():
     ap.add_argument("--target-sources", type=int, default=1024, help="target: sources per query")
     ap.add_argument("--target-walks", type=int, default=8192, help="target: walks per source")
     ap.add_argument("--target-rmax", type=float, default=1e-5, help="target: reverse-push threshold")
-    ap.add_argument("--target-scale", type=int, default=25, help="target: R-MAT scale (edge factor 32)")
+    ap.add_argument("--target-scale", "--scale", type=int, default=25,
+                    help="target, wcc: R-MAT scale (edge factor 32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-scale", type=int, default=19)
     return ap.parse_args()
+
+
+def rmat_spec(scale):
+    """R-MAT, edge factor 32, seed 3: the scale-25 benchmark graph or a smaller one of the same recipe."""
+    if scale == 25:
+        return workload("rmat25")
+    from gen.workloads import GraphSpec
+    return GraphSpec(f"rmat-s{scale}-ef32", "rmat", 1 << scale, 1 << (scale + 5), seed=3)
 
 
 def workload(name):
@@ -782,7 +791,7 @@ def run_wcc(args, world, rank, local):
         dt = time.perf_counter() - t0
         cpu = (gs.m / dt / 1e9, dt, f"R-MAT scale {args.cpu_sample_scale}, edge factor 32 (m={gs.m}); union-find, "
                                     "single-threaded oracle")
-    spec = workload("rmat25")
+    spec = rmat_spec(args.target_scale)
     src, dst = make_coo_device(torch, spec)
     g = gpr.graph_build(src, dst, spec.n)
     del src, dst
@@ -829,8 +838,9 @@ def run_wcc(args, world, rank, local):
         "metric": "WCC GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "wcc-rmat-s25-ef32", "n": n, "m": m, "components": k,
-                   "step": "one wcc call: hook/compress rounds to convergence + labels by caller id",
+        "config": {"workload": f"wcc-rmat-s{spec.scale}-ef32", "n": n, "m": m, "components": k,
+                   "step": "one wcc call: sampled links, giant component skipped in one edge pass, labels by "
+                           "caller id",
                    "value_counts": "m / time"},
         "clocks": clk.summary(), "gpu_launches": launches, "save_load": io,
     }
@@ -943,12 +953,7 @@ def run_target(args, world, rank, local):
         dt = time.perf_counter() - t0
         cpu = (done / dt, dt, f"R-MAT scale {args.cpu_sample_scale}, edge factor 32; {done // ks} targets x {ks} "
                               f"sources, r_max {r_max:g}, {W} walks; single-threaded oracle")
-    if args.target_scale == 25:
-        spec = workload("rmat25")
-    else:
-        from gen.workloads import GraphSpec
-        spec = GraphSpec(f"rmat-s{args.target_scale}-ef32", "rmat", 1 << args.target_scale,
-                         1 << (args.target_scale + 5), seed=3)
+    spec = rmat_spec(args.target_scale)
     src, dst = make_coo_device(torch, spec)
     g = gpr.graph_build(src, dst, spec.n)
     del src, dst

@@ -200,8 +200,11 @@ gpr_status eigen_centrality(const gpr_graph* g, int32_t iters, float* x_out, int
  * GPR_PTR_HOST) receives for each node the smallest node id of its
  * component, so the output does not depend on scheduling; num_components
  * (host, nullable) receives the number of components (isolated nodes count).
- * Synchronous.  GPR_ETIMEOUT if the hook rounds do not converge (not
- * expected: a bound that turns a fault into an error). */
+ * Synchronous.  Union-find in the manner of Afforest: two sampled
+ * in-neighbours per node, then one pass over the in-edges not already inside
+ * the largest sampled component.  GPR_ETIMEOUT if a link gives up after 2^20
+ * compare-and-swap retries (not expected: a bound that turns a fault into an
+ * error). */
 gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components, int flags, void* stream);
 
 /* ---- single-target personalised PageRank (bidirectional) --------------------

@@ -42,21 +42,25 @@ __global__ void check_offsets_kernel(const int32_t* __restrict__ col_ptr, int32_
   }
 }
 
-// One thread per row (offsets already checked): sources in range, ascending,
-// no self-loop; counts out-degrees.
+// One warp per row (offsets already checked), lanes over its edges: sources
+// in range, strictly ascending, no self-loop; counts out-degrees.
 __global__ void check_rows_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
                                   int32_t* __restrict__ outdeg, int* __restrict__ err) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    int32_t prev = -1;
-    for (int32_t e = col_ptr[p]; e < col_ptr[p + 1]; ++e) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < n; p += nwarps) {
+    const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+    bool bad = false;
+    for (int32_t e = e0 + lane; e < e1; e += 32) {
       const int32_t u = row_idx[e];
-      if (u <= prev || u >= n || u == (int32_t)p) {
-        atomicOr(err, IOERR_ROWS);
-        break;
+      if (u < 0 || u >= n || u == (int32_t)p || (e > e0 && u <= row_idx[e - 1])) {
+        bad = true;
+      } else {
+        atomicAdd(outdeg + u, 1);
       }
-      atomicAdd(outdeg + u, 1);
-      prev = u;
     }
+    if (bad) atomicOr(err, IOERR_ROWS);
   }
 }
 

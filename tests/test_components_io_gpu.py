@@ -64,6 +64,25 @@ def test_wcc_power_law_and_chains(torch):
     assert k == 77 and (lab == np.arange(77)).all()
 
 
+def test_wcc_giant_choice_and_ties(torch):
+    # two equal cycles (the sampled mode may pick either), a hub whose long
+    # in-row is cut into chunks, nodes reachable only along out-edges into the
+    # giant component, and isolated nodes between them
+    n = 30_000
+    a = np.arange(0, 10_000, dtype=np.int32) * 2            # even ids 0..19998: one cycle
+    b = a + 1                                               # odd ids: another
+    src = [a, b, np.arange(20_000, 29_000, dtype=np.int32)]  # 20000.. point into the hub 5
+    dst = [np.roll(a, 1), np.roll(b, 1), np.full(9_000, 5, np.int32)]
+    src.append(np.array([29_500], np.int32))                 # 29500 -> 3 (only an out-edge)
+    dst.append(np.array([3], np.int32))
+    s_, d_ = np.concatenate(src), np.concatenate(dst)
+    g = gpr.graph_build(s_, d_, n)
+    lab, k = gpu_wcc(torch, g)
+    ref, kr = oracle.wcc(oracle.build_csc(n, s_, d_))
+    assert k == kr and (lab == ref).all()
+    assert lab[29_500] == 1 and lab[25_000] == 1 and lab[0] == 0 and lab[29_999] == 29_999 and k == 1001
+
+
 def test_save_load_round_trip(torch, tmp_path):
     n = 40_000
     src, dst = gen.rmat_coo(n, 700_000, seed=12)
