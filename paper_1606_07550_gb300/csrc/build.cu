@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include "gpr_internal.cuh"
 
@@ -136,7 +137,7 @@ __global__ void digit_starts_kernel(const uint32_t* __restrict__ hist, uint32_t*
 // held warp-striped (item j of warp w is tile position w*512 + j*32 + lane),
 // so (warp, item, lane) order is input order and the per-warp match-based
 // ranking keeps the sort stable.
-__global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(
+__global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
     const uint32_t* __restrict__ dstart, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
     uint32_t epoch, int* __restrict__ derr) {
@@ -159,14 +160,14 @@ __global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(
     int64_t i = base + j * 32;
     k[j] = i < n ? __ldcs(in + i) : kSentinel;
   }
-  uint32_t rk[kItems];
+  uint32_t rk[kItems / 2] = {};  // ranks in the warp (< 512), two 16-bit halves per word
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t d = (uint32_t)(k[j] >> shift) & 255u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t c = s_wcnt[w][d];
-    rk[j] = c + __popc(peers & lt);
+    rk[j >> 1] |= (c + __popc(peers & lt)) << (16 * (j & 1));
     __syncwarp();
     if ((peers & lt) == 0) s_wcnt[w][d] = c + __popc(peers);
     __syncwarp();
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t d = (uint32_t)(k[j] >> shift) & 255u;
-    s_keys[s_tstart[d] + s_wcnt[w][d] + rk[j]] = k[j];
+    s_keys[s_tstart[d] + s_wcnt[w][d] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu)] = k[j];
   }
   __syncthreads();
   for (int i = t; i < kTile; i += kThreads) {
@@ -249,6 +250,11 @@ uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cud
     digit_starts_kernel<<<passes, 256, 0, s>>>(hist, starts);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
+    static std::once_flag carveout;  // four 44 KB blocks per SM need the largest shared-memory carve-out
+    std::call_once(carveout, [] {
+      cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+    });
     uint64_t* a = keys;
     uint64_t* b = alt;
     for (int p = 0; p < passes; ++p) {
@@ -287,6 +293,13 @@ __global__ void degree_kernel(const int32_t* __restrict__ src, const int32_t* __
     }
   }
   if (bad) atomicOr(derr, DERR_BAD_ID);
+}
+
+// out[old2new[v]] = a[v]
+__global__ void permute_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ old2new, int32_t n,
+                               int32_t* __restrict__ out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    out[old2new[v]] = a[v];
 }
 
 __global__ void max_kernel(const int32_t* __restrict__ a, int32_t n, int32_t* __restrict__ out) {
@@ -404,7 +417,7 @@ __global__ void __launch_bounds__(kThreads) dedupe_kernel(
     const uint64_t* __restrict__ keys, int64_t m_raw, int b, int32_t n, int32_t* __restrict__ row_idx,
     int32_t* __restrict__ col_ptr, int32_t* __restrict__ outdeg, uint64_t* __restrict__ status,
     uint32_t* __restrict__ tile_ctr, int64_t* __restrict__ m_out, Gap* __restrict__ gaps,
-    uint32_t* __restrict__ ngaps, int* __restrict__ derr, int withhold_tile0) {
+    uint32_t* __restrict__ ngaps, int* __restrict__ derr, int withhold_tile0, int degree_from_raw) {
   __shared__ uint32_t s_wsum[kWarps];
   __shared__ uint64_t s_excl;
   __shared__ uint32_t s_tile;
@@ -462,10 +475,11 @@ __global__ void __launch_bounds__(kThreads) dedupe_kernel(
     const uint64_t next = next_key(k, j, lane, i, keys, m_raw);
     if (i < m_raw && k[j] != kSentinel) {
       const int32_t v = (int32_t)(k[j] >> b);
+      const int32_t u = (int32_t)(k[j] & src_mask);
+      if (!keep && degree_from_raw) atomicSub(&outdeg[u], 1);  // a duplicate: counted in the raw degree
       if (keep) {
-        const int32_t u = (int32_t)(k[j] & src_mask);
         row_idx[my_o] = u;
-        atomicAdd(&outdeg[u], 1);
+        if (!degree_from_raw) atomicAdd(&outdeg[u], 1);
         // rows (pv, v] start at my_o; the previous key is valid because
         // sentinels sort last
         const int32_t pv = (i > 0) ? (int32_t)(prev >> b) : -1;
@@ -521,11 +535,14 @@ static int grid_for(int64_t items, int per_sm = 8) {
 }
 
 // Sorted unique-or-not keys (length m_keys) -> CSC arrays; returns m.
+// degree_from_raw: outdeg already holds each source's count of non-loop keys
+// (duplicates included), and the de-duplication subtracts the duplicates;
+// otherwise outdeg is counted from the kept keys.
 static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b, int32_t n, uint32_t* hist,
                            int32_t* col_ptr, int32_t* row_idx, int32_t* outdeg, int* derr, Temps& tmp,
-                           cudaStream_t s, bool presorted = false) {
+                           cudaStream_t s, bool presorted = false, bool degree_from_raw = false) {
   GPR_CUDA(cudaMemsetAsync(col_ptr, 0, ((size_t)n + 1) * 4, s));
-  GPR_CUDA(cudaMemsetAsync(outdeg, 0, (size_t)n * 4, s));
+  if (!degree_from_raw) GPR_CUDA(cudaMemsetAsync(outdeg, 0, (size_t)n * 4, s));
   if (m_keys == 0) return 0;
   uint64_t* sorted = presorted ? keys : radix_sort_u64(keys, alt, m_keys, 2 * b, s, derr, hist);
   const int64_t tiles = (m_keys + kTile - 1) / kTile;
@@ -542,7 +559,7 @@ static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b,
   const char* inj = getenv("GPR_INJECT_LOOKBACK_STALL");
   const int withhold = (inj && atoi(inj) != 0 && tiles > 1) ? 1 : 0;
   dedupe_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(sorted, m_keys, b, n, row_idx, col_ptr, outdeg, status, ctr,
-                                                     m_dev, gaps, ngaps, derr, withhold);
+                                                     m_dev, gaps, ngaps, derr, withhold, degree_from_raw ? 1 : 0);
   GPR_CUDA(cudaGetLastError());
   count_launches(1);
   gap_fill_kernel<<<num_sms() * 2, kThreads, 0, s>>>(col_ptr, gaps, ngaps);
@@ -640,7 +657,11 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       row_idx_full = (int32_t*)tmp.get((size_t)m_raw * 4);
-      m = keys_to_csc(keys, alt, m_raw, b, n, hist, g->col_ptr, row_idx_full, g->outdeg, derr, tmp, s);
+      permute_kernel<<<grid_for(n), kThreads, 0, s>>>(odeg, g->plan.old2new, n, g->outdeg);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      m = keys_to_csc(keys, alt, m_raw, b, n, hist, g->col_ptr, row_idx_full, g->outdeg, derr, tmp, s,
+                      /*presorted=*/false, /*degree_from_raw=*/true);
       GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
       GPR_CUDA(cudaStreamSynchronize(s));
       if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_build: a device-side wait timed out"};
