@@ -127,22 +127,16 @@ __device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int32_t d, u
 // ---- layout construction --------------------------------------------------
 
 // key = row-in-bin | source-in-block | (b * S + s), one per CSC edge, in CSC
-// order.  Warp per row.
+// order.
 __global__ void bk_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
                                int sb_bits, int w_bits, int kbits, int32_t S, uint64_t* __restrict__ keys) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint32_t sb_mask = (1u << sb_bits) - 1;
-  for (int64_t p = warp; p < n; p += nwarps) {
-    const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
+  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
     const uint64_t b = (uint64_t)(p >> w_bits);
     const uint64_t hi = (uint64_t)(p & ((1 << w_bits) - 1)) << (sb_bits + kbits);
-    for (int32_t e = e0 + lane; e < e1; e += 32) {
-      const uint32_t u = (uint32_t)row_idx[e];
-      keys[e] = hi | ((uint64_t)(u & sb_mask) << kbits) | (b * (uint64_t)S + (u >> sb_bits));
-    }
-  }
+    const uint32_t u = (uint32_t)row_idx[e];
+    keys[e] = hi | ((uint64_t)(u & sb_mask) << kbits) | (b * (uint64_t)S + (u >> sb_bits));
+  });
 }
 
 // From the keys sorted (stably) on their low kbits bits: the local ids of

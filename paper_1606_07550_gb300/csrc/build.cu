@@ -571,16 +571,12 @@ static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b,
   return m;
 }
 
-// Keys (src << b | dst) of every edge of a CSC, in CSC order: one warp per row.
+// Keys (src << b | dst) of every edge of a CSC, in CSC order.
 __global__ void transpose_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                                       int32_t n, int b, uint64_t* __restrict__ keys) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = warp; p < n; p += nwarps) {
-    const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
-    for (int32_t e = e0 + lane; e < e1; e += 32) keys[e] = ((uint64_t)(uint32_t)row_idx[e] << b) | (uint64_t)p;
-  }
+  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
+    keys[e] = ((uint64_t)(uint32_t)row_idx[e] << b) | (uint64_t)p;
+  });
 }
 
 void graph_free_device(gpr_graph* g, cudaStream_t s);
@@ -755,18 +751,13 @@ gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s) {
   }
 }
 
-// Keys (caller src << b | caller dst) of every edge: one warp per row.
+// Keys (caller src << b | caller dst) of every edge.
 __global__ void caller_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                                    const int32_t* __restrict__ new2old, int32_t n, int b,
                                    uint64_t* __restrict__ keys) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = warp; p < n; p += nwarps) {
-    const uint64_t dst = (uint32_t)new2old[p];
-    const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
-    for (int32_t e = e0 + lane; e < e1; e += 32) keys[e] = ((uint64_t)(uint32_t)new2old[row_idx[e]] << b) | dst;
-  }
+  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
+    keys[e] = ((uint64_t)(uint32_t)new2old[row_idx[e]] << b) | (uint64_t)(uint32_t)new2old[p];
+  });
 }
 
 // The out-adjacency in the caller's ids: out_ptr[u] .. out_ptr[u + 1] indexes
@@ -830,12 +821,9 @@ __global__ void check_ids_kernel(const int32_t* __restrict__ src, const int32_t*
 // key = row << b | source for every edge of a CSC, in CSC (= key) order.
 __global__ void own_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
                                 int b, uint64_t* __restrict__ keys) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = warp; p < n; p += nwarps)
-    for (int32_t e = col_ptr[p] + lane; e < col_ptr[p + 1]; e += 32)
-      keys[e] = ((uint64_t)p << b) | (uint64_t)(uint32_t)row_idx[e];
+  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
+    keys[e] = ((uint64_t)p << b) | (uint64_t)(uint32_t)row_idx[e];
+  });
 }
 
 __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t key) {
