@@ -236,6 +236,10 @@ def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
         return
+    if args.workload not in ("rmat25", "rmat-lj", "er10k"):
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on the PageRank "
+                                                             "workloads only (rmat25, rmat-lj, er10k)"}), flush=True)
+        return
     spec = workload(args.workload)
     scale = min(args.cpu_sample_scale - 1, spec.scale)
     for _ in range(args.warmup):
