@@ -249,7 +249,8 @@ gpr_status wcc(const gpr_graph* g, int32_t* labels_out, int32_t* num_components,
  * over each source's walks is taken in a fixed order, so a call's result
  * depends only on its arguments and the push's rounding. 
  * The first call on a graph builds the out-adjacency in node-id order and
- * keeps it with the graph.  Synchronous.  GPR_EINVAL for a bad argument
+ * a push workspace and keeps them with the graph; calls on one graph take
+ * turns (a per-graph lock).  Synchronous.  GPR_EINVAL for a bad argument
  * (including a source id out of range), GPR_ETIMEOUT as above. */
 typedef struct {
   int64_t pushes;     /* pushes taken by the backward phase */

@@ -26,8 +26,11 @@ gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, 
                           int32_t walks, uint64_t seed, double* est_out, gpr_target_stats* st, int flags,
                           cudaStream_t s);
 
+void target_work_free(const gpr_graph* g, cudaStream_t s);  // bippr.cu
+
 void graph_free_device(gpr_graph* g, cudaStream_t s) {
   if (!g) return;
+  target_work_free(g, s);
   if (g->transposed) {
     graph_free_device(g->transposed, s);
     delete g->transposed;

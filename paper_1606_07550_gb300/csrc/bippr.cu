@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kBlock) push_scatter_kernel(
     const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, const int32_t* __restrict__ outdeg,
     const int32_t* __restrict__ frontier, const int32_t* __restrict__ item_f, const int32_t* __restrict__ item_e,
     const double* __restrict__ famt, PushCtl* ctl, int cur, double r_max, double* __restrict__ r,
-    int32_t* __restrict__ next, int32_t n, uint32_t item_cap) {
+    int32_t* __restrict__ next, int32_t n, uint32_t item_cap, uint32_t* __restrict__ dirty) {
   const int nxt = cur ^ 1;
   const uint32_t I = min(ctl->icount[cur], item_cap);
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -153,7 +153,10 @@ __global__ void __launch_bounds__(kBlock) push_scatter_kernel(
 #pragma unroll
     for (int q = 0; q < kItemEdges; ++q) inc[q] = u[q] >= 0 ? amt / (double)outdeg[u[q]] : 0.0;
 #pragma unroll
-    for (int q = 0; q < kItemEdges; ++q) old[q] = u[q] >= 0 ? atomicAdd(r + u[q], inc[q]) : 0.0;
+    for (int q = 0; q < kItemEdges; ++q) old[q] = u[q] >= 0 ? atomicAdd(r + u[q], inc[q]) : 1.0;
+#pragma unroll
+    for (int q = 0; q < kItemEdges; ++q)  // first touch since zero: to be cleared after the call
+      if (old[q] == 0.0) atomicOr(dirty + (u[q] >> 5), 1u << (u[q] & 31));
 #pragma unroll
     for (int q = 0; q < kItemEdges; ++q) {
       if (u[q] >= 0 && old[q] <= r_max && old[q] + inc[q] > r_max) {
@@ -171,8 +174,9 @@ __global__ void __launch_bounds__(kBlock) push_scatter_kernel(
 }
 
 __global__ void set_residual_kernel(double* __restrict__ r, int32_t v, int32_t* __restrict__ frontier,
-                                    PushCtl* ctl, int above) {
+                                    PushCtl* ctl, int above, uint32_t* __restrict__ dirty) {
   r[v] = 1.0;
+  dirty[v >> 5] |= 1u << (v & 31);
   frontier[0] = v;
   ctl->fcount[0] = above ? 1u : 0u;
 }
@@ -361,10 +365,16 @@ struct Buffers {
   }
 };
 
-// Device buffers of one reverse push (allocated before any fork, so that a
-// second stream may use them).
-struct PushBufs {
+// The reverse push's device workspace, one per graph, kept between calls.
+// p and r are zero between calls: a call marks in `dirty` (one bit per node)
+// every node whose residual it touches first, and wipe_kernel clears exactly
+// those entries (and the bits) at its end, instead of two n-sized memsets.
+struct PushWork {
+  int32_t n = 0;
   int64_t item_cap = 0;
+  double* p = nullptr;
+  double* r = nullptr;
+  uint32_t* dirty = nullptr;
   int32_t* front[2] = {nullptr, nullptr};
   double* famt = nullptr;
   int32_t* item_f = nullptr;
@@ -372,34 +382,103 @@ struct PushBufs {
   PushCtl* ctl = nullptr;
 };
 
-PushBufs push_bufs(const gpr_graph* g, Buffers& buf) {
-  PushBufs b;
-  const int32_t n = g->n;
-  b.item_cap = (int64_t)n + g->m / kItemEdges + 32;
-  b.front[0] = (int32_t*)buf.get((size_t)n * 4);
-  b.front[1] = (int32_t*)buf.get((size_t)n * 4);
-  b.famt = (double*)buf.get((size_t)n * 8);
-  b.item_f = (int32_t*)buf.get((size_t)b.item_cap * 4);
-  b.item_e = (int32_t*)buf.get((size_t)b.item_cap * 4);
-  b.ctl = (PushCtl*)buf.get(sizeof(PushCtl));
-  return b;
+std::mutex g_work_mu;
+std::map<const gpr_graph*, PushWork*> g_work;
+
+void free_work(PushWork* w, cudaStream_t s) {
+  for (void* q : {(void*)w->p, (void*)w->r, (void*)w->dirty, (void*)w->front[0], (void*)w->front[1],
+                  (void*)w->famt, (void*)w->item_f, (void*)w->item_e, (void*)w->ctl})
+    dfree(q, s);
+  delete w;
 }
 
-// Reverse push from relabelled node tn into p, r (relabelled, n each) on
-// stream s; its counters into st (pushes, edges, rounds).
-void reverse_push(const gpr_graph* g, int32_t tn, double d, double r_max, double* p, double* r, const PushBufs& B,
-                  cudaStream_t s, gpr_target_stats* st) {
+// The graph's workspace, made on first use; the work lists grow with m
+// (edge updates).  Callers hold g->mu.
+PushWork* push_work(const gpr_graph* g, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_work_mu);
+  PushWork*& w = g_work[g];
   const int32_t n = g->n;
-  const int64_t item_cap = B.item_cap;
-  int32_t* const* front = B.front;
-  double* famt = B.famt;
-  int32_t* item_f = B.item_f;
-  int32_t* item_e = B.item_e;
-  PushCtl* ctl = B.ctl;
-  GPR_CUDA(cudaMemsetAsync(p, 0, (size_t)n * 8, s));
-  GPR_CUDA(cudaMemsetAsync(r, 0, (size_t)n * 8, s));
+  const int64_t cap = (int64_t)n + g->m / kItemEdges + 32;
+  if (!w) {
+    w = new PushWork();
+    try {
+      w->n = n;
+      w->p = (double*)dalloc((size_t)n * 8, s);
+      w->r = (double*)dalloc((size_t)n * 8, s);
+      w->dirty = (uint32_t*)dalloc(((size_t)n + 31) / 32 * 4, s);
+      w->front[0] = (int32_t*)dalloc((size_t)n * 4, s);
+      w->front[1] = (int32_t*)dalloc((size_t)n * 4, s);
+      w->famt = (double*)dalloc((size_t)n * 8, s);
+      w->ctl = (PushCtl*)dalloc(sizeof(PushCtl), s);
+      GPR_CUDA(cudaMemsetAsync(w->p, 0, (size_t)n * 8, s));
+      GPR_CUDA(cudaMemsetAsync(w->r, 0, (size_t)n * 8, s));
+      GPR_CUDA(cudaMemsetAsync(w->dirty, 0, ((size_t)n + 31) / 32 * 4, s));
+    } catch (...) {
+      free_work(w, s);
+      g_work.erase(g);
+      throw;
+    }
+  }
+  if (w->item_cap < cap) {
+    dfree(w->item_f, s);
+    dfree(w->item_e, s);
+    w->item_f = w->item_e = nullptr;
+    w->item_cap = 0;
+    w->item_f = (int32_t*)dalloc((size_t)cap * 4, s);
+    w->item_e = (int32_t*)dalloc((size_t)cap * 4, s);
+    w->item_cap = cap;
+  }
+  return w;
+}
+
+// After a failed call the workspace may hold residue: drop it.
+void drop_work(const gpr_graph* g, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_work_mu);
+  auto it = g_work.find(g);
+  if (it == g_work.end()) return;
+  cudaDeviceSynchronize();  // the push may have been running on another stream
+  free_work(it->second, s);
+  g_work.erase(it);
+}
+
+// p[v] = r[v] = 0 for every node marked in dirty; the marks cleared.
+__global__ void wipe_kernel(double* __restrict__ p, double* __restrict__ r, uint32_t* __restrict__ dirty,
+                            int32_t n) {
+  const int64_t words = ((int64_t)n + 31) / 32;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t bits = dirty[i];
+    if (!bits) continue;
+    dirty[i] = 0;
+    for (; bits; bits &= bits - 1) {
+      const int64_t v = i * 32 + __ffs(bits) - 1;
+      p[v] = 0.0;
+      r[v] = 0.0;
+    }
+  }
+}
+
+void wipe(PushWork* w, cudaStream_t s) {
+  wipe_kernel<<<grid_items((w->n + 31) / 32), kBlock, 0, s>>>(w->p, w->r, w->dirty, w->n);
+  GPR_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+// Reverse push from relabelled node tn into the workspace's p, r
+// (relabelled, zero on entry) on stream s; its counters into st (pushes,
+// edges, rounds).
+void reverse_push(const gpr_graph* g, int32_t tn, double d, double r_max, PushWork* W, cudaStream_t s,
+                  gpr_target_stats* st) {
+  const int32_t n = g->n;
+  const int64_t item_cap = W->item_cap;
+  int32_t* const* front = W->front;
+  double* famt = W->famt;
+  int32_t* item_f = W->item_f;
+  int32_t* item_e = W->item_e;
+  PushCtl* ctl = W->ctl;
+  double* p = W->p;
+  double* r = W->r;
   GPR_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PushCtl), s));
-  set_residual_kernel<<<1, 1, 0, s>>>(r, tn, front[0], ctl, 1.0 > r_max ? 1 : 0);
+  set_residual_kernel<<<1, 1, 0, s>>>(r, tn, front[0], ctl, 1.0 > r_max ? 1 : 0, W->dirty);
   GPR_CUDA(cudaGetLastError());
   count_launches(1);
   const double a = 1.0 - d;
@@ -412,7 +491,7 @@ void reverse_push(const gpr_graph* g, int32_t tn, double d, double r_max, double
       push_take_kernel<<<gt, kBlock, 0, s>>>(g->col_ptr, front[cur], ctl, cur, a, d, p, r, famt, item_f, item_e, n,
                                              (uint32_t)item_cap);
       push_scatter_kernel<<<gs, kBlock, 0, s>>>(g->col_ptr, g->row_idx, g->outdeg, front[cur], item_f, item_e, famt,
-                                                ctl, cur, r_max, r, front[cur ^ 1], n, (uint32_t)item_cap);
+                                                ctl, cur, r_max, r, front[cur ^ 1], n, (uint32_t)item_cap, W->dirty);
     }
     GPR_CUDA(cudaGetLastError());
     count_launches(2 * batch);
@@ -458,22 +537,31 @@ int32_t relabelled(const gpr_graph* g, int32_t v, cudaStream_t s) {
 
 }  // namespace
 
+// Frees the push workspace of g, if it has one (called when g is freed).
+void target_work_free(const gpr_graph* g, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_work_mu);
+  auto it = g_work.find(g);
+  if (it == g_work.end()) return;
+  free_work(it->second, s);
+  g_work.erase(it);
+}
+
 gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max, double* p_out, double* r_out,
                             gpr_target_stats* stats, int flags, cudaStream_t s) {
   try {
     check_args(g, target, d, r_max);
     const int32_t n = g->n;
+    std::lock_guard<std::mutex> lock(g->mu);
     Buffers buf{s, {}};
     Events ev;
     gpr_target_stats st{};
-    double* p = (double*)buf.get((size_t)n * 8);
-    double* r = (double*)buf.get((size_t)n * 8);
+    PushWork* W = push_work(g, s);
     const int32_t tn = relabelled(g, target, s);
     GPR_CUDA(cudaEventRecord(ev.e[0], s));
-    reverse_push(g, tn, d, r_max, p, r, push_bufs(g, buf), s, &st);
+    reverse_push(g, tn, d, r_max, W, s, &st);
     GPR_CUDA(cudaEventRecord(ev.e[1], s));
     double* outs[2] = {p_out, r_out};
-    const double* ins[2] = {p, r};
+    const double* ins[2] = {W->p, W->r};
     for (int q = 0; q < 2; ++q) {
       if (!outs[q]) continue;
       double* dst = (flags & GPR_PTR_HOST) ? (double*)buf.get((size_t)n * 8) : outs[q];
@@ -482,16 +570,19 @@ gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max
       count_launches(1);
       if (flags & GPR_PTR_HOST) GPR_CUDA(cudaMemcpyAsync(outs[q], dst, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
     }
+    wipe(W, s);
     GPR_CUDA(cudaStreamSynchronize(s));
     st.push_ms = ev.ms(0, 1);
     st.total_ms = st.push_ms;
     if (stats) *stats = st;
     return GPR_OK;
   } catch (const StatusFail& f) {
+    drop_work(g, s);
     set_error("ppr_reverse_push: %s", f.msg.c_str());
     return f.st;
   } catch (const CudaFail& f) {
     cudaGetLastError();
+    drop_work(g, s);
     set_error("ppr_reverse_push: %s failed: %s", f.what, cudaGetErrorString(f.err));
     return GPR_ECUDA;
   }
@@ -500,6 +591,7 @@ gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max
 gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, const int32_t* sources, int32_t k,
                           int32_t walks, uint64_t seed, double* est_out, gpr_target_stats* stats, int flags,
                           cudaStream_t s) {
+  bool pushed = false;
   try {
     check_args(g, target, d, r_max);
     if (k < 0 || walks < 1) throw StatusFail{GPR_EINVAL, "need k >= 0 sources and walks >= 1"};
@@ -509,16 +601,14 @@ gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, 
       return GPR_OK;
     }
     const int32_t n = g->n;
-    {
-      std::lock_guard<std::mutex> lock(g->mu);
-      if (!g->walk_ptr) {
-        build_caller_out_adjacency(g, s, &g->walk_ptr, &g->walk_adj);
-        g->walk_nbr = (int2*)dalloc((size_t)std::max<int64_t>(g->m, 1) * sizeof(int2), s);
-        walk_nbr_kernel<<<grid_items(g->m), kBlock, 0, s>>>(g->walk_ptr, g->walk_adj, g->plan.old2new, g->m,
-                                                             g->walk_nbr);
-        GPR_CUDA(cudaGetLastError());
-        count_launches(1);
-      }
+    std::lock_guard<std::mutex> lock(g->mu);  // the walk arrays and the push workspace are the graph's
+    if (!g->walk_ptr) {
+      build_caller_out_adjacency(g, s, &g->walk_ptr, &g->walk_adj);
+      g->walk_nbr = (int2*)dalloc((size_t)std::max<int64_t>(g->m, 1) * sizeof(int2), s);
+      walk_nbr_kernel<<<grid_items(g->m), kBlock, 0, s>>>(g->walk_ptr, g->walk_adj, g->plan.old2new, g->m,
+                                                           g->walk_nbr);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
     }
     Buffers buf{s, {}};
     Events ev;
@@ -534,12 +624,10 @@ gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, 
     check_sources_kernel<<<grid_items(k), kBlock, 0, s>>>(src, k, n, err);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
-    double* p = (double*)buf.get((size_t)n * 8);
-    double* r = (double*)buf.get((size_t)n * 8);
     const int64_t total = (int64_t)k * walks;
     int32_t* end = (int32_t*)buf.get((size_t)total * 4);
     unsigned long long* steps_dev = (unsigned long long*)buf.get(8);
-    const PushBufs pb = push_bufs(g, buf);
+    PushWork* W = push_work(g, s);
     GPR_CUDA(cudaMemsetAsync(steps_dev, 0, 8, s));
     int32_t tn = 0;
     int herr = 0;
@@ -564,14 +652,16 @@ gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, 
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
     GPR_CUDA(cudaEventRecord(ev.e[2], s));
-    reverse_push(g, tn, d, r_max, p, r, pb, ps, &st);
+    pushed = true;
+    reverse_push(g, tn, d, r_max, W, ps, &st);
     GPR_CUDA(cudaEventRecord(ev.e[1], ps));
     GPR_CUDA(cudaStreamWaitEvent(s, ev.e[1], 0));
     double* out = (flags & GPR_PTR_HOST) ? (double*)buf.get((size_t)k * 8) : est_out;
-    estimate_kernel<<<k, kBlock, 0, s>>>(p, r, g->plan.old2new, src, end, walks, d / a, out);
+    estimate_kernel<<<k, kBlock, 0, s>>>(W->p, W->r, g->plan.old2new, src, end, walks, d / a, out);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
     GPR_CUDA(cudaEventRecord(ev.e[3], s));
+    wipe(W, s);
     unsigned long long steps = 0;
     GPR_CUDA(cudaMemcpyAsync(&steps, steps_dev, 8, cudaMemcpyDeviceToHost, s));
     if (flags & GPR_PTR_HOST) GPR_CUDA(cudaMemcpyAsync(est_out, out, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
@@ -583,10 +673,12 @@ gpr_status run_ppr_target(gpr_graph* g, int32_t target, double d, double r_max, 
     if (stats) *stats = st;
     return GPR_OK;
   } catch (const StatusFail& f) {
+    if (pushed) drop_work(g, s);
     set_error("ppr_target: %s", f.msg.c_str());
     return f.st;
   } catch (const CudaFail& f) {
     cudaGetLastError();
+    if (pushed) drop_work(g, s);
     set_error("ppr_target: %s failed: %s", f.what, cudaGetErrorString(f.err));
     return GPR_ECUDA;
   }
