@@ -729,7 +729,7 @@ def run_hits(args, world, rank, local):
     hub = torch.empty(n, device="cuda")
     auth = torch.empty(n, device="cuda")
     for _ in range(args.warmup):
-        gpr.hits(g, hub, auth, iters=iters, stream=stream)
+        gpr.hits(g, hub, auth, iters=iters, stream=stream, spmv=args.spmv)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
@@ -740,7 +740,7 @@ def run_hits(args, world, rank, local):
     with ClockSampler(gpu_index) as clk:
         for k in range(args.steps):
             evs[k][0].record(stream)
-            gpr.hits(g, hub, auth, iters=iters, stream=stream)
+            gpr.hits(g, hub, auth, iters=iters, stream=stream, spmv=args.spmv)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
     barrier(world)
@@ -758,9 +758,10 @@ def run_hits(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "hits-rmat-s25-ef32", "n": n, "m": m, "iters": iters,
-                   "step": "one hits call: 20 iterations (two pull products each) + L2 output",
+                   "step": "one hits call: 20 iterations (two products each) + L2 output",
+                   "schedule": "blocked" if args.spmv != "pull" and m >= (1 << 22) else "pull",
                    "value_counts": "2 m iters / time", "l2": "inputs larger than L2 (CSC 4 GiB x 2)"},
-        "roofline": {"kernel": "HITS iteration (bucketed pull SpMV on the CSC and its transpose + fold)",
+        "roofline": {"kernel": "HITS iteration (two products, on the CSC and its transpose, + folds)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "bytes_model": "2 x (8m + 12n + 4) per iteration", "traffic": None},
         "clocks": clk.summary(), "gpu_launches": launches,

@@ -188,7 +188,10 @@ gpr_status pagerank_tune(const gpr_graph* g, gpr_dtype dt, int32_t trial_steps, 
  * floats each, unit L2 norm, indexed by node id; device memory, or host
  * memory with GPR_PTR_HOST (then the call is synchronous).  FP32 products,
  * FP64 norms.  hits builds the graph's out-adjacency on its first call and
- * keeps it with the graph.  Calls on one graph must not overlap in time (they
+ * keeps it with the graph.  The products take the pull schedule, or the
+ * blocked one (GPR_SPMV_BLOCKED, the default for graphs of 2^22 or more
+ * edges; GPR_SPMV_PULL forces the pull schedule), with the vectors
+ * L1-normalised between products.  Calls on one graph must not overlap in time (they
  * share the graph's workspace with pagerank). */
 gpr_status hits(const gpr_graph* g, int32_t iters, float* hub_out, float* auth_out, int flags, void* stream);
 gpr_status eigen_centrality(const gpr_graph* g, int32_t iters, float* x_out, int flags, void* stream);

@@ -311,20 +311,22 @@ def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int =
     return st
 
 
-def hits(g: Graph, hub_out, auth_out, iters: int = 50, stream=None):
+def hits(g: Graph, hub_out, auth_out, iters: int = 50, stream=None, spmv: str = "auto"):
     """HITS hubs and authorities (unit L2 norm, by node id) into two CUDA
-    tensors, or host arrays / CPU tensors."""
+    tensors, or host arrays / CPU tensors.  spmv: "auto", "pull" or "blocked"."""
     ph, host = _ptr_and_flag(hub_out)
     pa, host2 = _ptr_and_flag(auth_out)
     if host != host2:
         raise ValueError("hub_out and auth_out must both be on the device or both on the host")
-    _check(lib().hits(g.handle, iters, ph, pa, PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
+    _check(lib().hits(g.handle, iters, ph, pa, (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv],
+                      _stream_ptr(stream)))
 
 
-def eigen_centrality(g: Graph, out, iters: int = 50, stream=None):
+def eigen_centrality(g: Graph, out, iters: int = 50, stream=None, spmv: str = "auto"):
     """Eigenvector centrality (unit L2 norm, by node id) into `out`."""
     po, host = _ptr_and_flag(out)
-    _check(lib().eigen_centrality(g.handle, iters, po, PTR_HOST if host else PTR_DEVICE, _stream_ptr(stream)))
+    _check(lib().eigen_centrality(g.handle, iters, po, (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv],
+                                  _stream_ptr(stream)))
 
 
 def wcc(g: Graph, out, stream=None) -> int:

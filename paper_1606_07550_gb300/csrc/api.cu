@@ -234,8 +234,9 @@ static gpr_status check_centrality(const char* what, const gpr_graph* g, int32_t
     set_error("%s: iters %d outside [0, 2^20]", what, (int)iters);
     return GPR_EINVAL;
   }
-  if (flags & ~GPR_PTR_HOST) {
-    set_error("%s: unknown flags 0x%x", what, flags);
+  if ((flags & ~(GPR_PTR_HOST | GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) ||
+      (flags & (GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) == (GPR_SPMV_PULL | GPR_SPMV_BLOCKED)) {
+    set_error("%s: unknown or conflicting flags 0x%x", what, flags);
     return GPR_EINVAL;
   }
   return GPR_OK;

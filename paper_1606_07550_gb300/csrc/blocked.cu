@@ -728,7 +728,7 @@ void blocked_record_reset(Blocked* k, cudaStream_t s) { GPR_CUDA(cudaMemsetAsync
 
 template <typename T>
 void blocked_record_step(Blocked* k, const gpr_graph* g, const T* c_in, const float* x_in, float* x_out, T* c_out,
-                         StepParams* prm, double* log_row, int32_t it, cudaStream_t s) {
+                         const float* inv_deg, StepParams* prm, double* log_row, int32_t it, cudaStream_t s) {
   // every CTA of a launch takes units until one fetch fails: a launch moves
   // a counter by exactly (units + grid)
   const unsigned int ex = (unsigned int)((int64_t)it * (k->n_xu + k->xgrid));
@@ -737,13 +737,14 @@ void blocked_record_step(Blocked* k, const gpr_graph* g, const T* c_in, const fl
       c_in, g->n, k->sb_bits, k->ubits, k->B, k->xseg, k->xu, k->n_xu, k->src_lo, k->vals, k->ctr, ex);
   bk_accum_kernel<T><<<k->agrid, kBkThreads, accum_smem(k->w_bits), s>>>(
       k->vals, k->dst_lo, g->n, k->w_bits, k->ubits, k->au, k->n_au, k->ctr, ea, k->acc_g, k->bin_arrive, x_in,
-      g->plan.inv_deg, x_out, c_out, prm, k->partials, k->B, log_row);
+      inv_deg, x_out, c_out, prm, k->partials, k->B, log_row);
   GPR_CUDA(cudaGetLastError());
 }
 
 template void blocked_record_step<float>(Blocked*, const gpr_graph*, const float*, const float*, float*, float*,
-                                         StepParams*, double*, int32_t, cudaStream_t);
+                                         const float*, StepParams*, double*, int32_t, cudaStream_t);
 template void blocked_record_step<__nv_bfloat16>(Blocked*, const gpr_graph*, const __nv_bfloat16*, const float*,
-                                                 float*, __nv_bfloat16*, StepParams*, double*, int32_t, cudaStream_t);
+                                                 float*, __nv_bfloat16*, const float*, StepParams*, double*, int32_t,
+                                                 cudaStream_t);
 
 }  // namespace gpr

@@ -53,9 +53,9 @@ void blocked_free(Blocked* k, cudaStream_t s);
 void blocked_record_reset(Blocked* k, cudaStream_t s);
 
 // Records step `it` (0-based within the run): y from c_in, finish into
-// x_out / c_out, fold into prm and log_row.
+// x_out / c_out = x_out * inv_deg, fold into prm and log_row.
 template <typename T>
 void blocked_record_step(Blocked* k, const gpr_graph* g, const T* c_in, const float* x_in, float* x_out, T* c_out,
-                         StepParams* prm, double* log_row, int32_t it, cudaStream_t s);
+                         const float* inv_deg, StepParams* prm, double* log_row, int32_t it, cudaStream_t s);
 
 }  // namespace gpr

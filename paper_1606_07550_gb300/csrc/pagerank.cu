@@ -450,7 +450,8 @@ static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, int 
     blocked_record_reset(w->blk, s);
     for (int32_t it = 0; it < iters; ++it) {
       const int a = it & 1, b = a ^ 1;
-      blocked_record_step<T>(w->blk, g, c[a], x[a], x[b], c[b], w->prm, w->log + 3 * (int64_t)(it + 1), it, s);
+      blocked_record_step<T>(w->blk, g, c[a], x[a], x[b], c[b], P.inv_deg, w->prm, w->log + 3 * (int64_t)(it + 1), it,
+                             s);
     }
     return;
   }
@@ -939,6 +940,30 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
     }
+    // the blocked schedule (unit weights: c = x) when asked for, or on a large
+    // graph; vectors are L1-normalised between products, so every row sum is
+    // at most 1, within the fixed-point range of the blocked sums
+    Choice bc{kSchedBlocked, 15, 14, default_unit(g)};
+    if (w->tuned && w->choice.sched == kSchedBlocked) bc = w->choice;
+    bool blocked = (flags & GPR_SPMV_BLOCKED) || (!(flags & GPR_SPMV_PULL) && g->m >= kTuneMinEdges);
+    blocked = blocked && blocked_eligible(g, bc.sb, bc.wb) && (kind == 0 || blocked_eligible(t, bc.sb, bc.wb));
+    if (blocked) {
+      ensure_layout(g, w, bc, s);
+      blocked_record_reset(w->blk, s);
+      if (kind == 1) {
+        ensure_layout(t, wt, bc, s);
+        blocked_record_reset(wt->blk, s);
+      }
+    }
+    int32_t it_g = 0, it_t = 0;  // steps since the reset, per layout
+    auto product = [&](gpr_graph* gg, PagerankWork* ww, const float* c_in, const float* x_in, float* x_out,
+                       float* c_out, double* log_row) {
+      if (blocked)
+        blocked_record_step<float>(ww->blk, gg, c_in, x_in, x_out, c_out, w->ones, w->prm, log_row,
+                                   gg == g ? it_g++ : it_t++, s);
+      else
+        launch_pull_step(gg, ww, s, c_in, x_in, x_out, c_out, w->ones, w->prm, log_row);
+    };
     ensure_log(w, 2 * iters + 2, s);
     const StepParams hp{0.f, 0.f, 1.0, (double)n};  // d = 1: no teleport, coefA = 1 / mass
     GPR_CUDA(cudaMemcpyAsync(w->prm, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
@@ -954,8 +979,7 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
     if (kind == 0) {
       for (int32_t it = 0; it < iters; ++it) {
         const int a = it & 1, b = a ^ 1;
-        launch_pull_step(g, w, s, (const float*)w->c[a], w->x[a], w->x[b], (float*)w->c[b], w->ones, w->prm,
-                         w->log + 3 * (int64_t)(it + 1));
+        product(g, w, (const float*)w->c[a], w->x[a], w->x[b], (float*)w->c[b], w->log + 3 * (int64_t)(it + 1));
       }
       write_l2_output(g, w, w->x[iters & 1], out_x, flags, s);
     } else {
@@ -963,10 +987,9 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
       // block, so each fold hands 1 / ||x||_1 to the other product
       for (int32_t it = 0; it < iters; ++it) {
         const int a = it & 1, b = a ^ 1;
-        launch_pull_step(g, w, s, (const float*)wt->c[0], w->x[a], w->x[b], (float*)w->c[0], w->ones, w->prm,
-                         w->log + 3 * (int64_t)(2 * it + 1));
-        launch_pull_step(t, wt, s, (const float*)w->c[0], wt->x[a], wt->x[b], (float*)wt->c[0], w->ones, w->prm,
-                         w->log + 3 * (int64_t)(2 * it + 2));
+        product(g, w, (const float*)wt->c[0], w->x[a], w->x[b], (float*)w->c[0], w->log + 3 * (int64_t)(2 * it + 1));
+        product(t, wt, (const float*)w->c[0], wt->x[a], wt->x[b], (float*)wt->c[0],
+                w->log + 3 * (int64_t)(2 * it + 2));
       }
       write_l2_output(g, w, wt->x[iters & 1], out_hub, flags, s);
       write_l2_output(g, w, w->x[iters & 1], out_x, flags, s);

@@ -25,22 +25,57 @@ def torch():
     return torch
 
 
-def gpu_hits(torch, g, iters):
+def gpu_hits(torch, g, iters, spmv="auto"):
     hub = torch.empty(g.n, device="cuda")
     auth = torch.empty(g.n, device="cuda")
-    gpr.hits(g, hub, auth, iters=iters)
+    gpr.hits(g, hub, auth, iters=iters, spmv=spmv)
     return hub.cpu().numpy().astype(np.float64), auth.cpu().numpy().astype(np.float64)
 
 
-def gpu_eig(torch, g, iters):
+def gpu_eig(torch, g, iters, spmv="auto"):
     x = torch.empty(g.n, device="cuda")
-    gpr.eigen_centrality(g, x, iters=iters)
+    gpr.eigen_centrality(g, x, iters=iters, spmv=spmv)
     return x.cpu().numpy().astype(np.float64)
 
 
 def close(x, ref):
     assert np.linalg.norm(x - ref) <= TOL, np.linalg.norm(x - ref)
     assert (x[ref == 0] == 0).all()
+
+
+@pytest.mark.parametrize("spmv", ["pull", "blocked"])
+@pytest.mark.parametrize("n,m_raw,seed", [(257, 3000, 12), (40_000, 600_000, 13)])
+def test_both_schedules_match_oracle(torch, spmv, n, m_raw, seed):
+    # the blocked schedule carries unit weights and L1-normalised vectors
+    # through fixed-point sums; the pull schedule gathers FP32
+    src, dst = gen.rmat_coo(n, m_raw, seed=seed)
+    g = gpr.graph_build(src, dst, n)
+    ref = oracle.build_csc(n, src, dst)
+    for iters in (1, 7, 30):
+        hub, auth = gpu_hits(torch, g, iters, spmv)
+        rh, ra = oracle.hits(ref, iters)
+        close(hub, rh)
+        close(auth, ra)
+        close(gpu_eig(torch, g, iters, spmv), oracle.eigen_centrality(ref, iters))
+    # the schedules agree with each other too, and with PageRank run between them
+    x = torch.empty(n, device="cuda")
+    gpr.pagerank(g, x, iters=20, spmv=spmv)
+    assert l1(x.cpu().numpy(), oracle.pagerank(ref, 0.85, 20)) <= 1e-5
+    hub2, auth2 = gpu_hits(torch, g, 30, spmv)
+    rh, ra = oracle.hits(ref, 30)
+    close(hub2, rh)
+    close(auth2, ra)
+    g.free()
+
+
+def test_conflicting_schedule_flags(torch):
+    g = gpr.graph_build(np.array([0, 1], np.int32), np.array([1, 2], np.int32), 3)
+    x = torch.empty(3, device="cuda")
+    from paper_1606_07550_gb300 import SPMV_BLOCKED, SPMV_PULL, lib
+    st = lib().eigen_centrality(g.handle, 3, x.data_ptr(), SPMV_PULL | SPMV_BLOCKED,
+                                torch.cuda.current_stream().cuda_stream)
+    assert st == gpr.EINVAL
+    g.free()
 
 
 @pytest.mark.parametrize("n,m_raw,seed", [(1, 5, 0), (2, 1, 1), (257, 3000, 2), (4099, 40_000, 3),
