@@ -83,6 +83,20 @@ def test_wcc_giant_choice_and_ties(torch):
     assert lab[29_500] == 1 and lab[25_000] == 1 and lab[0] == 0 and lab[29_999] == 29_999 and k == 1001
 
 
+def test_wcc_edge_into_a_node_outside_the_giant(torch):
+    # node 2's first two in-neighbours (0, 1) have no in-edges, so sampling
+    # leaves {0, 1, 2} outside the giant cycle 5..19; the only tie is 10 -> 2,
+    # an edge whose source is inside the giant: the rows-outside pass links it
+    n = 20
+    cyc = np.arange(5, 20)
+    src = np.concatenate([cyc, [0, 1, 10]]).astype(np.int32)
+    dst = np.concatenate([np.roll(cyc, -1), [2, 2, 2]]).astype(np.int32)
+    g = gpr.graph_build(src, dst, n)
+    lab, k = gpu_wcc(torch, g)
+    ref, kr = oracle.wcc(oracle.build_csc(n, src, dst))
+    assert k == kr == 3 and (lab == ref).all()
+
+
 def test_save_load_round_trip(torch, tmp_path):
     n = 40_000
     src, dst = gen.rmat_coo(n, 700_000, seed=12)
