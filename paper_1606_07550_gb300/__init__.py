@@ -34,6 +34,12 @@ WARM_START = 0x40
 _SPMV = {"auto": 0, "pull": SPMV_PULL, "blocked": SPMV_BLOCKED}
 
 
+def _spmv_flag(spmv: str) -> int:
+    if spmv not in _SPMV:
+        raise ValueError(f"spmv must be one of {sorted(_SPMV)}, not {spmv!r}")
+    return _SPMV[spmv]
+
+
 def sources():
     return sorted(os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".cu"))
 
@@ -305,7 +311,7 @@ def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int =
     warm_start: start from the vector `out` holds instead of uniform."""
     po, host = _ptr_and_flag(out)
     st = Stats() if stats else None
-    flags = (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv] | (WARM_START if warm_start else 0)
+    flags = (PTR_HOST if host else PTR_DEVICE) | _spmv_flag(spmv) | (WARM_START if warm_start else 0)
     _check(lib().pagerank(g.handle, damping, iters, dtype, flags, po,
                           ctypes.byref(st) if st is not None else None, _stream_ptr(stream)))
     return st
@@ -314,19 +320,19 @@ def pagerank(g: Graph, out, damping: float = 0.85, iters: int = 50, dtype: int =
 def hits(g: Graph, hub_out, auth_out, iters: int = 50, stream=None, spmv: str = "auto"):
     """HITS hubs and authorities (unit L2 norm, by node id) into two CUDA
     tensors, or host arrays / CPU tensors.  spmv: "auto", "pull" or "blocked"."""
+    sp = _spmv_flag(spmv)
     ph, host = _ptr_and_flag(hub_out)
     pa, host2 = _ptr_and_flag(auth_out)
     if host != host2:
         raise ValueError("hub_out and auth_out must both be on the device or both on the host")
-    _check(lib().hits(g.handle, iters, ph, pa, (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv],
-                      _stream_ptr(stream)))
+    _check(lib().hits(g.handle, iters, ph, pa, (PTR_HOST if host else PTR_DEVICE) | sp, _stream_ptr(stream)))
 
 
 def eigen_centrality(g: Graph, out, iters: int = 50, stream=None, spmv: str = "auto"):
     """Eigenvector centrality (unit L2 norm, by node id) into `out`."""
+    sp = _spmv_flag(spmv)
     po, host = _ptr_and_flag(out)
-    _check(lib().eigen_centrality(g.handle, iters, po, (PTR_HOST if host else PTR_DEVICE) | _SPMV[spmv],
-                                  _stream_ptr(stream)))
+    _check(lib().eigen_centrality(g.handle, iters, po, (PTR_HOST if host else PTR_DEVICE) | sp, _stream_ptr(stream)))
 
 
 def wcc(g: Graph, out, stream=None) -> int:
