@@ -173,6 +173,8 @@ typedef struct {
   double ms_per_step;       /* the winner's device time per step */
   double pull_ms_per_step;  /* the pull schedule's */
   int32_t candidates;       /* schedules timed */
+  int32_t dense_sources;    /* blocked: sources (highest out-degree first) whose edges read their
+                               contribution directly instead of through the expand phase (else 0) */
 } gpr_tune_result;
 
 gpr_status pagerank_tune(const gpr_graph* g, gpr_dtype dt, int32_t trial_steps, gpr_tune_result* out,

@@ -118,7 +118,8 @@ class TargetStats(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("sb_bits", ctypes.c_int32), ("w_bits", ctypes.c_int32),
                 ("unit_edges", ctypes.c_int64), ("ms_per_step", ctypes.c_double),
-                ("pull_ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32)]
+                ("pull_ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("dense_sources", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

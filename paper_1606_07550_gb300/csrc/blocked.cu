@@ -1,33 +1,47 @@
 // Blocked schedule of the PageRank step (section 4 Table "snap_methods"):
 // the same step as the pull kernels of pagerank.cu, with the per-edge random
-// gather c[u] replaced by two streaming phases.
+// gather c[u] replaced by streaming phases.
 //
 // Sources are cut into blocks of 2^sb_bits relabelled ids and rows
-// (destinations) into bins of 2^w_bits.  The edges are stored once in
-// bin-major order: bin b, then source block s, then (row, source) as in the
-// CSC; the edges of one (b, s) pair form segment (b, s).  Per step:
-//   expand      for each source block s, c[block s] is copied into shared
-//               memory and every edge of its segments gets vals[e] = c[u],
-//               reading 16-bit local source ids: a read stream and a write
-//               stream, with the random reads served by shared memory;
-//   accumulate  for each bin, vals and the 16-bit local rows of its edges are
-//               streamed and added into one accumulator per row in shared
-//               memory; the bin's rows are then finished (x', c', partial
-//               sums) exactly as in the pull schedule.
+// (destinations) into bins of 2^w_bits.  Relabelled ids run by descending
+// out-degree, so the first sources hold a large share of the edges (at R-MAT
+// scale 25 the first 2^18 of 2^25 sources hold about 60%).  The first
+// n_dense sources (whole blocks, n_dense < 2^(32 - w_bits)) are "dense".  The
+// edges are stored once in bin-major order: in bin b, first the edges of the
+// dense sources, ordered by source then row, each as one packed 32-bit word
+// source | row << (32 - w_bits); then, for each other source block s, the
+// edges of segment (b, s) in CSC order (row, then source) as 16-bit local
+// source and row ids.  The contributions c are held as 32-bit codes (below).
+// Per step:
+//   expand      for each non-dense source block s, its codes are copied into
+//               shared memory and every edge of its segments gets
+//               vals[e] = code[u], reading 16-bit local source ids: a read
+//               stream and a write stream, with the random reads served by
+//               shared memory;
+//   accumulate  for each bin, the packed words of its dense-source edges are
+//               streamed and each edge's code read straight from c (the dense
+//               sources' codes, at most 1 MB, stay in cache, and a run of
+//               edges shares few consecutive sources), then the codes and
+//               16-bit rows of its other edges are streamed; all are added
+//               into one accumulator per row in shared memory; the bin's rows
+//               are then finished (x', c', partial sums) as in the pull
+//               schedule.
 // Sums are exact integers.  With a unit of 2^-U (U = min(60, 28 +
 // ceil(log2 n))), contribution c is the integer q = floor(c * 2^U), and each
 // row's accumulator holds the exact 64-bit sum of its q, so y[v] does not
-// depend on the order of the additions and runs are bitwise reproducible
-// however units are scheduled.  The expand phase stores a 32-bit code per
-// edge: q itself when q < 2^31 (c < 2^(31-U), about 8 / n: nearly every
+// depend on the order of the additions, nor on which sources are dense: runs
+// are bitwise reproducible however units are scheduled.  The 32-bit code of
+// c is q itself when q < 2^31 (c < 2^(31-U), about 8 / n: nearly every
 // contribution), else the bits of c with the top bit set, converted again
 // where it is added.  Truncation costs less than 2^-U per edge (at most
 // m * 2^-U in L1, 1.2e-7 for 2^25 nodes and 2^30 edges); y[v] is rounded
-// to the nearest float.
+// to the nearest float.  With BF16 storage c is rounded to BF16 before it is
+// coded.
 //
-// Streamed bytes per edge: 2 (source id) + 4 (code written) in expand,
-// 4 (code) + 2 (row id) in accumulate: 12, for FP32 and BF16 storage of c
-// alike (c itself is read once per unit).
+// Streamed bytes per edge: 4 (packed word) for a dense source's edge;
+// 2 (source id) + 4 (code written) in expand and 4 (code) + 2 (row id) in
+// accumulate, 12, for the others.  The dense sources' codes are read from
+// cache once per bin and source; the others' once per expand unit.
 // Long rows need no special case: runs of one row are summed in registers
 // before they reach shared memory (a warp step inside one row is added
 // once), and a bin with many edges is cut into units whose sums meet in a
@@ -93,65 +107,80 @@ __device__ __forceinline__ float from_fixed(unsigned long long a, int U) {
 // the high word the high half plus the carry out of the low word, seen in
 // the value the low atomic returns.  Whatever the order of the additions,
 // the number of carries is floor(sum of low halves / 2^32), so hi:lo ends
-// as the exact sum.  The high atomic is skipped when it would add 0 (every
-// code below 2^31 without a carry).
+// as the exact sum.  (A 64-bit shared-memory atomic measured about twice as
+// slow on GB300: four times the shared-memory wavefronts.)
 // qh plus the carry out of old + ql.
 __device__ __forceinline__ uint32_t carry_into(uint32_t old, uint32_t ql, uint32_t qh) {
   uint32_t up;
   asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, 0;\n\t}" : "=r"(up) : "r"(old), "r"(ql), "r"(qh));
   return up;
 }
-// Predicated shared-memory additions at 32-bit shared addresses (no branch):
-// the low-word add returns the old value; the high-word add happens only
-// for a non-zero amount.
-__device__ __forceinline__ uint32_t atom_add_if(uint32_t addr, uint32_t v, bool on) {
-  uint32_t old = 0;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t@p atom.shared.add.u32 %0, [%1], %2;\n\t}"
-      : "+r"(old)
-      : "r"(addr), "r"(v), "r"((uint32_t)on)
-      : "memory");
+__device__ __forceinline__ uint32_t atom_add(uint32_t addr, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v) : "memory");
   return old;
 }
+// Shared-memory addition of a non-zero amount (predicated: no branch).
 __device__ __forceinline__ void red_add_nonzero(uint32_t addr, uint32_t v) {
   asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr),
                "r"(v)
                : "memory");
 }
 
-__device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int32_t d, uint32_t ql, uint32_t qh) {
-  const uint32_t up = carry_into(atomicAdd(lo + d, ql), ql, qh);
-  if (up) atomicAdd(hi + d, up);
-}
-
 // ---- layout construction --------------------------------------------------
 
-// key = row-in-bin | source-in-block | (b * S + s), one per CSC edge, in CSC
+// The sort index of an edge: bin b, then its dense source u (u < n_dense),
+// or n_dense + (its source block - D); kb_bits bits per bin.
+__device__ __forceinline__ uint64_t bk_index(uint64_t b, uint32_t u, int sb_bits, int32_t n_dense, int32_t D,
+                                             int kb_bits) {
+  const uint64_t j = u < (uint32_t)n_dense ? (uint64_t)u : (uint64_t)n_dense + ((u >> sb_bits) - (uint32_t)D);
+  return (b << kb_bits) | j;
+}
+// The segment (b, s) of a sort index.
+__device__ __forceinline__ int64_t bk_segment(uint64_t kidx, int sb_bits, int32_t n_dense, int32_t D, int kb_bits,
+                                              int32_t S) {
+  const int64_t b = (int64_t)(kidx >> kb_bits);
+  const uint64_t j = kidx & ((1ull << kb_bits) - 1);
+  const int64_t s = j < (uint64_t)n_dense ? (int64_t)(j >> sb_bits) : (int64_t)D + (int64_t)(j - (uint64_t)n_dense);
+  return b * S + s;
+}
+
+// key = row-in-bin | source-in-block | sort index, one per CSC edge, in CSC
 // order.
 __global__ void bk_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
-                               int sb_bits, int w_bits, int kbits, int32_t S, uint64_t* __restrict__ keys) {
+                               int sb_bits, int w_bits, int kbits, int32_t n_dense, int32_t D, int kb_bits,
+                               uint64_t* __restrict__ keys) {
   const uint32_t sb_mask = (1u << sb_bits) - 1;
   for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
     const uint64_t b = (uint64_t)(p >> w_bits);
     const uint64_t hi = (uint64_t)(p & ((1 << w_bits) - 1)) << (sb_bits + kbits);
     const uint32_t u = (uint32_t)row_idx[e];
-    keys[e] = hi | ((uint64_t)(u & sb_mask) << kbits) | (b * (uint64_t)S + (u >> sb_bits));
+    keys[e] = hi | ((uint64_t)(u & sb_mask) << kbits) | bk_index(b, u, sb_bits, n_dense, D, kb_bits);
   });
 }
 
-// From the keys sorted (stably) on their low kbits bits: the local ids of
-// every edge in bin-major order, and seg[k] = first edge of segment k
-// (seg[nseg] = m).
+// From the keys sorted (stably) on their low kbits bits, in bin-major edge
+// order: the packed word of every dense-source edge, the local ids of every
+// other edge, and seg[k] = first edge of segment k (seg[nseg] = m).
 __global__ void bk_extract_kernel(const uint64_t* __restrict__ keys, int64_t m, int sb_bits, int kbits,
-                                  int64_t nseg, uint16_t* __restrict__ src_lo, uint16_t* __restrict__ dst_lo,
-                                  int32_t* __restrict__ seg) {
+                                  int32_t n_dense, int32_t D, int kb_bits, int dense_bits, int32_t S, int64_t nseg,
+                                  uint16_t* __restrict__ src_lo, uint16_t* __restrict__ dst_lo,
+                                  uint32_t* __restrict__ vals, int32_t* __restrict__ seg) {
   const uint64_t kmask = (1ull << kbits) - 1;
+  const uint64_t jmask = (1ull << kb_bits) - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[i];
-    const int64_t k = (int64_t)(key & kmask);
-    src_lo[i] = (uint16_t)((key >> kbits) & ((1u << sb_bits) - 1));
-    dst_lo[i] = (uint16_t)(key >> (kbits + sb_bits));
-    const int64_t first = i > 0 ? (int64_t)(keys[i - 1] & kmask) + 1 : 0;
+    const uint64_t kidx = key & kmask;
+    const uint64_t j = kidx & jmask;
+    const uint32_t r = (uint32_t)(key >> (kbits + sb_bits));
+    if (j < (uint64_t)n_dense) {
+      vals[i] = (uint32_t)j | (r << dense_bits);
+    } else {
+      src_lo[i] = (uint16_t)((key >> kbits) & ((1u << sb_bits) - 1));
+      dst_lo[i] = (uint16_t)r;
+    }
+    const int64_t k = bk_segment(kidx, sb_bits, n_dense, D, kb_bits, S);
+    const int64_t first = i > 0 ? bk_segment(keys[i - 1] & kmask, sb_bits, n_dense, D, kb_bits, S) + 1 : 0;
     for (int64_t kk = first; kk <= k; ++kk) seg[kk] = (int32_t)i;
     if (i == m - 1)
       for (int64_t kk = k + 1; kk <= nseg; ++kk) seg[kk] = (int32_t)m;
@@ -197,12 +226,14 @@ constexpr size_t kExpandStageBytes = (size_t)(kBkThreads / 32) * 128 * 8;
 constexpr size_t kAccumSlotBytes = kChunk * 4 + kChunk * 2;
 constexpr size_t kAccumStageBytes = (size_t)(kBkThreads / 32) * 2 * kAccumSlotBytes;
 
-__device__ __forceinline__ float to_f32(float v) { return v; }
-__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+// Contributions as stored: FP32, or rounded to BF16 (nearest, ties to even).
+__device__ __forceinline__ float round_store(float v, float*) { return v; }
+__device__ __forceinline__ float round_store(float v, __nv_bfloat16*) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
 
-template <typename T>
 __global__ void __launch_bounds__(kBkThreads, 1) bk_expand_kernel(
-    const T* __restrict__ c_in, int32_t n, int sb_bits, int U, int32_t B, const int2* __restrict__ xseg,
+    const uint32_t* __restrict__ c_in, int32_t n, int sb_bits, int32_t B, const int2* __restrict__ xseg,
     const ExpandUnit* __restrict__ units, int32_t nunits, const uint16_t* __restrict__ src_lo,
     uint32_t* __restrict__ vals, unsigned int* __restrict__ ctr, unsigned int epoch) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -224,30 +255,23 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_expand_kernel(
     const int32_t u = s_unit;
     if (u < 0 || u >= nunits) return;
     const ExpandUnit eu = units[u];
-    // the block's contributions, as codes
+    // the block's codes: 16-byte loads, four in flight per thread
     const int64_t v0 = (int64_t)eu.s << sb_bits;
     const int32_t nb = (int32_t)(n - v0 < SB ? n - v0 : SB);
     {
-      // 16-byte loads, four in flight per thread, then the conversions
-      constexpr int kPer = 16 / sizeof(T);
-      const int32_t nvec = nb / kPer;
+      const int32_t nvec = nb / 4;
       const uint4* src = reinterpret_cast<const uint4*>(c_in + v0);
+      uint4* dst = reinterpret_cast<uint4*>(s_code);
       for (int32_t i0 = tid; i0 < nvec; i0 += 4 * blockDim.x) {
         uint4 r[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (i0 + k * (int32_t)blockDim.x < nvec) r[k] = __ldg(src + i0 + k * blockDim.x);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int32_t i = i0 + k * blockDim.x;
-          if (i < nvec) {
-            const T* e = reinterpret_cast<const T*>(&r[k]);
-#pragma unroll
-            for (int j = 0; j < kPer; ++j) s_code[i * kPer + j] = code_of(to_f32(e[j]), U);
-          }
-        }
+        for (int k = 0; k < 4; ++k)
+          if (i0 + k * (int32_t)blockDim.x < nvec) dst[i0 + k * blockDim.x] = r[k];
       }
-      for (int32_t i = nvec * kPer + tid; i < nb; i += blockDim.x) s_code[i] = code_of(to_f32(c_in[v0 + i]), U);
+      for (int32_t i = nvec * 4 + tid; i < nb; i += blockDim.x) s_code[i] = __ldg(c_in + v0 + i);
     }
     // clipped segment ranges and the prefix of their chunk counts
     const int nseg = eu.b_hi - eu.b_lo;
@@ -346,22 +370,60 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_expand_kernel(
 
 // ---- accumulate -----------------------------------------------------------
 
+// Values of 8 codes: codes below 2^31 are the value; the rest are converted
+// (once any lane of the warp holds one).
+__device__ __forceinline__ void codes_to_values(const uint32_t (&w)[8], int U, unsigned long long (&q)[8]) {
+  const uint32_t any = (w[0] | w[1] | w[2] | w[3]) | (w[4] | w[5] | w[6] | w[7]);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) q[j] = w[j];
+  if (__any_sync(0xffffffffu, any >> 31)) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) q[j] = value_of(w[j], U);
+  }
+}
+
+// Adds q[j] into row d[j] of the two-word accumulators (low words at a_lo,
+// high words hw bytes above): the low words with independent atomics, then
+// the high halves and carries, issued only when some lane of the warp has
+// one (most steps carry nothing: codes are far below 2^32).
+__device__ __forceinline__ void acc_add8(uint32_t a_lo, uint32_t hw, const uint32_t (&d)[8],
+                                         const unsigned long long (&q)[8]) {
+  uint32_t up[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) up[j] = atom_add(a_lo + 4u * d[j], (uint32_t)q[j]);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) up[j] = carry_into(up[j], (uint32_t)q[j], (uint32_t)(q[j] >> 32));
+  const uint32_t any = (up[0] | up[1] | up[2] | up[3]) | (up[4] | up[5] | up[6] | up[7]);
+  if (__any_sync(0xffffffffu, any != 0u)) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red_add_nonzero(a_lo + hw + 4u * d[j], up[j]);
+  }
+}
+
+// Edge index of slot j of this lane in a 256-edge chunk at `base`: lane l
+// holds edges 4l..4l+3 and 128+4l..128+4l+3.
+__device__ __forceinline__ int32_t chunk_edge(int32_t base, int lane, int j) {
+  return base + (j < 4 ? 4 * lane + j : 128 + 4 * lane + j - 4);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
-    const uint32_t* __restrict__ vals, const uint16_t* __restrict__ dst_lo, int32_t n, int w_bits, int U,
-    const AccumUnit* __restrict__ units, int32_t nunits, unsigned int* __restrict__ ctr, unsigned int epoch,
-    unsigned long long* __restrict__ acc_g, unsigned int* __restrict__ bin_arrive, const float* __restrict__ x_in,
-    const float* __restrict__ inv_deg, float* __restrict__ x_out, T* __restrict__ c_out, StepParams* __restrict__ prm,
+    const uint32_t* __restrict__ vals, const uint16_t* __restrict__ dst_lo, const uint32_t* __restrict__ c_in,
+    int dense_bits, int32_t n, int w_bits, int U, const AccumUnit* __restrict__ units, int32_t nunits,
+    unsigned int* __restrict__ ctr, unsigned int epoch, unsigned long long* __restrict__ acc_g,
+    unsigned int* __restrict__ bin_arrive, const float* __restrict__ x_in, const float* __restrict__ inv_deg,
+    float* __restrict__ x_out, uint32_t* __restrict__ c_out, StepParams* __restrict__ prm,
     double* __restrict__ partials, int32_t nbins, double* __restrict__ log_row) {
   extern __shared__ __align__(16) uint32_t s_acc32[];
   __shared__ int32_t s_unit;
   __shared__ int s_flag;
   const int32_t W = 1 << w_bits;
-  uint32_t* s_lo = s_acc32;
-  uint32_t* s_hi = s_acc32 + W;
-  const uint32_t a_lo = (uint32_t)__cvta_generic_to_shared(s_lo), a_hi = (uint32_t)__cvta_generic_to_shared(s_hi);
+  uint32_t* s_lo = s_acc32;      // low words of the row accumulators
+  uint32_t* s_hi = s_acc32 + W;  // high words
+  const uint32_t a_lo = (uint32_t)__cvta_generic_to_shared(s_lo), hw = 4u * (uint32_t)W;
+  const uint32_t dmask = (1u << dense_bits) - 1;  // dense_bits = 32 - w_bits <= 28
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  // this warp's two staging slots: 256 codes, then 256 row ids
+  // this warp's two staging slots: 256 codes or packed words, then 256 row ids
   unsigned char* w_stage = reinterpret_cast<unsigned char*>(s_acc32 + 2 * W) + (size_t)warp * 2 * kAccumSlotBytes;
   for (;;) {
     __syncthreads();
@@ -374,99 +436,128 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
     const int32_t nv = min(W, n - v0);
     for (int32_t i = tid; i < nv; i += blockDim.x) s_lo[i] = s_hi[i] = 0u;
     __syncthreads();
-    // lane l handles edges 4l..4l+3 and 128+4l..128+4l+3 of each 256-edge
-    // chunk; it copies exactly those codes and row ids into its slot while
-    // the previous chunk is added
-    auto stage = [&](int slot, int32_t b) {
-      unsigned char* st = w_stage + slot * kAccumSlotBytes;
-      cp_async16(st + 16 * lane, vals + b + 4 * lane);
-      cp_async16(st + 512 + 16 * lane, vals + b + 128 + 4 * lane);
-      cp_async8(st + 1024 + 8 * lane, dst_lo + b + 4 * lane);
-      cp_async8(st + 1280 + 8 * lane, dst_lo + b + 128 + 4 * lane);
-    };
-    const int32_t first = (un.lo & ~(kChunk - 1)) + warp * kChunk;
-    if (first < un.hi) stage(0, first);
-    cp_async_commit();
-    int slot = 0;
-    for (int32_t base = first; base < un.hi; base += nwarps * kChunk, slot ^= 1) {
-      if (base + nwarps * kChunk < un.hi) stage(slot ^ 1, base + nwarps * kChunk);
+    // Lane l handles edges 4l..4l+3 and 128+4l..128+4l+3 of each 256-edge
+    // chunk; it copies exactly those words (and row ids) into its slot while
+    // the previous chunk is added.  An edge outside the unit's range (in a
+    // chunk at either end) adds 0 to row 0.
+    //
+    // Dense sources, edges [lo, mid): each word packs the source and the row;
+    // the source's code is read from c_in (at most 1 MB of codes, kept in
+    // cache: a chunk's edges come from few, consecutive sources).
+    {
+      auto stage = [&](int slot, int32_t b) {
+        unsigned char* st = w_stage + slot * kAccumSlotBytes;
+        cp_async16(st + 16 * lane, vals + b + 4 * lane);
+        cp_async16(st + 512 + 16 * lane, vals + b + 128 + 4 * lane);
+      };
+      const int32_t first = (un.lo & ~(kChunk - 1)) + warp * kChunk;
+      if (first < un.mid) stage(0, first);
       cp_async_commit();
-      cp_async_wait<1>();  // this lane's copies for the current chunk are in
-      const unsigned char* st = w_stage + slot * kAccumSlotBytes;
-      const uint4 wa = *reinterpret_cast<const uint4*>(st + 16 * lane);
-      const uint4 wb = *reinterpret_cast<const uint4*>(st + 512 + 16 * lane);
-      const uint2 ra = *reinterpret_cast<const uint2*>(st + 1024 + 8 * lane);
-      const uint2 rb = *reinterpret_cast<const uint2*>(st + 1280 + 8 * lane);
-      uint32_t w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-      int32_t d[8] = {(int32_t)(ra.x & 0xFFFFu), (int32_t)(ra.x >> 16), (int32_t)(ra.y & 0xFFFFu), (int32_t)(ra.y >> 16),
-                      (int32_t)(rb.x & 0xFFFFu), (int32_t)(rb.x >> 16), (int32_t)(rb.y & 0xFFFFu), (int32_t)(rb.y >> 16)};
-      if (base < un.lo || base + kChunk > un.hi) {  // a boundary chunk: edges outside the unit are not added here
+      int slot = 0;
+      for (int32_t base = first; base < un.mid; base += nwarps * kChunk, slot ^= 1) {
+        if (base + nwarps * kChunk < un.mid) stage(slot ^ 1, base + nwarps * kChunk);
+        cp_async_commit();
+        cp_async_wait<1>();
+        const unsigned char* st = w_stage + slot * kAccumSlotBytes;
+        const uint4 wa = *reinterpret_cast<const uint4*>(st + 16 * lane);
+        const uint4 wb = *reinterpret_cast<const uint4*>(st + 512 + 16 * lane);
+        uint32_t w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        uint32_t offm = 0;  // edges outside the range: word 0 (source 0, row 0), value 0
+        if (base < un.lo || base + kChunk > un.mid) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int32_t e = base + (j < 4 ? 4 * lane + j : 128 + 4 * lane + j - 4);
-          if (e < un.lo || e >= un.hi) {
-            w[j] = 0u;
-            d[j] = -1;
+          for (int j = 0; j < 8; ++j) {
+            const int32_t e = chunk_edge(base, lane, j);
+            if (e < un.lo || e >= un.mid) {
+              w[j] = 0u;
+              offm |= 1u << j;
+            }
           }
         }
-      }
-      // values: codes below 2^31 are the value; the rest are converted
-      unsigned long long q[8];
-      bool big = false;
+        uint32_t cw[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        q[j] = w[j];
-        big = big || (w[j] >> 31);
-      }
-      if (__any_sync(0xffffffffu, big)) {
+        for (int j = 0; j < 8; ++j) cw[j] = __ldg(c_in + (w[j] & dmask));
+        unsigned long long q[8];
+        codes_to_values(cw, U, q);
+        if (offm) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) q[j] = value_of(w[j], U);
-      }
-      // runs of equal rows within each group of 4 consecutive edges are
-      // folded into their first edge (backward, so a head holds its whole
-      // run: consecutive edges of one row would otherwise meet in one
-      // atomic instruction); skipped when the warp step has no such pair
-      bool dup = false;
+          for (int j = 0; j < 8; ++j)
+            if ((offm >> j) & 1u) q[j] = 0ull;
+        }
+        uint32_t d[8];
 #pragma unroll
-      for (int j = 0; j < 7; ++j)
-        if (j != 3) dup = dup || (d[j] >= 0 && d[j] == d[j + 1]);
-      bool whole = false;
-      int32_t c0 = -1;
-      if (__any_sync(0xffffffffu, dup)) {
+        for (int j = 0; j < 8; ++j) d[j] = w[j] >> dense_bits;
+        acc_add8(a_lo, hw, d, q);
+      }
+      cp_async_wait<0>();
+    }
+    // Other sources, edges [mid, hi): codes written by the expand phase and
+    // 16-bit rows.
+    {
+      auto stage = [&](int slot, int32_t b) {
+        unsigned char* st = w_stage + slot * kAccumSlotBytes;
+        cp_async16(st + 16 * lane, vals + b + 4 * lane);
+        cp_async16(st + 512 + 16 * lane, vals + b + 128 + 4 * lane);
+        cp_async8(st + 1024 + 8 * lane, dst_lo + b + 4 * lane);
+        cp_async8(st + 1280 + 8 * lane, dst_lo + b + 128 + 4 * lane);
+      };
+      const int32_t first = (un.mid & ~(kChunk - 1)) + warp * kChunk;
+      if (first < un.hi) stage(0, first);
+      cp_async_commit();
+      int slot = 0;
+      for (int32_t base = first; base < un.hi; base += nwarps * kChunk, slot ^= 1) {
+        if (base + nwarps * kChunk < un.hi) stage(slot ^ 1, base + nwarps * kChunk);
+        cp_async_commit();
+        cp_async_wait<1>();  // this lane's copies for the current chunk are in
+        const unsigned char* st = w_stage + slot * kAccumSlotBytes;
+        const uint4 wa = *reinterpret_cast<const uint4*>(st + 16 * lane);
+        const uint4 wb = *reinterpret_cast<const uint4*>(st + 512 + 16 * lane);
+        const uint2 ra = *reinterpret_cast<const uint2*>(st + 1024 + 8 * lane);
+        const uint2 rb = *reinterpret_cast<const uint2*>(st + 1280 + 8 * lane);
+        uint32_t w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        uint32_t d[8] = {ra.x & 0xFFFFu, ra.x >> 16, ra.y & 0xFFFFu, ra.y >> 16,
+                         rb.x & 0xFFFFu, rb.x >> 16, rb.y & 0xFFFFu, rb.y >> 16};
+        if (base < un.mid || base + kChunk > un.hi) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int32_t e = chunk_edge(base, lane, j);
+            if (e < un.mid || e >= un.hi) {
+              w[j] = 0u;  // adds 0 to row 0
+              d[j] = 0u;
+            }
+          }
+        }
+        unsigned long long q[8];
+        codes_to_values(w, U, q);
+        // a warp step inside one row (a long row): one shared-memory addition
+        const uint32_t r0 = __shfl_sync(0xffffffffu, d[0], 0);
+        bool one = true;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) one = one && d[j] == r0;
+        if (__all_sync(0xffffffffu, one)) {
+          unsigned long long r = ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+          if (lane == 0) {
+            const uint32_t up = carry_into(atom_add(a_lo + 4u * r0, (uint32_t)r), (uint32_t)r, (uint32_t)(r >> 32));
+            red_add_nonzero(a_lo + hw + 4u * r0, up);
+          }
+          continue;
+        }
+        // runs of equal rows within each group of 4 consecutive edges are
+        // folded into their first edge (backward, so a head holds its whole
+        // run; the rest add 0): consecutive edges of one row would otherwise
+        // meet in one atomic instruction
 #pragma unroll
         for (int j = 6; j >= 0; --j) {
-          if (j != 3 && d[j] >= 0 && d[j] == d[j + 1]) {
+          if (j != 3 && d[j] == d[j + 1]) {
             q[j] += q[j + 1];
-            d[j + 1] = -1;
+            q[j + 1] = 0ull;
           }
         }
-        // a warp step inside one row (long rows): one shared-memory addition
-        c0 = __shfl_sync(0xffffffffu, d[0], 0);
-        bool one = d[0] >= 0 && d[0] == c0 && d[4] == c0;
-#pragma unroll
-        for (int j = 1; j < 8; ++j)
-          if (j != 4) one = one && d[j] < 0;
-        whole = __all_sync(0xffffffffu, one);
+        acc_add8(a_lo, hw, d, q);
       }
-      if (whole) {
-        unsigned long long r = q[0] + q[4];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-        if (lane == 0) acc_add(s_lo, s_hi, c0, (uint32_t)r, (uint32_t)(r >> 32));
-      } else {
-        // every head's low word with independent atomics, then the carries
-        // (predicated: no branches)
-        uint32_t old[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) old[j] = atom_add_if(a_lo + 4u * (uint32_t)d[j], (uint32_t)q[j], d[j] >= 0);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint32_t up = carry_into(old[j], (uint32_t)q[j], (uint32_t)(q[j] >> 32));
-          red_add_nonzero(a_hi + 4u * (uint32_t)d[j], d[j] >= 0 ? up : 0u);
-        }
-      }
+      cp_async_wait<0>();
     }
-    cp_async_wait<0>();
     __syncthreads();
     if (un.nparts > 1) {
       unsigned long long* g = acc_g + (int64_t)un.split * W;
@@ -489,11 +580,19 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
       if (tid == 0) bin_arrive[un.split] = 0;
       __syncthreads();
     }
+    // finish the bin's rows: x' = coefB + coefA y, c' = code(T(x' / outdeg))
     const float A = prm->coefA, Bc = prm->coefB;
     float mass = 0.f, dang = 0.f, res = 0.f;
     for (int32_t i = tid; i < nv; i += blockDim.x) {
       const float y = from_fixed(((unsigned long long)s_hi[i] << 32) | s_lo[i], U);
-      finish_row(v0 + i, y, A, Bc, x_in, inv_deg, x_out, c_out, mass, dang, res);
+      const int32_t r = v0 + i;
+      const float idg = inv_deg[r];
+      const float xs = fmaf(A, y, Bc);
+      x_out[r] = xs;
+      c_out[r] = code_of(round_store(xs * idg, (T*)nullptr), U);
+      mass += xs;
+      res += fabsf(xs - x_in[r]);
+      if (idg == 0.0f) dang += xs;
     }
     block_partials3(mass, dang, res, partials + 3 * (int64_t)un.b);
     if (tid == 0) {
@@ -510,6 +609,14 @@ __global__ void __launch_bounds__(kBkThreads, 1) bk_accum_kernel(
   }
 }
 
+// c = code(T(x * inv_deg)): the codes of a start vector.
+template <typename T>
+__global__ void bk_codes_kernel(const float* __restrict__ x, const float* __restrict__ inv_deg, int32_t n, int U,
+                                uint32_t* __restrict__ c) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    c[v] = code_of(round_store(x[v] * inv_deg[v], (T*)nullptr), U);
+}
+
 // ---- host side --------------------------------------------------------------
 
 static int bits_to_hold(uint64_t v) {
@@ -518,11 +625,25 @@ static int bits_to_hold(uint64_t v) {
   return b;
 }
 
-// Key bits of the segment index: the radix sort orders whole 8-bit digits,
-// so the index takes whole digits and the payload above it stays out of them.
-static int segment_key_bits(int64_t nseg) {
-  const int b = std::max(1, bits_to_hold((uint64_t)(nseg - 1)));
+// Key bits of the sort index: the radix sort orders whole 8-bit digits, so
+// the index takes whole digits and the payload above it stays out of them.
+static int segment_key_bits(int64_t nidx) {
+  const int b = std::max(1, bits_to_hold((uint64_t)(nidx - 1)));
   return (b + 7) & ~7;
+}
+
+// Geometry of the sort index for n_dense dense sources: kb_bits bits per bin
+// (room for n_dense dense sources and S - D other source blocks), kbits in
+// all (whole digits).
+struct KeyGeom {
+  int kb_bits, kbits;
+};
+static KeyGeom key_geom(int64_t S, int64_t B, int32_t n_dense, int sb_bits) {
+  const int64_t per_bin = (int64_t)n_dense + S - ((int64_t)n_dense >> sb_bits);
+  KeyGeom k;
+  k.kb_bits = bits_to_hold((uint64_t)std::max<int64_t>(per_bin - 1, 0));
+  k.kbits = segment_key_bits(B << k.kb_bits);
+  return k;
 }
 
 static int smem_optin() {
@@ -534,6 +655,13 @@ static int smem_optin() {
 static size_t expand_smem(int sb_bits) { return expand_ids_offset(sb_bits) + kExpandStageBytes; }
 static size_t accum_smem(int w_bits) { return ((size_t)8 << w_bits) + kAccumStageBytes; }
 
+static bool geometry_fits(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_dense) {
+  const int64_t S = ((int64_t)g->n + (1 << sb_bits) - 1) >> sb_bits;
+  const int64_t B = ((int64_t)g->n + (1 << w_bits) - 1) >> w_bits;
+  const KeyGeom kg = key_geom(S, B, n_dense, sb_bits);
+  return kg.kbits + sb_bits + w_bits <= 64;
+}
+
 bool blocked_eligible(const gpr_graph* g, int sb_bits, int w_bits) {
   if (sb_bits < 4 || sb_bits > 16 || w_bits < 4 || w_bits > 16) return false;
   if (g->n < 1 || g->m > (int64_t)INT32_MAX - 2 * kChunk) return false;
@@ -541,11 +669,19 @@ bool blocked_eligible(const gpr_graph* g, int sb_bits, int w_bits) {
   const int64_t B = ((int64_t)g->n + (1 << w_bits) - 1) >> w_bits;
   const int64_t nseg = S * B;
   if (nseg > ((int64_t)1 << 26)) return false;  // segment tables of at most 2^26 entries
-  const int kbits = segment_key_bits(nseg);
-  if (kbits + sb_bits + w_bits > 64) return false;
+  if (!geometry_fits(g, sb_bits, w_bits, 0)) return false;
   const size_t optin = (size_t)smem_optin();
   // static shared memory of the kernels is below 2 KB
   return expand_smem(sb_bits) + 2048 <= optin && accum_smem(w_bits) + 2048 <= optin;
+}
+
+int32_t blocked_max_dense(const gpr_graph* g, int sb_bits, int w_bits) {
+  if (!blocked_eligible(g, sb_bits, w_bits)) return 0;
+  const int dense_bits = 32 - w_bits;
+  int64_t d = std::min<int64_t>((int64_t)1 << dense_bits, g->n);
+  d = (d >> sb_bits) << sb_bits;  // whole source blocks
+  while (d > 0 && !geometry_fits(g, sb_bits, w_bits, (int32_t)d)) d = ((d >> 1) >> sb_bits) << sb_bits;
+  return (int32_t)d;
 }
 
 void blocked_free(Blocked* k, cudaStream_t s) {
@@ -571,7 +707,8 @@ static int persistent_grid(K kernel, size_t smem) {
   return num_sms() * std::max(per_sm, 1);
 }
 
-Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit_edges, cudaStream_t s) {
+Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_dense_req, int64_t unit_edges,
+                       cudaStream_t s) {
   const int64_t unit = std::max<int64_t>(unit_edges, 1 << 12);
   const int64_t xunit = std::min<int64_t>(1 << 20, 4 * unit);  // expand units stage a source block each
   if (!blocked_eligible(g, sb_bits, w_bits))
@@ -580,6 +717,13 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
   k->sb_bits = sb_bits;
   k->w_bits = w_bits;
   k->unit_edges = unit;
+  k->dense_bits = 32 - w_bits;
+  {
+    const int32_t cap = blocked_max_dense(g, sb_bits, w_bits);
+    int32_t nd = std::max<int32_t>(0, std::min(n_dense_req, cap));
+    k->n_dense = (nd >> sb_bits) << sb_bits;
+    k->D = k->n_dense >> sb_bits;
+  }
   {
     int lg = 0;
     while (((int64_t)1 << lg) < g->n) ++lg;  // ceil(log2 n)
@@ -589,9 +733,9 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
   const int64_t m = g->m;
   k->S = (int32_t)(((int64_t)n + (1 << sb_bits) - 1) >> sb_bits);
   k->B = (int32_t)(((int64_t)n + (1 << w_bits) - 1) >> w_bits);
-  const int32_t S = k->S, B = k->B;
+  const int32_t S = k->S, B = k->B, D = k->D;
   const int64_t nseg = (int64_t)S * B;
-  const int kbits = segment_key_bits(nseg);
+  const KeyGeom kg = key_geom(S, B, k->n_dense, sb_bits);
   uint64_t* keys = nullptr;
   uint64_t* alt = nullptr;
   int32_t* seg = nullptr;
@@ -612,11 +756,13 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
     if (m > 0) {
       keys = (uint64_t*)dalloc((size_t)m * 8, s);
       alt = (uint64_t*)dalloc((size_t)m * 8, s);
-      bk_keys_kernel<<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, n, sb_bits, w_bits, kbits, S, keys);
+      bk_keys_kernel<<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, n, sb_bits, w_bits, kg.kbits, k->n_dense, D,
+                                          kg.kb_bits, keys);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
-      const uint64_t* sorted = radix_sort_u64(keys, alt, m, kbits, s, derr);
-      bk_extract_kernel<<<grid, 256, 0, s>>>(sorted, m, sb_bits, kbits, nseg, k->src_lo, k->dst_lo, seg);
+      const uint64_t* sorted = radix_sort_u64(keys, alt, m, kg.kbits, s, derr);
+      bk_extract_kernel<<<grid, 256, 0, s>>>(sorted, m, sb_bits, kg.kbits, k->n_dense, D, kg.kb_bits, k->dense_bits,
+                                             S, nseg, k->src_lo, k->dst_lo, k->vals, seg);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       dfree(keys, s);
@@ -640,11 +786,11 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
     derr = nullptr;
     if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "blocked layout: a look-back wait of the sort timed out"};
 
-    // expand units: per source block, runs of consecutive bins' segments of
-    // at most unit edges and kMaxUnitSegs segments; a longer segment
-    // is cut into pieces of its own
+    // expand units (source blocks past the dense ones): per source block,
+    // runs of consecutive bins' segments of at most unit edges and
+    // kMaxUnitSegs segments; a longer segment is cut into pieces of its own
     std::vector<ExpandUnit> xu;
-    for (int32_t sb = 0; sb < S; ++sb) {
+    for (int32_t sb = D; sb < S; ++sb) {
       int32_t first = -1, last = -1, clo = 0, chi = 0;
       int64_t edges = 0;
       auto flush = [&]() {
@@ -673,17 +819,25 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
       }
       flush();
     }
-    // accumulate units: each bin whole, or cut into near-equal edge ranges
+    // accumulate units: each bin whole, or cut into near-equal edge ranges;
+    // each knows where the bin's dense-source edges end
     std::vector<AccumUnit> au;
     int32_t n_split = 0;
+    int64_t dense_edges = 0;
     for (int32_t b = 0; b < B; ++b) {
       const int64_t lo = h[(size_t)b * S], hi = h[(size_t)(b + 1) * S];
+      const int64_t mid = h[(size_t)b * S + D];
+      dense_edges += mid - lo;
       const int64_t e = hi - lo;
       const int32_t parts = (int32_t)std::max<int64_t>(1, (e + unit - 1) / unit);
       const int32_t split = parts > 1 ? n_split++ : -1;
-      for (int32_t q = 0; q < parts; ++q)
-        au.push_back(AccumUnit{b, (int32_t)(lo + e * q / parts), (int32_t)(lo + e * (q + 1) / parts), parts, split});
+      for (int32_t q = 0; q < parts; ++q) {
+        const int64_t pl = lo + e * q / parts, ph = lo + e * (q + 1) / parts;
+        const int64_t pm = std::min(std::max(mid, pl), ph);
+        au.push_back(AccumUnit{b, (int32_t)pl, (int32_t)pm, (int32_t)ph, parts, split});
+      }
     }
+    k->dense_edges = dense_edges;
     // largest first: the dynamic queues then end with small units
     std::stable_sort(xu.begin(), xu.end(),
                      [](const ExpandUnit& a, const ExpandUnit& b) { return a.hi - a.lo > b.hi - b.lo; });
@@ -707,8 +861,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
     k->ctr = (unsigned int*)dalloc(16, s);
     GPR_CUDA(cudaMemsetAsync(k->ctr, 0, 16, s));
     k->partials = (double*)dalloc((size_t)B * 3 * sizeof(double), s);
-    k->xgrid = std::max(persistent_grid(bk_expand_kernel<float>, expand_smem(sb_bits)),
-                        persistent_grid(bk_expand_kernel<__nv_bfloat16>, expand_smem(sb_bits)));
+    k->xgrid = persistent_grid(bk_expand_kernel, expand_smem(sb_bits));
     k->agrid = std::max(persistent_grid(bk_accum_kernel<float>, accum_smem(w_bits)),
                         persistent_grid(bk_accum_kernel<__nv_bfloat16>, accum_smem(w_bits)));
     k->bytes = (int64_t)me * 8 + nseg * (int64_t)sizeof(int2) + (int64_t)xu.size() * sizeof(ExpandUnit) +
@@ -727,24 +880,37 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int64_t unit
 void blocked_record_reset(Blocked* k, cudaStream_t s) { GPR_CUDA(cudaMemsetAsync(k->ctr, 0, 16, s)); }
 
 template <typename T>
-void blocked_record_step(Blocked* k, const gpr_graph* g, const T* c_in, const float* x_in, float* x_out, T* c_out,
-                         const float* inv_deg, StepParams* prm, double* log_row, int32_t it, cudaStream_t s) {
+void blocked_record_codes(Blocked* k, const gpr_graph* g, const float* x, const float* inv_deg, uint32_t* c,
+                          cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, num_sms() * 8));
+  bk_codes_kernel<T><<<grid, 256, 0, s>>>(x, inv_deg, g->n, k->ubits, c);
+  GPR_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void blocked_record_step(Blocked* k, const gpr_graph* g, const uint32_t* c_in, const float* x_in, float* x_out,
+                         uint32_t* c_out, const float* inv_deg, StepParams* prm, double* log_row, int32_t it,
+                         cudaStream_t s) {
   // every CTA of a launch takes units until one fetch fails: a launch moves
   // a counter by exactly (units + grid)
   const unsigned int ex = (unsigned int)((int64_t)it * (k->n_xu + k->xgrid));
   const unsigned int ea = (unsigned int)((int64_t)it * (k->n_au + k->agrid));
-  bk_expand_kernel<T><<<k->xgrid, kBkThreads, expand_smem(k->sb_bits), s>>>(
-      c_in, g->n, k->sb_bits, k->ubits, k->B, k->xseg, k->xu, k->n_xu, k->src_lo, k->vals, k->ctr, ex);
+  bk_expand_kernel<<<k->xgrid, kBkThreads, expand_smem(k->sb_bits), s>>>(
+      c_in, g->n, k->sb_bits, k->B, k->xseg, k->xu, k->n_xu, k->src_lo, k->vals, k->ctr, ex);
   bk_accum_kernel<T><<<k->agrid, kBkThreads, accum_smem(k->w_bits), s>>>(
-      k->vals, k->dst_lo, g->n, k->w_bits, k->ubits, k->au, k->n_au, k->ctr, ea, k->acc_g, k->bin_arrive, x_in,
-      inv_deg, x_out, c_out, prm, k->partials, k->B, log_row);
+      k->vals, k->dst_lo, c_in, k->dense_bits, g->n, k->w_bits, k->ubits, k->au, k->n_au, k->ctr, ea, k->acc_g,
+      k->bin_arrive, x_in, inv_deg, x_out, c_out, prm, k->partials, k->B, log_row);
   GPR_CUDA(cudaGetLastError());
 }
 
-template void blocked_record_step<float>(Blocked*, const gpr_graph*, const float*, const float*, float*, float*,
-                                         const float*, StepParams*, double*, int32_t, cudaStream_t);
-template void blocked_record_step<__nv_bfloat16>(Blocked*, const gpr_graph*, const __nv_bfloat16*, const float*,
-                                                 float*, __nv_bfloat16*, const float*, StepParams*, double*, int32_t,
+template void blocked_record_codes<float>(Blocked*, const gpr_graph*, const float*, const float*, uint32_t*,
+                                          cudaStream_t);
+template void blocked_record_codes<__nv_bfloat16>(Blocked*, const gpr_graph*, const float*, const float*, uint32_t*,
+                                                  cudaStream_t);
+template void blocked_record_step<float>(Blocked*, const gpr_graph*, const uint32_t*, const float*, float*,
+                                         uint32_t*, const float*, StepParams*, double*, int32_t, cudaStream_t);
+template void blocked_record_step<__nv_bfloat16>(Blocked*, const gpr_graph*, const uint32_t*, const float*, float*,
+                                                 uint32_t*, const float*, StepParams*, double*, int32_t,
                                                  cudaStream_t);
 
 }  // namespace gpr

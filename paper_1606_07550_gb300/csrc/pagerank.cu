@@ -289,12 +289,15 @@ struct Choice {
   int sched = kSchedPull;
   int sb = 15, wb = 14;   // source-block and bin bits
   int64_t unit = 1 << 16; // edges per work unit
+  int32_t dense = -1;     // dense sources (-1: as many as the layout takes)
 };
 
 struct PagerankWork {
   int device = 0;
   float* x[2] = {nullptr, nullptr};  // n floats each: the rank vector, always FP32
-  void* c[2] = {nullptr, nullptr};   // n * 4 bytes each: contributions x / outdeg, FP32 or BF16
+  // n * 4 bytes each: contributions x / outdeg, FP32 or BF16 (pull), or
+  // their 32-bit fixed-point codes (blocked)
+  void* c[2] = {nullptr, nullptr};
   float* out_tmp = nullptr;          // n floats, for host-pointer output
   float* y_hot = nullptr;            // n floats: hot-pass row sums
   int hot_grid = 0;                  // 0: no hot pass
@@ -447,11 +450,13 @@ static void record_iterations(gpr_graph* g, PagerankWork* w, int32_t iters, int 
                                     P.split_cbeg, P.split_cend, 0, w->chunk_sum, w->partials, w->init_grid + 1,
                                     w->prm, w->log, w->arrive);
   if (sched == kSchedBlocked) {
+    uint32_t* cc[2] = {(uint32_t*)w->c[0], (uint32_t*)w->c[1]};
+    blocked_record_codes<T>(w->blk, g, x[0], P.inv_deg, cc[0], s);
     blocked_record_reset(w->blk, s);
     for (int32_t it = 0; it < iters; ++it) {
       const int a = it & 1, b = a ^ 1;
-      blocked_record_step<T>(w->blk, g, c[a], x[a], x[b], c[b], P.inv_deg, w->prm, w->log + 3 * (int64_t)(it + 1), it,
-                             s);
+      blocked_record_step<T>(w->blk, g, cc[a], x[a], x[b], cc[b], P.inv_deg, w->prm, w->log + 3 * (int64_t)(it + 1),
+                             it, s);
     }
     return;
   }
@@ -528,25 +533,33 @@ static PagerankWork* work_make(gpr_graph* g, cudaStream_t s) {
 
 // ---- schedule choice and the autotuner ----------------------------------------
 
-// Units of about m / 2048 edges, between 2^16 and 2^20: every SM gets several.
+// Units of about m / 1024 edges, between 2^16 and 2^21: every SM gets
+// several, and few bins are cut into parts that meet in global memory.
 static int64_t default_unit(const gpr_graph* g) {
   int64_t u = 1 << 16;
-  while (u < (1 << 20) && u * 2048 < g->m) u <<= 1;
+  while (u < (1 << 21) && u * 1024 < g->m) u <<= 1;
   return u;
 }
 
-// GPR_BLOCK_BITS="sb,w[,log2 unit]" overrides the blocked shape (tests,
-// experiments); returns false if unset.
+// GPR_BLOCK_BITS="sb,w[,log2 unit[,dense sources]]" overrides the blocked
+// shape (tests, experiments); returns false if unset.
 static bool env_block_shape(Choice* c) {
   const char* e = getenv("GPR_BLOCK_BITS");
   if (!e) return false;
-  int a = 0, b = 0, u = 0;
-  const int k = sscanf(e, "%d,%d,%d", &a, &b, &u);
+  int a = 0, b = 0, u = 0, dn = -1;
+  const int k = sscanf(e, "%d,%d,%d,%d", &a, &b, &u, &dn);
   if (k < 2) return false;
   c->sb = a;
   c->wb = b;
-  if (k == 3 && u >= 12 && u <= 30) c->unit = (int64_t)1 << u;
+  if (k >= 3 && u >= 12 && u <= 30) c->unit = (int64_t)1 << u;
+  if (k == 4) c->dense = dn;
   return true;
+}
+
+// The dense-source count a choice asks of g's layout.
+static int32_t dense_of(const gpr_graph* g, const Choice& c) {
+  const int32_t cap = blocked_max_dense(g, c.sb, c.wb);
+  return c.dense < 0 ? cap : std::min(c.dense, cap);
 }
 
 // Tuned choices by graph shape (ceil log2 n, ceil log2 m, storage type):
@@ -576,13 +589,15 @@ static void drop_exec(PagerankWork* w) {
 
 // The blocked layout of shape c (rebuilt if another shape is held).
 static void ensure_layout(gpr_graph* g, PagerankWork* w, const Choice& c, cudaStream_t s) {
-  if (w->blk && (w->blk->sb_bits != c.sb || w->blk->w_bits != c.wb || w->blk->unit_edges != c.unit)) {
+  const int32_t nd = (dense_of(g, c) >> c.sb) << c.sb;
+  if (w->blk && (w->blk->sb_bits != c.sb || w->blk->w_bits != c.wb || w->blk->unit_edges != c.unit ||
+                 w->blk->n_dense != nd)) {
     drop_exec(w);
     GPR_CUDA(cudaStreamSynchronize(s));
     blocked_free(w->blk, s);
     w->blk = nullptr;
   }
-  if (!w->blk) w->blk = blocked_build(g, c.sb, c.wb, c.unit, s);
+  if (!w->blk) w->blk = blocked_build(g, c.sb, c.wb, nd, c.unit, s);
 }
 
 // The iteration loop of `iters` steps with schedule `sched`, as a CUDA graph.
@@ -627,7 +642,7 @@ static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype 
   w->exec_dt = (int)dt;
   w->exec_sched = sched;
   w->exec_warm = warm;
-  w->exec_kernels = sched == kSchedBlocked ? 2 + (int64_t)iters * 2
+  w->exec_kernels = sched == kSchedBlocked ? 3 + (int64_t)iters * 2
                                            : 2 + (int64_t)iters * (g->plan.nbuckets + 1 + (w->hot_grid > 0 ? 1 : 0));
 }
 
@@ -657,12 +672,19 @@ static Choice tune(gpr_graph* g, PagerankWork* w, gpr_dtype dt, int32_t trial_st
   std::vector<Choice> cands;
   cands.push_back(Choice{});  // pull
   const int64_t u = default_unit(g);
-  const int shapes[][2] = {{15, 14}, {14, 14}, {15, 13}, {13, 13}};
-  for (const auto& sh : shapes)
-    for (int64_t uu : {u, std::max<int64_t>(u / 4, 1 << 14)}) {
-      Choice c{kSchedBlocked, sh[0], sh[1], uu};
-      if (blocked_eligible(g, c.sb, c.wb)) cands.push_back(c);
-    }
+  // block shapes with the most dense sources; for the first shape also a
+  // quarter of them, none, and halved and doubled units
+  const int shapes[][2] = {{15, 14}, {14, 14}, {15, 13}};
+  for (const auto& sh : shapes) {
+    if (!blocked_eligible(g, sh[0], sh[1])) continue;
+    const int32_t cap = blocked_max_dense(g, sh[0], sh[1]);
+    cands.push_back(Choice{kSchedBlocked, sh[0], sh[1], u, cap});
+    if (cands.size() > 2) continue;
+    if (((cap / 4) >> sh[0]) > 0) cands.push_back(Choice{kSchedBlocked, sh[0], sh[1], u, (cap / 4) >> sh[0] << sh[0]});
+    if (cap > 0) cands.push_back(Choice{kSchedBlocked, sh[0], sh[1], u, 0});
+    cands.push_back(Choice{kSchedBlocked, sh[0], sh[1], std::max<int64_t>(u / 2, 1 << 14), cap});
+    cands.push_back(Choice{kSchedBlocked, sh[0], sh[1], u * 2, cap});
+  }
   Choice best;
   double best_ms = 0.0, pull_ms = 0.0;
   for (size_t i = 0; i < cands.size(); ++i) {
@@ -684,6 +706,7 @@ static Choice tune(gpr_graph* g, PagerankWork* w, gpr_dtype dt, int32_t trial_st
     out->sb_bits = best.sched == kSchedBlocked ? best.sb : 0;
     out->w_bits = best.sched == kSchedBlocked ? best.wb : 0;
     out->unit_edges = best.sched == kSchedBlocked ? best.unit : 0;
+    out->dense_sources = best.sched == kSchedBlocked ? dense_of(g, best) : 0;
     out->ms_per_step = best_ms;
     out->pull_ms_per_step = pull_ms;
     out->candidates = (int32_t)cands.size();
@@ -958,9 +981,9 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
     int32_t it_g = 0, it_t = 0;  // steps since the reset, per layout
     auto product = [&](gpr_graph* gg, PagerankWork* ww, const float* c_in, const float* x_in, float* x_out,
                        float* c_out, double* log_row) {
-      if (blocked)
-        blocked_record_step<float>(ww->blk, gg, c_in, x_in, x_out, c_out, w->ones, w->prm, log_row,
-                                   gg == g ? it_g++ : it_t++, s);
+      if (blocked)  // the contributions are held as codes
+        blocked_record_step<float>(ww->blk, gg, (const uint32_t*)c_in, x_in, x_out, (uint32_t*)c_out, w->ones,
+                                   w->prm, log_row, gg == g ? it_g++ : it_t++, s);
       else
         launch_pull_step(gg, ww, s, c_in, x_in, x_out, c_out, w->ones, w->prm, log_row);
     };
@@ -976,6 +999,10 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
                                           w->chunk_sum, w->partials, w->init_grid + 1, w->prm, w->log, w->arrive);
     GPR_CUDA(cudaGetLastError());
     count_launches(2);
+    if (blocked) {  // the first product reads c0 through g's layout
+      blocked_record_codes<float>(w->blk, g, x0, w->ones, (uint32_t*)c0, s);
+      count_launches(1);
+    }
     if (kind == 0) {
       for (int32_t it = 0; it < iters; ++it) {
         const int a = it & 1, b = a ^ 1;

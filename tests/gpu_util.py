@@ -38,3 +38,36 @@ def random_coo_with_dups(rng, n, m_raw, p_loop=0.05, p_dup=0.2):
         j = rng.integers(0, m_raw, k)
         src[idx], dst[idx] = src[j], dst[j]
     return src, dst
+
+
+def load_rmat25_oracle():
+    """The oracle's stored PageRank of the R-MAT scale-25 workload (written by
+    tests/golden/make_rmat25_oracle.py): the committed summary, and the whole
+    FP64 vector when its file is present and its sha256 matches (else None)."""
+    import hashlib
+    import json
+    import os
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    js = os.path.join(root, "tests", "golden", "rmat-s25-ef32_pagerank100.json")
+    if not os.path.exists(js):
+        return None, None
+    with open(js) as f:
+        meta = json.load(f)
+    path = os.path.join(root, meta["vector_file"])
+    full = None
+    if os.path.exists(path):
+        raw = open(path, "rb").read()
+        if hashlib.sha256(raw).hexdigest() == meta["vector_sha256"]:
+            full = np.frombuffer(raw, np.float64)
+    return meta, full
+
+
+def sampled_errors(x, meta):
+    """On the summary's sampled nodes: the L1 error relative to the sampled
+    mass (an unbiased estimate of the full-vector L1, whose mass is 1) and
+    the largest relative error."""
+    nodes = np.asarray(meta["sample_nodes"], np.int64)
+    ref = np.asarray(meta["sample_x"], np.float64)
+    got = np.asarray(x, np.float64)[nodes]
+    return float(np.abs(got - ref).sum() / ref.sum()), max_rel(got, ref)
