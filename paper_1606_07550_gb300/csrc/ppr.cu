@@ -22,11 +22,22 @@
 //
 // Per-column arithmetic does not depend on the other columns of a job or on
 // the batch around it: a column gives the same bits alone or in any mix.
+//
+// Storage of the gathered contributions c = x / outdeg: FP32; FP16 times
+// 2^10; or BF16 as error-feedback deltas.  With BF16, a node keeps in FP32
+// the sum s of every value it has sent so far and sends q = bf16(c - s) (round
+// to nearest), then s += q; a row keeps in FP32 the running sum y of the
+// q it has gathered, so that y is the sum of its in-neighbours' s.  Each s
+// differs from the exact c by one rounding of the last difference c - s,
+// which shrinks with the step-to-step change of x: the rounding of one step
+// is corrected by the next instead of staying in the result.  The state per
+// node and column is x, y and s (FP32); the gathers read 2 bytes.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <climits>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -61,31 +72,8 @@ __device__ __forceinline__ float2 ld_pair(const __nv_bfloat16* p) {
 __device__ __forceinline__ void st_pair(float* p, float a, float b, uint32_t) {
   *reinterpret_cast<float2*>(p) = make_float2(a, b);
 }
-// BF16 contributions are rounded stochastically: add 16 random bits below the
-// kept mantissa and truncate (non-negative finite values only).  Round-to-
-// nearest would round the same value the same way at every step near the
-// fixed point and bias the result by up to d/(1-d) unit roundoffs; random
-// rounding makes the errors of successive steps independent, so the
-// contraction damps them.  The bits come from a counter-based hash of
-// (column, step, node), so a column gives the same bits alone or in a batch.
-__device__ __forceinline__ uint16_t bf16_sr(float v, uint32_t r16) {
-  return (uint16_t)((__float_as_uint(v) + (r16 & 0xFFFFu)) >> 16);
-}
-__device__ __forceinline__ void st_pair(__nv_bfloat16* p, float a, float b, uint32_t rnd) {
-  const uint32_t packed = (uint32_t)bf16_sr(a, rnd) | ((uint32_t)bf16_sr(b, rnd >> 16) << 16);
-  *reinterpret_cast<uint32_t*>(p) = packed;
-}
 __device__ __forceinline__ void st_pair(__half* p, float a, float b, uint32_t) {
   *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * kHalfScale, b * kHalfScale);
-}
-__device__ __forceinline__ uint32_t hash32(uint32_t x) {
-  // a 32-bit integer finaliser (Wang / Jenkins style mix)
-  x ^= x >> 16;
-  x *= 0x7feb352du;
-  x ^= x >> 15;
-  x *= 0x846ca68bu;
-  x ^= x >> 16;
-  return x;
 }
 template <typename T>
 __device__ __forceinline__ void st_one(T* p, float a);
@@ -133,26 +121,49 @@ struct ColRegs {
   float b0, b1;      // seed coefficient (1 - d) + d D
   int32_t s0, s1;    // relabelled seed rows
   bool l0, l1;       // live
-  uint32_t k0, k1;   // rounding-hash keys of (column, step)
 };
 
 // The row's previous state: loaded before the gathers so its latency overlaps them.
 __device__ __forceinline__ float2 ld_state(const float* X, int32_t p, int lane) {
   return *reinterpret_cast<const float2*>(X + (int64_t)p * kPprCols + 2 * lane);
 }
+// BF16 deltas: the row's running sums (y0, y1) and sent sums (s0, s1) of the
+// lane's two columns, one 16-byte record per lane (null for other storage).
+__device__ __forceinline__ float4 ld_ys(const float4* YS, int32_t p, int lane) {
+  return YS ? YS[(int64_t)p * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ uint32_t bf16_bits_rn(float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  return (uint32_t)*reinterpret_cast<const uint16_t*>(&h);
+}
+__device__ __forceinline__ float bf16_bits_to_float(uint32_t b) { return __uint_as_float(b << 16); }
 
 template <typename T>
-__device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, float2 xo, const ColRegs& c,
-                                               float* __restrict__ X, T* __restrict__ Cout,
-                                               const float* __restrict__ inv_deg, int lane, float (&acc)[2][3]) {
+__device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, float2 xo, float4 ys, const ColRegs& c,
+                                               float* __restrict__ X, float4* __restrict__ YS,
+                                               T* __restrict__ Cout, const float* __restrict__ inv_deg, int lane,
+                                               float (&acc)[2][3]) {
   const float inv = inv_deg[p];
   float* xp = X + (int64_t)p * kPprCols + 2 * lane;
+  constexpr bool kDelta = std::is_same<T, __nv_bfloat16>::value;
+  if constexpr (kDelta) {  // y holds this step's gathered deltas: add the running sums
+    y.x += ys.x;
+    y.y += ys.y;
+  }
   const float n0 = c.l0 ? fmaf(c.a0, y.x, p == c.s0 ? c.b0 : 0.f) : xo.x;
   const float n1 = c.l1 ? fmaf(c.a1, y.y, p == c.s1 ? c.b1 : 0.f) : xo.y;
   *reinterpret_cast<float2*>(xp) = make_float2(n0, n1);
-  const uint32_t hp = (uint32_t)p * 0x9E3779B1u;
-  const uint32_t rnd = (hash32(c.k0 ^ hp) & 0xFFFFu) | (hash32(c.k1 ^ hp) << 16);
-  st_pair(Cout + (int64_t)p * kPprCols + 2 * lane, n0 * inv, n1 * inv, rnd);
+  if constexpr (kDelta) {
+    // the new contributions as deltas against what was sent (0 for columns
+    // that are not running)
+    const uint32_t q0 = c.l0 ? bf16_bits_rn(n0 * inv - ys.z) : 0u;
+    const uint32_t q1 = c.l1 ? bf16_bits_rn(n1 * inv - ys.w) : 0u;
+    YS[(int64_t)p * 32 + lane] = make_float4(c.l0 ? y.x : ys.x, c.l1 ? y.y : ys.y, ys.z + bf16_bits_to_float(q0),
+                                             ys.w + bf16_bits_to_float(q1));
+    *reinterpret_cast<uint32_t*>(Cout + (int64_t)p * kPprCols + 2 * lane) = q0 | (q1 << 16);
+  } else {
+    st_pair(Cout + (int64_t)p * kPprCols + 2 * lane, n0 * inv, n1 * inv, 0u);
+  }
   acc[0][0] += n0;
   acc[1][0] += n1;
   if (inv == 0.f) {
@@ -237,7 +248,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
   __shared__ int32_t s_stall[kPprCols];
   __shared__ double s_D[kPprCols], s_res[kPprCols];
   __shared__ int32_t s_status[kPprCols], s_iters[kPprCols], s_maxit[kPprCols], s_newdone[kPprCols];
-  __shared__ uint32_t s_key[kPprCols];
 
   for (;;) {
     if (crank == 0 && tid == 0) s_job = (int)atomicAdd(queue, 1u);
@@ -255,6 +265,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
     T* Cb[2];
     Cb[0] = (T*)(base + (int64_t)J->n_cap * kPprCols * 4);
     Cb[1] = Cb[0] + (int64_t)J->n_cap * kPprCols;
+    // BF16 deltas: running and sent sums after the two contribution buffers
+    float4* YS = std::is_same<T, __nv_bfloat16>::value ? reinterpret_cast<float4*>(Cb[1] + (int64_t)J->n_cap * kPprCols)
+                                                       : nullptr;
     int parity = 0;
 
     // this block's rows: split by edges + kRowWeight * rows
@@ -292,7 +305,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       }
       s_d[tid] = cr.damping;
       s_tol[tid] = cr.tol;
-      s_key[tid] = hash32((uint32_t)cr.seed * 0x85EBCA6Bu ^ __float_as_uint(cr.damping));
       s_maxit[tid] = cr.max_iters;
     }
     __syncthreads();
@@ -303,12 +315,19 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         X[i] = 0.f;
         st_one(Cc + i, 0.f);
       }
+      if (YS)
+        for (int64_t i = (int64_t)r0 * 32 + tid; i < (int64_t)r1 * 32; i += kPprThreads)
+          YS[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       __syncthreads();
       if (tid < kPprCols && s_status[tid] == kColFresh) {
         const int32_t s = s_seed[tid];
         if (s >= r0 && s < r1) {
           X[(int64_t)s * kPprCols + tid] = 1.f;
           st_one(Cc + (int64_t)s * kPprCols + tid, inv_deg[s]);
+          if (YS) {  // the first delta is the whole contribution: it is what has been sent
+            float* ysf = reinterpret_cast<float*>(YS + (int64_t)s * 32 + (tid >> 1));
+            ysf[2 + (tid & 1)] = bf16_bits_to_float(bf16_bits_rn(inv_deg[s]));
+          }
         }
       }
       __syncthreads();
@@ -338,8 +357,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         c.b1 = (float)((1.0 - (double)s_d[k1]) + (double)s_d[k1] * s_D[k1]);
         c.s0 = s_seed[k0];
         c.s1 = s_seed[k1];
-        c.k0 = hash32(s_key[k0] ^ hash32((uint32_t)s_iters[k0] + 0x632BE5ABu));
-        c.k1 = hash32(s_key[k1] ^ hash32((uint32_t)s_iters[k1] + 0x632BE5ABu));
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       // light rows: one warp per row, round-robin (neighbouring rows share
@@ -348,8 +365,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
         const float2 xo = ld_state(X, p, lane);
+        const float4 ys = ld_ys(YS, p, lane);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
-        finish_ppr_row(p, y, xo, c, X, Cout, inv_deg, lane, acc);
+        finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
       }
       // long rows: the whole block, fixed-order combine
       for (int32_t hi = h0; hi < h1; ++hi) {
@@ -367,7 +385,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
             yx += s_heavy[w][2 * lane];
             yy += s_heavy[w][2 * lane + 1];
           }
-          finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), c, X, Cout, inv_deg, lane, acc);
+          finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), ld_ys(YS, p, lane), c, X, YS, Cout, inv_deg,
+                         lane, acc);
         }
         __syncthreads();
       }
@@ -461,7 +480,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
   __shared__ int32_t s_seed[kPprCols], s_status[kPprCols], s_iters[kPprCols], s_newdone[kPprCols];
   __shared__ float s_d[kPprCols];
   __shared__ double s_D[kPprCols];
-  __shared__ uint32_t s_key[kPprCols];
   const int cur = step & 1, prev = cur ^ 1;
   for (int32_t ii = blockIdx.x; ii < nitems; ii += gridDim.x) {
     const StepItem item = items[ii];
@@ -469,6 +487,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
     const int32_t r0 = S->part_rows[item.part], r1 = S->part_rows[item.part + 1];
     const float* __restrict__ inv_deg = S->inv_deg;
     float* X = S->X;
+    float4* YS = std::is_same<T, __nv_bfloat16>::value ? S->YS : nullptr;
 
     // ---- column state for this launch
     if (tid < kPprCols) {
@@ -476,7 +495,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       const int32_t seed_row = cr.status == kColEmpty ? -1 : S->old2new[cr.seed];
       s_seed[tid] = seed_row;
       s_d[tid] = cr.damping;
-      s_key[tid] = hash32((uint32_t)cr.seed * 0x85EBCA6Bu ^ __float_as_uint(cr.damping));
       int32_t status, iters, stall;
       double D, res, best;
       int newdone = 0;
@@ -573,6 +591,18 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
             X[o + k1] = v;
             st_one(Cc + o + k1, v * idg);
           }
+          if (YS) {  // running sums 0; sent sums = the first delta (the whole contribution)
+            float4 r = YS[(int64_t)p * 32 + lane];
+            if (f0) {
+              r.x = 0.f;
+              r.z = p == sr0 ? bf16_bits_to_float(bf16_bits_rn(idg)) : 0.f;
+            }
+            if (f1) {
+              r.y = 0.f;
+              r.w = p == sr1 ? bf16_bits_to_float(bf16_bits_rn(idg)) : 0.f;
+            }
+            YS[(int64_t)p * 32 + lane] = r;
+          }
         }
       }
       __syncthreads();
@@ -612,8 +642,6 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         c.b1 = (float)((1.0 - (double)s_d[k1]) + (double)s_d[k1] * s_D[k1]);
         c.s0 = s_seed[k0];
         c.s1 = s_seed[k1];
-        c.k0 = hash32(s_key[k0] ^ hash32((uint32_t)s_iters[k0] + 0x632BE5ABu));
-        c.k1 = hash32(s_key[k1] ^ hash32((uint32_t)s_iters[k1] + 0x632BE5ABu));
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       const int32_t heavy_deg = S->heavy_deg;
@@ -623,8 +651,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
         const float2 xo = ld_state(X, p, lane);
+        const float4 ys = ld_ys(YS, p, lane);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
-        finish_ppr_row(p, y, xo, c, X, Cout, inv_deg, lane, acc);
+        finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
       }
       // long rows: their chunk sums (this step's chunk launch), in chunk
       // order, a warp per row
@@ -643,7 +672,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
             yy += v.y;
           }
         }
-        finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), c, X, Cout, inv_deg, lane, acc);
+        finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), ld_ys(YS, p, lane), c, X, YS, Cout, inv_deg,
+                       lane, acc);
       }
       for (int v = 0; v < 3; ++v) {
         s_wpart[warp][v][2 * lane] = acc[0][v];
@@ -895,8 +925,11 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
     int clusters = ppr_max_clusters(dt);
     if (clusters <= 0) throw StatusFail{GPR_ECUDA, "no thread-block cluster of the PPR kernel fits on this GPU"};
     clusters = std::min(clusters, nj);
+    // per row and column: x (FP32), two contribution buffers, and with BF16
+    // deltas the running and sent sums (FP32 each)
     const size_t tsz = (dt == GPR_BF16 || dt == GPR_FP16) ? 2 : 4;
-    const int64_t stride = (((int64_t)n_cap * kPprCols * (4 + 2 * tsz)) + 255) & ~(int64_t)255;
+    const int64_t per = 4 + 2 * (int64_t)tsz + (dt == GPR_BF16 ? 8 : 0);
+    const int64_t stride = (((int64_t)n_cap * kPprCols * per) + 255) & ~(int64_t)255;
     char* ws = (char*)T((size_t)stride * clusters);
     ppr_launch(jobs_dev, order_dev, nj, queue, ws, stride, clusters, dt, s);
     // per-column results back to the caller

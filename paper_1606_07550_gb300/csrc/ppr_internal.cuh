@@ -3,6 +3,7 @@
 // (serve.cu).
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace gpr {
@@ -72,6 +73,7 @@ struct SlotDesc {
   const int32_t* part_rows;  // nparts + 1 row boundaries
   float* X;
   void* C[2];
+  float4* YS;                // BF16 deltas: per row and lane the running and sent sums (null otherwise)
   int32_t parity;            // C buffer holding the contributions at the start of the tick
   int32_t pad;
   PprCol* rec;               // 64 host-visible records

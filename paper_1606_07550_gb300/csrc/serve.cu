@@ -47,6 +47,7 @@ struct Slot {
   float* X = nullptr;
   void* C0 = nullptr;
   void* C1 = nullptr;
+  float4* YS = nullptr;  // BF16 deltas: running and sent sums
   int32_t parity = 0;
   int64_t bytes = 0;
   int32_t nparts = 1;
@@ -119,7 +120,9 @@ static int32_t parts_for(const gpr_server* S, const gpr_graph* g) {
 
 static int64_t slot_bytes(const gpr_server* S, const gpr_graph* g, gpr_dtype dt) {
   const int64_t P = parts_for(S, g);
-  return (int64_t)g->n * kPprCols * (4 + 2 * (int64_t)elem_bytes(dt)) + (P + 1) * 4 +
+  // per row and column: x, two contribution buffers, and with BF16 deltas
+  // the running and sent sums
+  return (int64_t)g->n * kPprCols * (4 + 2 * (int64_t)elem_bytes(dt) + (dt == GPR_BF16 ? 8 : 0)) + (P + 1) * 4 +
          kPprCols * (int64_t)(sizeof(PprCol) + 2 * sizeof(ColState)) + 2 * P * 3 * kPprCols * 8 +
          (int64_t)std::max(g->plan.nchunks, 1) * kPprCols * 4;
 }
@@ -159,6 +162,7 @@ static void fill_desc(SlotDesc& D, const gpr_graph* g, const Slot* sl) {
   D.X = sl->X;
   D.C[0] = sl->C0;
   D.C[1] = sl->C1;
+  D.YS = sl->YS;
   D.parity = sl->parity;
   D.rec = sl->d_rec;
   D.st[0] = sl->d_st;
@@ -171,6 +175,7 @@ static void free_slot(gpr_server* S, Slot* sl) {
   dfree(sl->X, S->stream);
   dfree(sl->C0, S->stream);
   dfree(sl->C1, S->stream);
+  dfree(sl->YS, S->stream);
   dfree(sl->part_rows, S->stream);
   dfree(sl->d_rec, S->stream);
   dfree(sl->d_st, S->stream);
@@ -208,6 +213,7 @@ static bool try_admit(gpr_server* S, Req& r, bool existing_only = false) {
         sl->X = (float*)dalloc((size_t)g->n * kPprCols * 4, S->stream);
         sl->C0 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
         sl->C1 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
+        if (r.dt == GPR_BF16) sl->YS = (float4*)dalloc((size_t)g->n * kPprCols * 8, S->stream);
         sl->part_rows = (int32_t*)dalloc(((size_t)sl->nparts + 1) * 4, S->stream);
         sl->d_rec = (PprCol*)dalloc(kPprCols * sizeof(PprCol), S->stream);
         sl->d_st = (ColState*)dalloc(2 * kPprCols * sizeof(ColState), S->stream);
@@ -218,6 +224,7 @@ static bool try_admit(gpr_server* S, Req& r, bool existing_only = false) {
         dfree(sl->X, S->stream);
         dfree(sl->C0, S->stream);
         dfree(sl->C1, S->stream);
+        dfree(sl->YS, S->stream);
         dfree(sl->part_rows, S->stream);
         dfree(sl->d_rec, S->stream);
         dfree(sl->d_st, S->stream);

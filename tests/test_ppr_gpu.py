@@ -1,10 +1,9 @@
 """Batched personalised PageRank on the GPU against the FP64 CPU oracle.
 
 Every column is compared with a single-seed oracle run at the same step count:
-L1 <= 1e-5 with FP32 contributions and <= 1e-3 with scaled FP16 ones.  BF16
-contributions (8-bit significand) have an error floor near 1e-3 for
-personalised columns, whose mass sits on few nodes; they are held to 3e-3.
-A column must give the same bits alone as inside a batch.
+L1 <= 1e-5 with FP32 contributions, <= 1e-3 with scaled FP16 ones and <= 1e-3
+with BF16 ones (sent as error-feedback deltas).  A column must give the same
+bits alone as inside a batch.
 """
 import numpy as np
 import pytest
@@ -17,7 +16,7 @@ from gpu_util import l1, random_coo_with_dups
 
 pytestmark = pytest.mark.gpu
 
-TOL = {gpr.FP32: 1e-5, gpr.FP16: 1e-3, gpr.BF16: 3e-3}
+TOL = {gpr.FP32: 1e-5, gpr.FP16: 1e-3, gpr.BF16: 1e-3}
 
 
 @pytest.fixture(scope="module")
@@ -53,12 +52,27 @@ def test_columns_match_oracle(torch, dt):
         damp = rng.uniform(0.8, 0.9, k).astype(np.float32)
         reqs.append((g, seeds, damp))
     xs, res = run(torch, reqs, 50, dt=dt)
+    worst = 0.0
     for (g, seeds, damp), (_, ref), x, (it, _) in zip(reqs, graphs, xs, res):
         assert (it == 50).all()
         for k, s in enumerate(seeds):
             xr, _ = oracle.ppr(ref, int(s), float(damp[k]), 50)
             err = l1(x[:, k], xr)
+            worst = max(worst, err)
             assert err <= TOL[dt], (k, s, err)
+    print(f"dtype {dt}: worst column L1 {worst:.3e}")
+
+
+def test_bf16_deltas_correct_their_rounding(torch):
+    # the error of a BF16 column is one rounding of the last step-to-step
+    # change, not of the contributions: far below the 8-bit significand's
+    # 2^-9 relative error once the iteration has settled
+    g, ref = make_graph(torch, 20_000, 400_000, 44)
+    seeds = np.array([0, 1, 2, 3, 100, 5000, 19_999], np.int32)
+    xs, _ = run(torch, [(g, seeds, 0.85)], 100, dt=gpr.BF16)
+    for k, s in enumerate(seeds):
+        xr, _ = oracle.ppr(ref, int(s), 0.85, 100)
+        assert l1(xs[0][:, k], xr) <= 1e-4
 
 
 def test_alone_equals_in_mix_bitwise(torch):
@@ -116,7 +130,7 @@ def test_tolerance_stop(torch):
             assert l1(xs[0][:, k], xstar) <= tol + 1e-5
 
 
-@pytest.mark.parametrize("dt,tol,err", [(gpr.FP32, 1e-12, 1e-5), (gpr.FP16, 1e-6, 1e-3), (gpr.BF16, 1e-6, 3e-3)])
+@pytest.mark.parametrize("dt,tol,err", [(gpr.FP32, 1e-12, 1e-5), (gpr.FP16, 1e-6, 1e-3), (gpr.BF16, 1e-9, 1e-3)])
 def test_tolerance_below_the_storage_floor_stops_at_the_floor(torch, dt, tol, err):
     # the bound d/(1-d)||x_k - x_{k-1}||_1 cannot reach tol in this storage:
     # a column stops once its residual has stopped shrinking, long before

@@ -59,6 +59,29 @@ def test_single_request_matches_oracle(torch, pool):
     srv.close()
 
 
+@pytest.mark.parametrize("dt,tol,storage", [(gpr.FP32, 1e-6, 1e-5), (gpr.FP32, 1e-3, 1e-5), (gpr.FP16, 1e-3, 1e-3),
+                                             (gpr.BF16, 1e-3, 1e-3), (gpr.BF16, 1e-6, 1e-5)])
+def test_served_columns_reach_the_oracle_fixed_point(torch, pool, dt, tol, storage):
+    # a request with a tolerance stops once d/(1-d) ||x_k - x_{k-1}||_1 <= tol
+    # (or its residual has stopped shrinking), so each served column lies
+    # within tol of the fixed point, plus the error of its storage type
+    graphs = [g for g, _ in pool]
+    srv = gpr.Server(graphs, budget_bytes=8 << 30)
+    rng = np.random.default_rng(int(tol * 1e9) + dt)
+    for gi in (1, 2):
+        seeds = rng.integers(0, graphs[gi].n, 5).astype(np.int32)
+        t = srv.submit(gi, seeds, damping=0.82, tol=tol, max_iters=1000, dtype=dt)
+        r = wait(srv, t)
+        assert r.status == gpr.OK
+        x = result(torch, srv, t, r)
+        for k, s in enumerate(seeds):
+            xstar, _ = oracle.ppr(pool[gi][1], int(s), 0.82, 300)
+            err = l1(x[:, k], xstar)
+            assert err <= tol + storage, (gi, int(s), err)
+        srv.release(t)
+    srv.close()
+
+
 def test_alone_equals_mix_and_admission_mid_flight(torch, pool):
     graphs = [g for g, _ in pool]
     srv = gpr.Server(graphs, budget_bytes=8 << 30, steps_per_tick=4)
