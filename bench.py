@@ -232,6 +232,27 @@ def sum_over_ranks(world, v):
     return float(t.item())
 
 
+def shard_indices(count, world, rank):
+    """The independent units (graphs of the batch, graphs of the serving
+    pool) this rank owns: index % world == rank."""
+    return [i for i in range(count) if i % world == rank]
+
+
+def gather_lists(world, items):
+    """Every rank's list, concatenated in rank order (gloo object gather)."""
+    if world == 1:
+        return list(items)
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, list(items))
+    return [x for part in out for x in part]
+
+
+def gpu_index_of(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    return vis.split(",")[local] if vis else str(local)
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -261,6 +282,44 @@ def run_reference(args, world, rank):
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def headline_accuracy(spec, x):
+    """L1 and max relative error of the ranks x (caller ids) against the FP64
+    oracle: for the scale-25 workload, the oracle's stored x_100 (written by
+    tests/golden/make_rmat25_oracle.py; the whole vector when its file is
+    present, else its committed sample of 2,048 nodes, where the L1 relative
+    to the sampled mass estimates the full L1); for the G(n, m) workload, an
+    oracle run here.  None for the others."""
+    import numpy as np
+    x = np.asarray(x, np.float64)
+    if spec.name == "rmat-s25-ef32":
+        js = os.path.join(ROOT, "tests", "golden", f"{spec.name}_pagerank{spec.iters}.json")
+        if not os.path.exists(js):
+            return {"vs": "oracle summary not written", "l1": None, "max_rel": None}
+        meta = json.load(open(js))
+        path = os.path.join(ROOT, meta["vector_file"])
+        if os.path.exists(path):
+            raw = open(path, "rb").read()
+            if hashlib.sha256(raw).hexdigest() == meta["vector_sha256"]:
+                ref = np.frombuffer(raw, np.float64)
+                nz = ref > 0
+                return {"vs": "FP64 oracle x_100, whole vector", "l1": float(np.abs(x - ref).sum()),
+                        "max_rel": float(np.max(np.abs(x[nz] - ref[nz]) / ref[nz]))}
+        nodes = np.asarray(meta["sample_nodes"], np.int64)
+        ref = np.asarray(meta["sample_x"], np.float64)
+        got = x[nodes]
+        return {"vs": f"FP64 oracle x_100 at {len(nodes)} sampled nodes (L1 relative to the sampled mass)",
+                "l1": float(np.abs(got - ref).sum() / ref.sum()),
+                "max_rel": float(np.max(np.abs(got - ref) / ref))}
+    if spec.kind == "er":
+        import gen
+        import oracle
+        src, dst = gen.er_gnm(spec.n, spec.m, spec.seed)
+        ref = oracle.pagerank(oracle.build_csc(spec.n, src, dst), DAMPING, spec.iters)
+        return {"vs": "FP64 oracle, whole vector", "l1": float(np.abs(x - ref).sum()),
+                "max_rel": float(np.max(np.abs(x - ref) / ref))}
+    return None
 
 
 def make_coo_device(torch, spec):
@@ -384,6 +443,7 @@ def run_gpr(args, world, rank, local):
 
     if rank != 0:
         return
+    accuracy = headline_accuracy(spec, out.cpu().numpy())
     line = {
         "metric": "PageRank GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step_max, "higher_is_better": True, "scaling": "weak",
@@ -411,6 +471,7 @@ def run_gpr(args, world, rank, local):
         "clocks": clk.summary(),
         "gpu_launches": launches,
         "wall_s_timed": wall,
+        "accuracy": accuracy,
     }
     if e2e:
         line["e2e"] = e2e
@@ -431,13 +492,27 @@ def build_graph_dev(torch, gpr, spec, stream=None):
     return gpr.graph_build(s, d, spec.n)
 
 
+def ppr_bytes_per_step(n, m, dt_name, cols=64):
+    """Modelled bytes of one personalised-PageRank step of a 64-column job:
+    indices 4m, offsets 4(n+1), the rank state read and written 8 per row and
+    column, the contributions written and gathered once per edge and column
+    (s bytes each: 4 FP32, 2 FP16 / BF16), and with BF16 deltas the running
+    and sent sums read and written (16 per row and column)."""
+    sz = 4 if dt_name == "fp32" else 2
+    extra = 16 if dt_name == "bf16" else 0
+    return 4 * m + 4 * (n + 1) + cols * n * (8 + sz + extra) + cols * m * sz
+
+
 def run_batched(args, world, rank, local):
     """Config: 4,096 R-MAT graphs (n log-uniform in [1e3, 2e5], mean out-degree
     uniform in [4, 32]), 64 personalised-PageRank seeds each, damping 0.85,
-    50 steps, one persistent launch per storage type.  Baselines on the same
-    GPU: one solve per call (ppr_batch with one seed) and plain PageRank
-    (pagerank, one vector) per solve, each timed on a sample and expressed in
-    solves/s.  Accuracy: sampled columns against the FP64 oracle."""
+    50 steps, one persistent launch per storage type.  Under torchrun the
+    graphs are shared out (graph g on rank g % world, no data-path
+    collective); value = all ranks' solves over the slowest rank's time.
+    Baselines on the same GPU: one solve per call (ppr_batch with one seed)
+    and plain PageRank (pagerank, one vector) per solve, each timed on a
+    sample and expressed in solves/s.  Accuracy: sampled columns against the
+    FP64 oracle."""
     import numpy as np
     import torch
 
@@ -447,40 +522,49 @@ def run_batched(args, world, rank, local):
     from gen import workloads
 
     torch.cuda.set_device(local)
-    specs = workloads.batched_specs(args.graphs)
+    specs_all = workloads.batched_specs(args.graphs)
+    mine = shard_indices(len(specs_all), world, rank)
+    specs = [specs_all[g] for g in mine]
     t0 = time.perf_counter()
     graphs = [build_graph_dev(torch, gpr, sp) for sp in specs]
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
-    seeds = [gen.seed_nodes(sp.n, 64, workloads.batched_seed_base(g)) for g, sp in enumerate(specs)]
+    seeds = [gen.seed_nodes(sp.n, 64, workloads.batched_seed_base(g)) for g, sp in zip(mine, specs)]
     outs = [torch.empty((sp.n, 64), dtype=torch.float32, device="cuda") for sp in specs]
     reqs = [(g, s, 0.85, o) for g, s, o in zip(graphs, seeds, outs)]
     iters = 50
-    n_solves = 64 * len(specs)
-    refs = []  # (graph, column, oracle x) on every 256th graph
-    for g in range(0, len(specs), 256):
-        sp = specs[g]
+    n_solves_all = 64 * len(specs_all)
+    refs = []  # (local graph, column, oracle x) on about every 256th graph of the batch
+    for i in range(0, len(specs), max(1, 256 // world)):
+        sp = specs[i]
         src, dst = gen.rmat_coo(sp.n, sp.m, seed=sp.seed)
         csc = oracle.build_csc(sp.n, src, dst)
         for k in (0, 21, 42, 63):
-            refs.append((g, k, oracle.ppr(csc, int(seeds[g][k]), 0.85, iters)[0]))
+            refs.append((i, k, oracle.ppr(csc, int(seeds[i][k]), 0.85, iters)[0]))
     dts = {"fp32": gpr.FP32, "bf16": gpr.BF16, "fp16": gpr.FP16}
     res = {}
     stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peak()
+    launches0 = gpr.lib().gpr_kernel_launches()
     for name in args.dtypes.split(","):
         dt = dts[name]
         for _ in range(max(1, args.warmup)):
             gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
         torch.cuda.synchronize()
         times = []
-        for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        ms = statistics.median(times)
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(gpu_index_of(local)) as clk:
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+        barrier(world)
+        ms_rank = statistics.median(times)
+        ms = max_over_ranks(world, ms_rank)
         # accuracy on sampled graphs, 4 seeds each, against the FP64 oracle
         l1s, mrs = [], []
         for g, k, xr in refs:
@@ -488,8 +572,20 @@ def run_batched(args, world, rank, local):
             l1s.append(float(np.abs(x - xr).sum()))
             nz = xr > 0
             mrs.append(float(np.max(np.abs(x[nz] - xr[nz]) / xr[nz])) if nz.any() else 0.0)
-        res[name] = {"ms": ms, "solves_per_s": n_solves / (ms * 1e-3), "l1_max": max(l1s),
-                     "l1_mean": statistics.mean(l1s), "max_rel_err_max": max(mrs), "sampled_columns": len(l1s)}
+        l1s, mrs = gather_lists(world, l1s), gather_lists(world, mrs)
+        bytes_rank = sum(ppr_bytes_per_step(sp.n, g.m, name) for sp, g in zip(specs, graphs)) * iters
+        achieved = bytes_rank / (ms_rank * 1e-3) / 1e9
+        res[name] = {"ms": ms, "solves_per_s": n_solves_all / (ms * 1e-3), "l1_max": max(l1s),
+                     "l1_mean": statistics.mean(l1s), "max_rel_err_max": max(mrs), "sampled_columns": len(l1s),
+                     "clocks": clk.summary(),
+                     "roofline": {"kernel": "ppr_kernel (one persistent cluster launch over every job)",
+                                  "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "peak_source": peak_kind,
+                                  "bytes_model": "per step and job: 4m + 4(n+1) + 64n(8 + s [+16 BF16]) + 64ms, "
+                                                 "s = stored bytes per contribution; gathers counted once "
+                                                 "per edge and column (cache hits count as bytes)",
+                                  "traffic": None}}
+    launches = gpr.lib().gpr_kernel_launches() - launches0
     # baselines: one solve at a time, on a sample of (graph, seed) pairs
     sample = list(range(0, len(specs), max(1, len(specs) // 64)))
     one_out = [torch.empty((specs[g].n, 1), dtype=torch.float32, device="cuda") for g in sample]
@@ -500,7 +596,7 @@ def run_batched(args, world, rank, local):
     for i, g in enumerate(sample):
         gpr.ppr_batch([(graphs[g], seeds[g][:1], 0.85, one_out[i])], max_iters=iters)
     torch.cuda.synchronize()
-    one_ppr = len(sample) / (time.perf_counter() - t0)
+    one_ppr = sum_over_ranks(world, len(sample) / (time.perf_counter() - t0))
     pr_out = [torch.empty(specs[g].n, dtype=torch.float32, device="cuda") for g in sample]
     for i, g in enumerate(sample[:4]):
         gpr.pagerank(graphs[g], pr_out[i], iters=iters)
@@ -509,18 +605,26 @@ def run_batched(args, world, rank, local):
     for i, g in enumerate(sample):
         gpr.pagerank(graphs[g], pr_out[i], iters=iters)
     torch.cuda.synchronize()
-    one_pr = len(sample) / (time.perf_counter() - t0)
-    sum_n = sum(sp.n for sp in specs)
-    sum_m = sum(g.m for g in graphs)
+    one_pr = sum_over_ranks(world, len(sample) / (time.perf_counter() - t0))
+    sum_n = sum(sp.n for sp in specs_all)
+    sum_m = int(sum_over_ranks(world, float(sum(g.m for g in graphs))))
     best = res.get("fp32") or next(iter(res.values()))
     line = {
         "metric": "PPR solves/s (batched)", "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batched-ppr-4096x64", "graphs": len(specs), "seeds_per_graph": 64, "iters": iters,
-                   "damping": 0.85, "sum_n": sum_n, "sum_m": sum_m, "sum_m_raw": sum(sp.m for sp in specs),
-                   "step": "one ppr_batch call: every column of every graph, one persistent launch"},
+        "config": {"workload": "batched-ppr-4096x64", "graphs": len(specs_all), "seeds_per_graph": 64,
+                   "iters": iters, "damping": 0.85, "sum_n": sum_n, "sum_m": sum_m,
+                   "sum_m_raw": sum(sp.m for sp in specs_all),
+                   "step": "one ppr_batch call: every column of every graph (of this rank), one persistent launch",
+                   "parallelism": f"graphs sharded over {world} rank(s), g % world",
+                   "l2": "per-job state 0.3-77 MB; the batch's working set far above L2"},
         "by_dtype": res,
+        "clocks": best["clocks"],
+        "roofline": best["roofline"],
+        "accuracy": {"l1_max": best["l1_max"], "max_rel": best["max_rel_err_max"], "vs": "FP64 oracle, sampled columns",
+                     "columns": best["sampled_columns"]},
+        "gpu_launches": launches,
         "one_at_a_time": {"ppr_single_seed_solves_per_s": one_ppr, "plain_pagerank_solves_per_s": one_pr,
                           "sample_pairs": len(sample),
                           "speedup_vs_single_seed": best["solves_per_s"] / one_ppr,
@@ -531,13 +635,15 @@ def run_batched(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def serve_window(torch, gpr, graphs, specs, rate, warm, window, budget, seed=7):
+def serve_window(torch, gpr, graphs, specs, rate, warm, window, budget, seed=7, world=1, rank=0, bf16_all=True):
     """One run of the server on a Poisson trace at `rate` requests/s:
     `warm` seconds of warm-up, then a `window`-second measured window, then
-    up to 30 s to drain.  Returns (summary dict, completed-request steps)."""
+    up to 30 s to drain.  `graphs` are this rank's pool graphs (pool graph j
+    on rank j % world); the rank serves the requests of the trace that name
+    them.  Returns (raw results of this rank, completed-request steps)."""
     import threading
 
-    trace = workloads_trace(specs, rate, warm + window, seed)
+    trace = [q for q in workloads_trace(specs, rate, warm + window, seed) if q.graph % world == rank]
     srv = gpr.Server(graphs, budget_bytes=budget, max_queue=1 << 20)
     info = {}     # ticket -> (arrival s, seeds)
     done = {}     # ticket -> (latency ms, status, steps, completion s)
@@ -565,8 +671,11 @@ def serve_window(torch, gpr, graphs, specs, rate, warm, window, budget, seed=7):
         while i < len(trace) and trace[i].t_arrive <= now:
             q = trace[i]
             try:
-                t = srv.submit(q.graph, q.seeds, damping=q.damping, tol=q.tol, max_iters=1000,
-                               dtype=gpr.BF16 if q.bf16 else gpr.FP32)
+                # 16-bit contributions (BF16 error-feedback deltas) for the
+                # 1e-3 requests: all of them with bf16_all, else the trace's half
+                use_bf16 = q.bf16 or (bf16_all and q.tol >= 1e-3)
+                t = srv.submit(q.graph // world, q.seeds, damping=q.damping, tol=q.tol, max_iters=1000,
+                               dtype=gpr.BF16 if use_bf16 else gpr.FP32)
                 info[t] = (q.t_arrive, len(q.seeds))
                 tickets.append((t, q))
             except gpr.GprError as e:
@@ -583,20 +692,34 @@ def serve_window(torch, gpr, graphs, specs, rate, warm, window, budget, seed=7):
     st = srv.stats()
     srv.close()
     in_window = [t for t, (a, _) in info.items() if warm <= a < warm + window]
-    lat = sorted(done[t][0] for t in in_window if t in done and done[t][1] == gpr.OK)
+    lat = [done[t][0] for t in in_window if t in done and done[t][1] == gpr.OK]
     unfinished = sum(1 for t in in_window if t not in done)
     solves = sum(info[t][1] for t, d in done.items() if d[1] == gpr.OK and warm <= d[3] < warm + window)
     offered = sum(info[t][1] for t in in_window)
+    raw = {"lat": lat, "unfinished": unfinished, "solves": solves, "offered": offered,
+           "arrived": len(in_window), "rejected": rejected, "server": st}
+    steps = [(q, done[t][2]) for t, q in tickets if t in done and done[t][1] == gpr.OK]
+    return raw, steps
+
+
+def merge_serve(world, raw, rate, window):
+    """All ranks' results of one serving run: latency percentiles over every
+    rank's requests, solves and offered work summed."""
+    lat = sorted(gather_lists(world, raw["lat"]))
 
     def pct(a, q):
         return a[min(len(a) - 1, int(q * len(a)))] if a else None
 
-    out = {"rate_req_per_s": rate, "window_s": window, "solves_per_s": solves / window,
-           "offered_solves_per_s": offered / window, "arrived_in_window": len(in_window),
-           "completed_in_window": len(lat), "unfinished_after_drain": unfinished,
-           "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99), "rejected": rejected, "server": st}
-    steps = [(q, done[t][2]) for t, q in tickets if t in done and done[t][1] == gpr.OK]
-    return out, steps
+    solves = sum_over_ranks(world, float(raw["solves"]))
+    offered = sum_over_ranks(world, float(raw["offered"]))
+    return {"rate_req_per_s": rate, "window_s": window, "solves_per_s": solves / window,
+            "offered_solves_per_s": offered / window,
+            "arrived_in_window": int(sum_over_ranks(world, float(raw["arrived"]))),
+            "completed_in_window": len(lat),
+            "unfinished_after_drain": int(sum_over_ranks(world, float(raw["unfinished"]))),
+            "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99),
+            "rejected": {k: int(sum_over_ranks(world, float(v))) for k, v in raw["rejected"].items()},
+            "server_rank0": raw["server"]}
 
 
 def workloads_trace(specs, rate, duration, seed):
@@ -607,44 +730,86 @@ def workloads_trace(specs, rate, duration, seed):
 def run_serve(args, world, rank, local):
     """Config: a resident pool of 256 R-MAT graphs (scales 14-22, edge factor
     16); Poisson arrivals at 2,000 requests/s, each naming a graph, 1-64 seeds,
-    damping in [0.80, 0.90] and tolerance 1e-6 or 1e-3 (BF16 contributions for
-    half of the 1e-3 requests); admission under a 40 GB device budget that
-    includes the pool.  Reports submit-to-completion p50/p99 over the requests
-    that arrived in the measured window, solves/s completed in the window (one
-    seed = one solve), rejections and the backlog.  The offered load is far
-    above capacity, so the same measurement is repeated at the lower rates of
-    --stable-rates: the highest rate whose window drains (no request left
-    unfinished, completions keeping up with arrivals) is the maximum stable
-    load, with its latencies.  Baseline on the same GPU: one-at-a-time plain
-    PageRank, one call per solve with the step count the request needed, on a
-    sample of the trace."""
+    damping in [0.80, 0.90] and tolerance 1e-6 (FP32 contributions) or 1e-3
+    (BF16 contributions, sent as error-feedback deltas); admission under a
+    40 GB device budget per GPU that includes the pool.  Under torchrun the
+    pool is shared out (graph j on rank j % world, with the requests that name
+    it; no data-path collective).  Reports submit-to-completion p50/p99 over
+    the requests that arrived in the measured window, solves/s completed in
+    the window (one seed = one solve), rejections and the backlog, with the
+    clocks seen during the window.  The offered load is far above capacity,
+    so the same measurement is repeated at the lower rates of --stable-rates:
+    the highest rate whose window drains (no request left unfinished,
+    completions keeping up with arrivals) is the maximum stable load, with its
+    latencies.  Baseline on the same GPU: one-at-a-time plain PageRank, one
+    call per solve with the step count the request needed, on a sample of the
+    trace."""
+    import numpy as np
     import torch
 
+    import gen
+    import oracle
     import paper_1606_07550_gb300 as gpr
     from gen import workloads
 
     torch.cuda.set_device(local)
     specs = workloads.serving_pool_specs(args.pool)
+    mine = shard_indices(len(specs), world, rank)
     t0 = time.perf_counter()
-    graphs = [build_graph_dev(torch, gpr, sp) for sp in specs]
+    graphs = [build_graph_dev(torch, gpr, specs[j]) for j in mine]
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     t_setup = time.perf_counter() - t0
     budget = 40 << 30
-    main_run, steps = serve_window(torch, gpr, graphs, specs, args.serve_rate, args.serve_warmup,
-                                   args.serve_seconds, budget)
+    launches0 = gpr.lib().gpr_kernel_launches()
+    barrier(world)
+    with ClockSampler(gpu_index_of(local)) as clk:
+        raw, steps = serve_window(torch, gpr, graphs, specs, args.serve_rate, args.serve_warmup,
+                                  args.serve_seconds, budget, world=world, rank=rank)
+    barrier(world)
+    launches = gpr.lib().gpr_kernel_launches() - launches0
+    main_run = merge_serve(world, raw, args.serve_rate, args.serve_seconds)
     sweep = []
     for r in [float(x) for x in args.stable_rates.split(",") if x]:
-        res, _ = serve_window(torch, gpr, graphs, specs, r, args.serve_warmup, args.stable_seconds, budget)
+        with ClockSampler(gpu_index_of(local)) as sclk:
+            rr, _ = serve_window(torch, gpr, graphs, specs, r, args.serve_warmup, args.stable_seconds, budget,
+                                 world=world, rank=rank)
+        res = merge_serve(world, rr, r, args.stable_seconds)
         res["stable"] = res["unfinished_after_drain"] == 0 and res["solves_per_s"] >= 0.9 * res[
             "offered_solves_per_s"]
+        res["clocks"] = sclk.summary()
         sweep.append(res)
     stable = [r for r in sweep if r["stable"]]
     max_stable = max(stable, key=lambda r: r["rate_req_per_s"]) if stable else None
 
+    # accuracy of served columns against the FP64 oracle's fixed point, on
+    # this rank's smallest pool graphs: FP32 at tol 1e-6, BF16 at tol 1e-3
+    acc = []
+    srv = gpr.Server(graphs, budget_bytes=budget)
+    small = [i for i, j in enumerate(mine) if specs[j].n <= (1 << 16)][:2]
+    for li in small:
+        sp = specs[mine[li]]
+        src, dst = gen.rmat_coo(sp.n, sp.m, seed=sp.seed)
+        csc = oracle.build_csc(sp.n, src, dst)
+        sd = gen.seed_nodes(sp.n, 4, 900 + mine[li])
+        for dt, tol in ((gpr.FP32, 1e-6), (gpr.BF16, 1e-3)):
+            t = srv.submit(li, sd, damping=0.85, tol=tol, max_iters=1000, dtype=dt)
+            r = None
+            while r is None:
+                r = srv.poll(t, 100_000)
+            o = torch.empty(r.n * r.num_seeds, device="cuda")
+            srv.fetch(t, o)
+            x = o.cpu().numpy().reshape(r.n, r.num_seeds)
+            srv.release(t)
+            for k, s_ in enumerate(sd):
+                xs, _ = oracle.ppr(csc, int(s_), 0.85, 400)
+                acc.append((int(dt), tol, float(np.abs(x[:, k] - xs).sum())))
+    srv.close()
+    acc = gather_lists(world, acc)
+
     # baseline: one-at-a-time plain PageRank, one call per solve, each with
     # the step count the served request needed; sampled requests of the
-    # trace, at most ~10 s of GPU time
+    # trace, at most ~10 s of GPU time per rank
     sample = steps[:: max(1, len(steps) // 200)]
     # the library tunes the step's schedule once per graph shape: do that
     # before the timed baseline
@@ -658,36 +823,47 @@ def run_serve(args, world, rank, local):
     b0 = time.perf_counter()
     nb = 0
     for q, k in sample:
-        o = torch.empty(graphs[q.graph].n, dtype=torch.float32, device="cuda")
+        o = torch.empty(graphs[q.graph // world].n, dtype=torch.float32, device="cuda")
         for _ in q.seeds:
-            gpr.pagerank(graphs[q.graph], o, damping=q.damping, iters=max(1, k))
+            gpr.pagerank(graphs[q.graph // world], o, damping=q.damping, iters=max(1, k))
             nb += 1
         torch.cuda.synchronize()
         if time.perf_counter() - b0 > 10.0:
             break
-    base = nb / (time.perf_counter() - b0) if nb else None
+    base_rank = nb / (time.perf_counter() - b0) if nb else 0.0
+    base = sum_over_ranks(world, base_rank)
+    nb_all = int(sum_over_ranks(world, float(nb)))
     value = main_run["solves_per_s"]
     line = {
         "metric": "PPR solves/s (served)", "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": args.serve_seconds * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
         "config": {"workload": "serving-pool256-poisson", "pool_graphs": len(specs),
                    "pool_raw_edges": sum(sp.m for sp in specs), "rate_req_per_s": args.serve_rate,
-                   "warmup_s": args.serve_warmup, "window_s": args.serve_seconds, "budget_bytes": budget,
-                   "steps_per_tick": 8, "edges_per_part": 1 << 18, "max_iters": 1000},
+                   "warmup_s": args.serve_warmup, "window_s": args.serve_seconds, "budget_bytes_per_gpu": budget,
+                   "steps_per_tick": 8, "edges_per_part": 1 << 18, "max_iters": 1000,
+                   "storage": "FP32 contributions for tol 1e-6 requests, BF16 error-feedback deltas for tol 1e-3",
+                   "parallelism": f"pool sharded over {world} rank(s), graph j on rank j % world"},
         "latency_ms": {"p50": main_run["p50_ms"], "p99": main_run["p99_ms"],
                        "completed": main_run["completed_in_window"],
                        "arrived_in_window": main_run["arrived_in_window"],
                        "unfinished_after_drain": main_run["unfinished_after_drain"]},
         "offered_solves_per_s": main_run["offered_solves_per_s"],
         "rejected": main_run["rejected"],
-        "server": main_run["server"],
+        "server": main_run["server_rank0"],
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
         "stable_load_sweep": sweep,
         "max_stable_load": ({"rate_req_per_s": max_stable["rate_req_per_s"],
                              "solves_per_s": max_stable["solves_per_s"], "p50_ms": max_stable["p50_ms"],
                              "p99_ms": max_stable["p99_ms"]} if max_stable else None),
-        "one_at_a_time_solves_per_s": base, "baseline_sample_solves": nb,
+        "accuracy": {"vs": "FP64 oracle fixed point (400 steps), served requests on small pool graphs",
+                     "columns": [{"dtype": "bf16" if d == int(gpr.BF16) else "fp32", "tol": t, "l1": e}
+                                 for d, t, e in acc],
+                     "max_l1_minus_tol": max((e - t for _, t, e in acc), default=None)},
+        "one_at_a_time_solves_per_s": base, "baseline_sample_solves": nb_all,
         "speedup_vs_one_at_a_time": value / base if base else None,
+        "speedup_at_max_stable_load": (max_stable["solves_per_s"] / base if max_stable and base else None),
         "setup_s": t_setup,
     }
     if rank == 0:

@@ -498,7 +498,19 @@ class Server:
 def pagerank_csc_noalloc(col_ptr, row_idx, outdeg, n: int, out, damping: float = 0.85, iters: int = 50,
                          stream=None):
     """PageRank on a caller-held device CSC without any device allocation
-    (int32 CUDA tensors col_ptr, row_idx, outdeg; float32 CUDA tensor out)."""
+    (int32 CUDA tensors col_ptr, row_idx, outdeg; float32 CUDA tensor out;
+    row_idx holds col_ptr[n] entries).  The tensors' types and the sizes that
+    n fixes are checked here, before the library reads or writes them."""
+    import torch
+    for name, t in (("col_ptr", col_ptr), ("row_idx", row_idx), ("outdeg", outdeg)):
+        if t.dtype != torch.int32:
+            raise ValueError(f"pagerank_csc_noalloc: {name} must be int32, not {t.dtype}")
+    if out.dtype != torch.float32:
+        raise ValueError(f"pagerank_csc_noalloc: out must be float32, not {out.dtype}")
+    if n < 1:
+        raise ValueError("pagerank_csc_noalloc: n must be at least 1")
+    if col_ptr.numel() < n + 1 or outdeg.numel() < n or out.numel() < n:
+        raise ValueError("pagerank_csc_noalloc: col_ptr needs n + 1 entries, outdeg and out n each")
     for t in (col_ptr, row_idx, outdeg, out):
         if not t.is_cuda or not t.is_contiguous():
             raise ValueError("pagerank_csc_noalloc takes contiguous CUDA tensors")

@@ -33,9 +33,10 @@ struct NoallocState {
   unsigned int pad;
 };
 
-// c[2][kNoallocMaxNodes] floats | x[kNoallocMaxNodes] floats | partials | state
+// c[2][kNoallocMaxNodes] floats | x[kNoallocMaxNodes] floats | partials (mass,
+// dangling mass per block) | state
 constexpr size_t kVecBytes = (size_t)kNoallocMaxNodes * 4;
-constexpr size_t kPartialBytes = (size_t)kNoallocMaxBlocks * 3 * sizeof(double);
+constexpr size_t kPartialBytes = (size_t)kNoallocMaxBlocks * 2 * sizeof(double);
 constexpr size_t kScratchBytes = 3 * kVecBytes + kPartialBytes + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -47,16 +48,18 @@ __device__ __forceinline__ float nz_warp_sum(float v) {
 
 // One step (mode 1) or the initial vector (mode 0) with one warp per row;
 // the last block to finish folds the block partials in index order and
-// writes the next step's coefficients.
+// writes the next step's coefficients.  The mass and dangling-mass partials
+// are summed in FP64 throughout (per warp, per block, then across blocks),
+// as the FP64 reductions of the main PageRank step are.
 __global__ void __launch_bounds__(kNoallocThreads) noalloc_step_kernel(
     const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, const int32_t* __restrict__ outdeg,
-    int32_t n, int mode, const float* __restrict__ c_in, const float* __restrict__ x_in, float* __restrict__ c_out,
-    float* __restrict__ x_out, double* __restrict__ partials, NoallocState* __restrict__ st) {
-  __shared__ double s[3][kNoallocThreads / 32];
+    int32_t n, int mode, const float* __restrict__ c_in, float* __restrict__ c_out, float* __restrict__ x_out,
+    double* __restrict__ partials, NoallocState* __restrict__ st) {
+  __shared__ double s[2][kNoallocThreads / 32];
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float A = st->coefA, B = st->coefB;
-  float mass = 0.f, dang = 0.f, res = 0.f;
+  double mass = 0.0, dang = 0.0;  // lane 0 of each warp finishes its rows
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < n; r += nwarps) {
@@ -72,30 +75,23 @@ __global__ void __launch_bounds__(kNoallocThreads) noalloc_step_kernel(
       const int32_t od = outdeg[r];
       x_out[r] = xs;
       c_out[r] = od > 0 ? xs / (float)od : 0.f;
-      mass += xs;
-      if (od == 0) dang += xs;
-      if (mode != 0) res += fabsf(xs - x_in[r]);
+      mass += (double)xs;
+      if (od == 0) dang += (double)xs;
     }
   }
-  mass = nz_warp_sum(mass);
-  dang = nz_warp_sum(dang);
-  res = nz_warp_sum(res);
   if (lane == 0) {
     s[0][w] = mass;
     s[1][w] = dang;
-    s[2][w] = res;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
+    double a = 0, b = 0;
     for (int i = 0; i < kNoallocThreads / 32; ++i) {
       a += s[0][i];
       b += s[1][i];
-      c += s[2][i];
     }
-    partials[3 * blockIdx.x] = a;
-    partials[3 * blockIdx.x + 1] = b;
-    partials[3 * blockIdx.x + 2] = c;
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
     __threadfence();
     s_last = atomicAdd(&st->arrive, 1u) == gridDim.x - 1;
   }
@@ -104,8 +100,8 @@ __global__ void __launch_bounds__(kNoallocThreads) noalloc_step_kernel(
   __threadfence();
   double total = 0, dsum = 0;
   for (unsigned int i = 0; i < gridDim.x; ++i) {
-    total += __ldcg(partials + 3 * i);
-    dsum += __ldcg(partials + 3 * i + 1);
+    total += __ldcg(partials + 2 * i);
+    dsum += __ldcg(partials + 2 * i + 1);
   }
   st->coefA = (float)(st->d / total);
   st->coefB = (float)((1.0 - st->d) / st->n + st->d * dsum / (st->n * total));
@@ -180,12 +176,12 @@ extern "C" gpr_status pagerank_csc_noalloc(const int32_t* col_ptr, const int32_t
       1, std::min<int64_t>({((int64_t)n * 32 + kNoallocThreads - 1) / kNoallocThreads, (int64_t)num_sms() * 8,
                             (int64_t)kNoallocMaxBlocks}));
   noalloc_reset_kernel<<<1, 1, 0, s>>>(st, damping, n);
-  noalloc_step_kernel<<<grid, kNoallocThreads, 0, s>>>(col_ptr, row_idx, outdeg, n, 0, c[1], x[1], c[0], x[0],
-                                                       partials, st);
+  noalloc_step_kernel<<<grid, kNoallocThreads, 0, s>>>(col_ptr, row_idx, outdeg, n, 0, c[1], c[0], x[0], partials,
+                                                       st);
   int launches = 2;
   for (int32_t it = 0; it < iters; ++it) {
     const int a = it & 1, bb = a ^ 1;
-    noalloc_step_kernel<<<grid, kNoallocThreads, 0, s>>>(col_ptr, row_idx, outdeg, n, 1, c[a], x[a], c[bb], x[bb],
+    noalloc_step_kernel<<<grid, kNoallocThreads, 0, s>>>(col_ptr, row_idx, outdeg, n, 1, c[a], c[bb], x[bb],
                                                          partials, st);
     ++launches;
   }
