@@ -93,9 +93,11 @@ __device__ __forceinline__ void st_one<__half>(__half* p, float a) {
 // Sum of the contribution rows of the sources of edges [e0, e1), two columns
 // per lane.  Warp-cooperative: all lanes call it with the same range; each
 // group of 32 indices is loaded once, coalesced, and broadcast by shuffles.
+// A lane whose two columns are not running (on = false) loads nothing: the
+// sectors of a row's dead columns are then not fetched at all.
 template <typename T>
 __device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx, const T* __restrict__ C,
-                                             int32_t e0, int32_t e1, int lane) {
+                                             int32_t e0, int32_t e1, int lane, bool on = true) {
   float ax = 0.f, ay = 0.f;
   for (int32_t e = e0; e < e1; e += 32) {
     const int32_t idx = (e + lane < e1) ? __ldcs(row_idx + e + lane) : 0;
@@ -107,7 +109,7 @@ __device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int32_t u = __shfl_sync(0xffffffffu, idx, (j + q) & 31);
-        v[q] = (j + q < cnt) ? ld_pair(C + (int64_t)u * kPprCols + 2 * lane) : make_float2(0.f, 0.f);
+        v[q] = (on && j + q < cnt) ? ld_pair(C + (int64_t)u * kPprCols + 2 * lane) : make_float2(0.f, 0.f);
       }
       ax += ((v[0].x + v[1].x) + (v[2].x + v[3].x)) + ((v[4].x + v[5].x) + (v[6].x + v[7].x));
       ay += ((v[0].y + v[1].y) + (v[2].y + v[3].y)) + ((v[4].y + v[5].y) + (v[6].y + v[7].y));
@@ -361,13 +363,15 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       // light rows: one warp per row, round-robin (neighbouring rows share
       // sources, so warps that walk them together share cache lines)
+      // (a lane whose two columns are not running reads and writes nothing)
+      const bool on = c.l0 || c.l1;
       for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
-        const float2 xo = ld_state(X, p, lane);
-        const float4 ys = ld_ys(YS, p, lane);
-        const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
-        finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
+        const float2 xo = on ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
+        const float4 ys = on ? ld_ys(YS, p, lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 y = gather_row(row_idx, Cin, e0, e1, lane, on);
+        if (on) finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
       }
       // long rows: the whole block, fixed-order combine
       for (int32_t hi = h0; hi < h1; ++hi) {
@@ -375,7 +379,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         const int32_t per = (((e1 - e0) + kPprWarps - 1) / kPprWarps + 31) & ~31;
         const int32_t a = min(e1, e0 + warp * per), b = min(e1, a + per);
-        const float2 y = gather_row(row_idx, Cin, a, b, lane);
+        const float2 y = gather_row(row_idx, Cin, a, b, lane, on);
         s_heavy[warp][2 * lane] = y.x;
         s_heavy[warp][2 * lane + 1] = y.y;
         __syncthreads();
@@ -385,8 +389,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
             yx += s_heavy[w][2 * lane];
             yy += s_heavy[w][2 * lane + 1];
           }
-          finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), ld_ys(YS, p, lane), c, X, YS, Cout, inv_deg,
-                         lane, acc);
+          if (on)
+            finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), ld_ys(YS, p, lane), c, X, YS, Cout,
+                           inv_deg, lane, acc);
         }
         __syncthreads();
       }
@@ -647,19 +652,22 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       const int32_t heavy_deg = S->heavy_deg;
       int32_t wr0, wr1;
       warp_rows(col_ptr, r0, r1, warp, wr0, wr1);
+      // (a lane whose two columns are not running reads and writes nothing:
+      // a part-filled slot moves only the sectors of its running columns)
+      const bool on = c.l0 || c.l1;
       for (int32_t p = wr0; p < wr1; ++p) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
-        const float2 xo = ld_state(X, p, lane);
-        const float4 ys = ld_ys(YS, p, lane);
-        const float2 y = gather_row(row_idx, Cin, e0, e1, lane);
-        finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
+        const float2 xo = on ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
+        const float4 ys = on ? ld_ys(YS, p, lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 y = gather_row(row_idx, Cin, e0, e1, lane, on);
+        if (on) finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
       }
       // long rows: their chunk sums (this step's chunk launch), in chunk
       // order, a warp per row
       const int32_t h0 = lower_bound_i32(S->heavy_rows, S->n_heavy, r0);
       const int32_t h1 = lower_bound_i32(S->heavy_rows, S->n_heavy, r1);
-      for (int32_t hi = h0 + warp; hi < h1; hi += kPprWarps) {
+      for (int32_t hi = h0 + warp; on && hi < h1; hi += kPprWarps) {
         const int32_t p = S->heavy_rows[hi];
         const int32_t sp = S->heavy_split0 + hi;
         float yx = 0.f, yy = 0.f;
@@ -704,8 +712,12 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_chunk_kernel(const SlotDes
     const SlotDesc* S = slots + item.slot;
     const T* __restrict__ Cin = (const T*)S->C[(S->parity + step - 1) & 1];
     const int32_t c_end = min(S->nchunks, (item.part + 1) * kChunksPerItem);
+    // columns running after the previous step (the step launch may still stop
+    // some of them; their sums then go unused)
+    const ColState* stp = S->st[(step - 1) & 1];
+    const bool on = stp[2 * lane].status == kColRunning || stp[2 * lane + 1].status == kColRunning;
     for (int32_t ch = item.part * kChunksPerItem + warp; ch < c_end; ch += kPprWarps) {
-      const float2 y = gather_row(S->row_idx, Cin, S->chunk_begin[ch], S->chunk_end[ch], lane);
+      const float2 y = gather_row(S->row_idx, Cin, S->chunk_begin[ch], S->chunk_end[ch], lane, on);
       reinterpret_cast<float2*>(S->chunk_sum + (int64_t)ch * kPprCols)[lane] = y;
     }
   }
