@@ -546,25 +546,40 @@ def run_batched(args, world, rank, local):
     stream = torch.cuda.current_stream()
     peak, peak_kind = measured_peak()
     launches0 = gpr.lib().gpr_kernel_launches()
+    def timed_runs(dt):
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return statistics.median(times)
+
     for name in args.dtypes.split(","):
         dt = dts[name]
+        # the autotuner: CTAs per cluster for each graph-size class
+        tuned = gpr.ppr_tune(reqs, dtype=dt, trial_steps=8)
         for _ in range(max(1, args.warmup)):
             gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
         torch.cuda.synchronize()
-        times = []
         barrier(world)
         torch.cuda.synchronize()
         with ClockSampler(gpu_index_of(local)) as clk:
-            for _ in range(args.steps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                times.append(e0.elapsed_time(e1))
+            ms_rank = timed_runs(dt)
         barrier(world)
-        ms_rank = statistics.median(times)
         ms = max_over_ranks(world, ms_rank)
+        # the same batch with the fixed shape (8 CTAs per cluster for every class)
+        os.environ["GPR_PPR_CLUSTER"] = "8"
+        try:
+            gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)
+            torch.cuda.synchronize()
+            ms8 = max_over_ranks(world, timed_runs(dt))
+        finally:
+            os.environ.pop("GPR_PPR_CLUSTER", None)
+        gpr.ppr_batch(reqs, max_iters=iters, dtype=dt)  # outputs of the tuned shapes for the accuracy check
+        torch.cuda.synchronize()
         # accuracy on sampled graphs, 4 seeds each, against the FP64 oracle
         l1s, mrs = [], []
         for g, k, xr in refs:
@@ -575,7 +590,10 @@ def run_batched(args, world, rank, local):
         l1s, mrs = gather_lists(world, l1s), gather_lists(world, mrs)
         bytes_rank = sum(ppr_bytes_per_step(sp.n, g.m, name) for sp, g in zip(specs, graphs)) * iters
         achieved = bytes_rank / (ms_rank * 1e-3) / 1e9
-        res[name] = {"ms": ms, "solves_per_s": n_solves_all / (ms * 1e-3), "l1_max": max(l1s),
+        res[name] = {"ms": ms, "solves_per_s": n_solves_all / (ms * 1e-3),
+                     "tuner": {"classes": tuned, "ms_fixed_8_cta_clusters": ms8,
+                               "speedup_vs_fixed_8_cta_clusters": ms8 / ms},
+                     "l1_max": max(l1s),
                      "l1_mean": statistics.mean(l1s), "max_rel_err_max": max(mrs), "sampled_columns": len(l1s),
                      "clocks": clk.summary(),
                      "roofline": {"kernel": "ppr_kernel (one persistent cluster launch over every job)",

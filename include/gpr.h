@@ -46,8 +46,11 @@ typedef enum {
  * bytes the pull step reads once per edge).  The rank vector x itself is
  * always FP32; accumulation is always FP32; the per-step mass,
  * dangling-mass and residual reductions are FP64.
- *   GPR_BF16: 8-bit significand.  pagerank rounds to nearest; ppr_batch
- *             rounds stochastically (deterministic counter-based bits).
+ *   GPR_BF16: 8-bit significand.  pagerank rounds to nearest.  ppr_batch
+ *             and the server send error-feedback deltas: a node keeps the
+ *             FP32 sum s of what it has sent and stores bf16(c - s) (round to
+ *             nearest), a row keeps the FP32 running sum of what it gathers,
+ *             so each step's rounding is corrected by the next.
  *   GPR_FP16: ppr_batch only: 11-bit significand, values stored times 2^10
  *             (a personalised column lies in [0, 1]). */
 typedef enum { GPR_FP32 = 0, GPR_BF16 = 1, GPR_FP16 = 2 } gpr_dtype;
@@ -300,6 +303,32 @@ typedef struct {
  * launched), GPR_ENOMEM, GPR_ECUDA. */
 gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
                      void* stream);
+
+/* ---- autotuner for the batched launch (no counterpart in the paper) -------
+ * ppr_batch groups its 64-column jobs by graph size, class k holding graphs
+ * with ceil(log2 n) <= log2n_max[k] (11, 13, 15, 17, then all larger), and
+ * runs each class as one persistent launch of thread-block clusters, each
+ * cluster one job at a time, its rows split among the cluster's CTAs.  The
+ * CTAs per cluster (1, 2, 4 or 8) of a (class, dt): ppr_tune times each on
+ * up to 64 of the class's jobs in `jobs` (trial_steps in [1, 1000] steps per
+ * trial; the jobs' outputs are overwritten) and keeps the fastest for later
+ * ppr_batch calls in this process; a class never tuned takes 4 CTAs (8 for
+ * ceil log2 n in 14..15, the choice measured on GB300 for R-MAT graphs).  The
+ * environment variable GPR_PPR_CLUSTER=1|2|4|8 forces one shape for every
+ * class.  A column's bits depend on its class's shape (the row split orders
+ * the FP64 partial sums), never on the other columns or jobs of a call.
+ * Synchronous.  out may be NULL. */
+typedef struct {
+  int32_t classes;         /* classes present in the jobs (entries below) */
+  int32_t log2n_max[5];    /* the class's largest ceil(log2 n) (31: unbounded) */
+  int32_t jobs[5];         /* 64-column jobs of the class */
+  int32_t cluster[5];      /* CTAs per cluster chosen */
+  double ms[5];            /* trial time with the chosen shape */
+  double ms_cluster8[5];   /* trial time with 8 CTAs per cluster */
+} gpr_ppr_tune_result;
+
+gpr_status ppr_tune(const gpr_ppr_job* jobs, int32_t num_jobs, gpr_dtype dt, int32_t trial_steps,
+                    gpr_ppr_tune_result* out, void* stream);
 
 /* ---- serving: continuous batching of personalised-PageRank requests ------
  * A server keeps a pool of graphs resident on the device and answers

@@ -122,6 +122,11 @@ class TuneResult(ctypes.Structure):
                 ("dense_sources", ctypes.c_int32)]
 
 
+class PprTuneResult(ctypes.Structure):
+    _fields_ = [("classes", ctypes.c_int32), ("log2n_max", ctypes.c_int32 * 5), ("jobs", ctypes.c_int32 * 5),
+                ("cluster", ctypes.c_int32 * 5), ("ms", ctypes.c_double * 5), ("ms_cluster8", ctypes.c_double * 5)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
                 ("dangling", ctypes.c_double), ("t_setup_ms", ctypes.c_double), ("t_iter_ms", ctypes.c_double),
@@ -160,6 +165,8 @@ def lib():
         L.pagerank_tune.argtypes = [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult), _VP]
         L.ppr_batch.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                 ctypes.c_int, _VP]
+        L.ppr_tune.argtypes = [ctypes.POINTER(PprJob), ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
+                               ctypes.POINTER(PprTuneResult), _VP]
         L.gpr_kernel_launches.restype = ctypes.c_int64
         L.serve_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, ctypes.POINTER(ServerConfig),
                                    ctypes.POINTER(_VP)]
@@ -174,7 +181,7 @@ def lib():
         L.pagerank_csc_noalloc.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _VP, _VP]
         L.pagerank_csc_noalloc.restype = ctypes.c_int
         for name in ("graph_build", "graph_free", "graph_info", "graph_export", "pagerank", "pagerank_tune", "hits",
-                     "eigen_centrality", "wcc", "graph_save", "graph_load", "graph_update", "ppr_batch",
+                     "eigen_centrality", "wcc", "graph_save", "graph_load", "graph_update", "ppr_batch", "ppr_tune",
                      "ppr_reverse_push", "ppr_target",
                      "serve_create", "serve_submit", "serve_poll", "serve_fetch", "serve_release", "serve_stats",
                      "serve_destroy", "serve_completed"):
@@ -403,13 +410,7 @@ def pagerank_tune(g: Graph, dtype: int = FP32, trial_steps: int = 5, stream=None
     return r
 
 
-def ppr_batch(requests, max_iters: int = 50, tol: float = 0.0, dtype: int = FP32, stream=None):
-    """Personalised PageRank for many (graph, seeds) requests in one launch.
-
-    requests: list of (graph, seeds, damping, out) with seeds an int sequence,
-    damping a float or a per-seed sequence, out a CUDA float32 tensor of shape
-    (n, len(seeds)) (node-major).  Returns [(iters, residual)] numpy arrays
-    per request."""
+def _ppr_jobs(requests):
     n_req = len(requests)
     arr = (PprJob * max(n_req, 1))()
     keep = []
@@ -426,8 +427,31 @@ def ppr_batch(requests, max_iters: int = 50, tol: float = 0.0, dtype: int = FP32
         arr[i] = PprJob(g.handle, k, seeds.ctypes.data, d.ctypes.data, out.data_ptr(), it.ctypes.data,
                         res.ctypes.data)
         results.append((it, res))
+    return arr, n_req, keep, results
+
+
+def ppr_batch(requests, max_iters: int = 50, tol: float = 0.0, dtype: int = FP32, stream=None):
+    """Personalised PageRank for many (graph, seeds) requests in one launch.
+
+    requests: list of (graph, seeds, damping, out) with seeds an int sequence,
+    damping a float or a per-seed sequence, out a CUDA float32 tensor of shape
+    (n, len(seeds)) (node-major).  Returns [(iters, residual)] numpy arrays
+    per request."""
+    arr, n_req, keep, results = _ppr_jobs(requests)
     _check(lib().ppr_batch(arr, n_req, max_iters, tol, dtype, _stream_ptr(stream)))
     return results
+
+
+def ppr_tune(requests, dtype: int = FP32, trial_steps: int = 8, stream=None):
+    """Times the cluster shapes of the batched launch for each graph-size
+    class of `requests` (as for ppr_batch; their outputs are overwritten) and
+    keeps the fastest.  Returns one dict per class: log2n_max, jobs, cluster,
+    ms, ms_cluster8."""
+    arr, n_req, keep, _ = _ppr_jobs(requests)
+    r = PprTuneResult()
+    _check(lib().ppr_tune(arr, n_req, dtype, trial_steps, ctypes.byref(r), _stream_ptr(stream)))
+    return [{"log2n_max": r.log2n_max[i], "jobs": r.jobs[i], "cluster": r.cluster[i], "ms": r.ms[i],
+             "ms_cluster8": r.ms_cluster8[i]} for i in range(r.classes)]
 
 
 class Server:

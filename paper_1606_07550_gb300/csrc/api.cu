@@ -19,6 +19,8 @@ gpr_status update_graph(gpr_graph* g, const int32_t* ins_src, const int32_t* ins
                         const int32_t* del_src, const int32_t* del_dst, int64_t n_del, int flags, cudaStream_t s);
 gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
                          cudaStream_t s);
+gpr_status run_ppr_tune(const gpr_ppr_job* jobs, int32_t num_jobs, gpr_dtype dt, int32_t trial_steps,
+                        gpr_ppr_tune_result* out, cudaStream_t s);
 
 gpr_status run_reverse_push(gpr_graph* g, int32_t target, double d, double r_max, double* p_out, double* r_out,
                             gpr_target_stats* st, int flags, cudaStream_t s);
@@ -308,39 +310,64 @@ gpr_status ppr_target(const gpr_graph* g, int32_t target, double damping, double
                         flags, (cudaStream_t)stream);
 }
 
-gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
-                     void* stream) {
-  clear_error();
+}  // extern "C"
+
+// Validation shared by ppr_batch and ppr_tune; `who` names the entry point.
+static gpr_status check_ppr_jobs(const char* who, const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters,
+                                 double tol, gpr_dtype dt) {
+
   if (num_jobs < 0 || (num_jobs > 0 && !jobs)) {
-    set_error("ppr_batch: bad job array");
+    set_error("%s: bad job array", who);
     return GPR_EINVAL;
   }
   if (max_iters < 0 || max_iters > (1 << 20) || !(tol >= 0.0)) {
-    set_error("ppr_batch: max_iters %d or tol %g out of range", (int)max_iters, tol);
+    set_error("%s: max_iters %d or tol %g out of range", who, (int)max_iters, tol);
     return GPR_EINVAL;
   }
   if (dt != GPR_FP32 && dt != GPR_BF16 && dt != GPR_FP16) {
-    set_error("ppr_batch: unknown dtype %d", (int)dt);
+    set_error("%s: unknown dtype %d", who, (int)dt);
     return GPR_EINVAL;
   }
   for (int32_t j = 0; j < num_jobs; ++j) {
     const gpr_ppr_job& q = jobs[j];
     if (!q.graph || q.num_seeds < 1 || !q.seeds || !q.damping || !q.x_out) {
-      set_error("ppr_batch: job %d: missing graph, seeds, damping or output, or num_seeds < 1", (int)j);
+      set_error("%s: job %d: missing graph, seeds, damping or output, or num_seeds < 1", who, (int)j);
       return GPR_EINVAL;
     }
     for (int32_t k = 0; k < q.num_seeds; ++k) {
       if (q.seeds[k] < 0 || q.seeds[k] >= q.graph->n) {
-        set_error("ppr_batch: job %d: seed %d outside [0, %d)", (int)j, (int)q.seeds[k], (int)q.graph->n);
+        set_error("%s: job %d: seed %d outside [0, %d)", who, (int)j, (int)q.seeds[k], (int)q.graph->n);
         return GPR_EINVAL;
       }
       if (!(q.damping[k] > 0.f && q.damping[k] < 1.f)) {
-        set_error("ppr_batch: job %d: damping %g outside (0, 1)", (int)j, (double)q.damping[k]);
+        set_error("%s: job %d: damping %g outside (0, 1)", who, (int)j, (double)q.damping[k]);
         return GPR_EINVAL;
       }
     }
   }
+  return GPR_OK;
+}
+
+extern "C" {
+
+gpr_status ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
+                     void* stream) {
+  clear_error();
+  const gpr_status st = check_ppr_jobs("ppr_batch", jobs, num_jobs, max_iters, tol, dt);
+  if (st != GPR_OK) return st;
   return run_ppr_batch(jobs, num_jobs, max_iters, tol, dt, (cudaStream_t)stream);
+}
+
+gpr_status ppr_tune(const gpr_ppr_job* jobs, int32_t num_jobs, gpr_dtype dt, int32_t trial_steps,
+                    gpr_ppr_tune_result* out, void* stream) {
+  clear_error();
+  if (trial_steps < 1 || trial_steps > 1000) {
+    set_error("ppr_tune: trial_steps %d outside [1, 1000]", (int)trial_steps);
+    return GPR_EINVAL;
+  }
+  const gpr_status st = check_ppr_jobs("ppr_tune", jobs, num_jobs, trial_steps, 0.0, dt);
+  if (st != GPR_OK) return st;
+  return run_ppr_tune(jobs, num_jobs, dt, trial_steps, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -36,6 +36,9 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <type_traits>
 #include <vector>
@@ -740,10 +743,6 @@ __global__ void part_bounds_kernel(const int32_t* __restrict__ col_ptr, int32_t 
 
 // ---- host side ----------------------------------------------------------------
 
-static int g_cluster_size = 8;
-
-int ppr_cluster_size() { return g_cluster_size; }
-
 template <typename T>
 static int max_clusters_for(int cluster) {
   cudaLaunchConfig_t cfg = {};
@@ -763,7 +762,6 @@ static int max_clusters_for(int cluster) {
   }
   return num;
 }
-
 
 void ppr_part_bounds(const int32_t* col_ptr, int32_t n, int64_t m, int32_t nparts, int32_t* part_rows,
                      cudaStream_t s) {
@@ -814,22 +812,23 @@ void ppr_chunk_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int3
   count_launches(1);
 }
 
-int ppr_max_clusters(gpr_dtype dt) {
-  if (dt == GPR_BF16) return max_clusters_for<__nv_bfloat16>(g_cluster_size);
-  if (dt == GPR_FP16) return max_clusters_for<__half>(g_cluster_size);
-  return max_clusters_for<float>(g_cluster_size);
+
+static int max_clusters(gpr_dtype dt, int cluster) {
+  if (dt == GPR_BF16) return max_clusters_for<__nv_bfloat16>(cluster);
+  if (dt == GPR_FP16) return max_clusters_for<__half>(cluster);
+  return max_clusters_for<float>(cluster);
 }
 
-void ppr_launch(PprJob* jobs_dev, const int32_t* order_dev, int32_t njobs, uint32_t* queue_dev, char* ws,
-                int64_t ws_stride, int clusters, gpr_dtype dt, cudaStream_t s) {
+static void ppr_launch(PprJob* jobs_dev, const int32_t* order_dev, int32_t njobs, uint32_t* queue_dev, char* ws,
+                       int64_t ws_stride, int clusters, int cluster, gpr_dtype dt, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(clusters * g_cluster_size), 1, 1);
+  cfg.gridDim = dim3((unsigned)(clusters * cluster), 1, 1);
   cfg.blockDim = dim3(kPprThreads, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = g_cluster_size;
+  attr[0].val.clusterDim.x = cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -837,19 +836,145 @@ void ppr_launch(PprJob* jobs_dev, const int32_t* order_dev, int32_t njobs, uint3
   cudaError_t e;
   if (dt == GPR_BF16)
     e = cudaLaunchKernelEx(&cfg, ppr_kernel<__nv_bfloat16>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
-                           g_cluster_size);
+                           cluster);
   else if (dt == GPR_FP16)
-    e = cudaLaunchKernelEx(&cfg, ppr_kernel<__half>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
-                           g_cluster_size);
+    e = cudaLaunchKernelEx(&cfg, ppr_kernel<__half>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride, cluster);
   else
-    e = cudaLaunchKernelEx(&cfg, ppr_kernel<float>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride,
-                           g_cluster_size);
+    e = cudaLaunchKernelEx(&cfg, ppr_kernel<float>, jobs_dev, order_dev, njobs, queue_dev, ws, ws_stride, cluster);
   if (e != cudaSuccess) throw CudaFail{e, "cudaLaunchKernelEx(ppr_kernel)"};
   count_launches(1);
 }
 
-gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
-                         cudaStream_t s) {
+// ---- graph-size classes and the cluster-shape autotuner ---------------------
+// A job's graph falls in class k by ceil(log2 n): <= 11, 12-13, 14-15, 16-17,
+// >= 18.  Each class present in a call runs as its own persistent launch with
+// its own number of CTAs per cluster: one CTA suits a small graph (its steps
+// need no cluster barrier and its rows fill one CTA), eight a large one.
+// ppr_tune times the shapes of a (class, storage type) on a sample of the
+// class's jobs and keeps the fastest for the process; an untuned class takes
+// kDefaultShape.  A column's bits depend on its class's shape (the row split
+// among a cluster's CTAs orders the FP64 partial sums), not on the other
+// columns or jobs of the call.
+constexpr int kPprClasses = 5;
+constexpr int kClusterCands[] = {1, 2, 4, 8};
+constexpr int kDefaultCluster = 8;
+constexpr int kDefaultShape[kPprClasses] = {4, 4, 8, 4, 4};  // measured on GB300 (R-MAT batch, FP32 and BF16)
+constexpr int32_t kTuneSampleJobs = 64;
+constexpr int64_t kWorkspaceBudget = (int64_t)16 << 30;  // per launch: clusters x stride at most
+
+static int ceil_log2_n(int32_t n) {
+  int lg = 0;
+  while (((int64_t)1 << lg) < n) ++lg;
+  return lg;
+}
+static int ppr_class_of(int32_t n) { return std::min(kPprClasses - 1, std::max(0, (ceil_log2_n(n) - 10) / 2)); }
+static int class_log2n_max(int k) { return k == kPprClasses - 1 ? 31 : 11 + 2 * k; }
+
+static std::mutex g_ppr_tune_mu;
+static std::map<std::pair<int, int>, int> g_ppr_tuned;  // (class, dtype) -> CTAs per cluster
+
+// GPR_PPR_CLUSTER=k (1, 2, 4 or 8) forces the shape of every class.
+static int env_cluster() {
+  const char* e = getenv("GPR_PPR_CLUSTER");
+  if (!e) return 0;
+  const int k = atoi(e);
+  return (k == 1 || k == 2 || k == 4 || k == 8) ? k : 0;
+}
+
+// Bytes per workspace row (64 columns): the rank state, two contribution
+// buffers, and with BF16 deltas the running and sent sums.
+static int64_t ws_row_bytes(gpr_dtype dt) {
+  const int64_t tsz = (dt == GPR_BF16 || dt == GPR_FP16) ? 2 : 4;
+  return (int64_t)kPprCols * (4 + 2 * tsz + (dt == GPR_BF16 ? 8 : 0));
+}
+
+// One persistent launch over jobs_dev[order[i]], i < order.size(), whose
+// graphs have at most n_cap rows; device temporaries through `alloc`.
+template <typename A>
+static void launch_set(PprJob* jobs_dev, const std::vector<int32_t>& order, int32_t n_cap, gpr_dtype dt,
+                       int cluster, cudaStream_t s, A alloc) {
+  const int32_t nj = (int32_t)order.size();
+  if (nj == 0) return;
+  int clusters = max_clusters(dt, cluster);
+  if (clusters <= 0) throw StatusFail{GPR_ECUDA, "no thread-block cluster of the PPR kernel fits on this GPU"};
+  const int64_t stride = ((int64_t)std::max(n_cap, 1) * ws_row_bytes(dt) + 255) & ~(int64_t)255;
+  clusters = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)clusters, (int64_t)nj, kWorkspaceBudget / stride}));
+  int32_t* order_dev = (int32_t*)alloc((size_t)nj * 4);
+  uint32_t* queue = (uint32_t*)alloc(16);
+  char* ws = (char*)alloc((size_t)stride * clusters);
+  GPR_CUDA(cudaMemcpyAsync(order_dev, order.data(), (size_t)nj * 4, cudaMemcpyHostToDevice, s));
+  GPR_CUDA(cudaMemsetAsync(queue, 0, 16, s));
+  ppr_launch(jobs_dev, order_dev, nj, queue, ws, stride, clusters, cluster, dt, s);
+}
+
+// Times each cluster shape on up to kTuneSampleJobs jobs of one class
+// (trial_steps steps from fresh columns) and returns the fastest; ms_out[i]
+// gets candidate i's time.  The trial writes into the jobs' outputs, which
+// the call's real run then overwrites.
+template <typename A>
+static int tune_class(const std::vector<PprJob>& dj, const std::vector<std::vector<PprCol>>& cols,
+                      const std::vector<int32_t>& members, int32_t n_cap, gpr_dtype dt, int32_t trial_steps,
+                      cudaStream_t s, A alloc, double* ms_out) {
+  std::vector<int32_t> pick;
+  const int32_t step = std::max<int32_t>(1, (int32_t)members.size() / kTuneSampleJobs);
+  for (size_t i = 0; i < members.size() && (int32_t)pick.size() < kTuneSampleJobs; i += step) pick.push_back(members[i]);
+  const int32_t nt = (int32_t)pick.size();
+  PprCol* tcols = (PprCol*)alloc((size_t)nt * kPprCols * sizeof(PprCol));
+  PprJob* tjobs = (PprJob*)alloc((size_t)nt * sizeof(PprJob));
+  std::vector<PprCol> flat((size_t)nt * kPprCols);
+  std::vector<PprJob> tj(nt);
+  for (int32_t i = 0; i < nt; ++i) {
+    tj[i] = dj[pick[i]];
+    tj[i].iters = trial_steps;
+    tj[i].cols = tcols + (size_t)i * kPprCols;
+    for (int k = 0; k < kPprCols; ++k) {
+      PprCol c = cols[pick[i]][k];
+      c.max_iters = std::min(c.max_iters, trial_steps);
+      c.tol = 0.f;
+      flat[(size_t)i * kPprCols + k] = c;
+    }
+  }
+  GPR_CUDA(cudaMemcpyAsync(tjobs, tj.data(), (size_t)nt * sizeof(PprJob), cudaMemcpyHostToDevice, s));
+  std::vector<int32_t> order(nt);
+  std::iota(order.begin(), order.end(), 0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GPR_CUDA(cudaEventCreate(&e0));
+  GPR_CUDA(cudaEventCreate(&e1));
+  int best = kDefaultCluster;
+  float best_ms = 0.f;
+  try {
+    for (int ci = 0; ci < 4; ++ci) {
+      const int cl = kClusterCands[ci];
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches
+        GPR_CUDA(cudaMemcpyAsync(tcols, flat.data(), flat.size() * sizeof(PprCol), cudaMemcpyHostToDevice, s));
+        GPR_CUDA(cudaEventRecord(e0, s));
+        launch_set(tjobs, order, n_cap, dt, cl, s, alloc);
+        GPR_CUDA(cudaEventRecord(e1, s));
+        GPR_CUDA(cudaStreamSynchronize(s));
+        GPR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      ms_out[ci] = ms;
+      if (ci == 0 || ms < best_ms) {
+        best = cl;
+        best_ms = ms;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+// The batch: one device job per 64 columns, grouped by class, each class
+// one launch with its shape; with tune_all, each class's shape is timed and
+// kept instead (nothing else runs).
+static gpr_status run_ppr(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
+                          cudaStream_t s, bool tune_all, int32_t trial_steps, gpr_ppr_tune_result* tres) {
   std::vector<void*> tmp;
   auto T = [&](size_t bytes) {
     void* p = dalloc(bytes, s);
@@ -857,11 +982,9 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
     return p;
   };
   try {
-    // one device job per 64 columns
     std::vector<PprJob> dj;
     std::vector<std::vector<PprCol>> cols;
     std::vector<std::pair<int32_t, int32_t>> src;  // (request, first column)
-    int32_t n_cap = 1;
     for (int32_t j = 0; j < num_jobs; ++j) {
       const gpr_graph* g = jobs[j].graph;
       for (int32_t k0 = 0; k0 < jobs[j].num_seeds; k0 += kPprCols) {
@@ -881,7 +1004,6 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
             J.heavy_deg = b > 0 ? g->plan.deg_threshold[b - 1] : -1;  // bucket 0 holds every degree from 0
           }
         J.iters = max_iters;
-        J.n_cap = 0;  // set below
         std::vector<PprCol> cc(kPprCols);
         for (int k = 0; k < kPprCols; ++k) {
           PprCol c{};
@@ -904,46 +1026,81 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
         dj.push_back(J);
         cols.push_back(cc);
         src.emplace_back(j, k0);
-        n_cap = std::max(n_cap, g->n);
       }
     }
     const int32_t nj = (int32_t)dj.size();
+    if (tres) *tres = gpr_ppr_tune_result{};
     if (nj == 0) return GPR_OK;
-    // largest work first
-    std::vector<int32_t> order(nj);
-    std::iota(order.begin(), order.end(), 0);
-    std::vector<int64_t> work(nj);
-    for (int32_t i = 0; i < nj; ++i) {
-      const gpr_graph* g = jobs[src[i].first].graph;
-      work[i] = g->m + g->n;
+    // classes: members (largest work first) and row capacity
+    std::vector<std::vector<int32_t>> members(kPprClasses);
+    std::vector<int32_t> ncap(kPprClasses, 1);
+    {
+      std::vector<int32_t> order(nj);
+      std::iota(order.begin(), order.end(), 0);
+      std::vector<int64_t> work(nj);
+      for (int32_t i = 0; i < nj; ++i) {
+        const gpr_graph* g = jobs[src[i].first].graph;
+        work[i] = g->m + g->n;
+      }
+      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+      for (int32_t i : order) {
+        const int k = ppr_class_of(dj[i].n);
+        members[k].push_back(i);
+        ncap[k] = std::max(ncap[k], dj[i].n);
+      }
     }
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
-
+    for (int32_t i = 0; i < nj; ++i) dj[i].n_cap = ncap[ppr_class_of(dj[i].n)];
     PprCol* cols_dev = (PprCol*)T((size_t)nj * kPprCols * sizeof(PprCol));
     std::vector<PprCol> flat((size_t)nj * kPprCols);
     for (int32_t i = 0; i < nj; ++i)
       std::copy(cols[i].begin(), cols[i].end(), flat.begin() + (size_t)i * kPprCols);
-    GPR_CUDA(cudaMemcpyAsync(cols_dev, flat.data(), flat.size() * sizeof(PprCol), cudaMemcpyHostToDevice, s));
-    for (int32_t i = 0; i < nj; ++i) {
-      dj[i].cols = cols_dev + (size_t)i * kPprCols;
-      dj[i].n_cap = n_cap;
-    }
+    for (int32_t i = 0; i < nj; ++i) dj[i].cols = cols_dev + (size_t)i * kPprCols;
     PprJob* jobs_dev = (PprJob*)T((size_t)nj * sizeof(PprJob));
-    int32_t* order_dev = (int32_t*)T((size_t)nj * 4);
-    uint32_t* queue = (uint32_t*)T(16);
     GPR_CUDA(cudaMemcpyAsync(jobs_dev, dj.data(), (size_t)nj * sizeof(PprJob), cudaMemcpyHostToDevice, s));
-    GPR_CUDA(cudaMemcpyAsync(order_dev, order.data(), (size_t)nj * 4, cudaMemcpyHostToDevice, s));
-    GPR_CUDA(cudaMemsetAsync(queue, 0, 16, s));
-    int clusters = ppr_max_clusters(dt);
-    if (clusters <= 0) throw StatusFail{GPR_ECUDA, "no thread-block cluster of the PPR kernel fits on this GPU"};
-    clusters = std::min(clusters, nj);
-    // per row and column: x (FP32), two contribution buffers, and with BF16
-    // deltas the running and sent sums (FP32 each)
-    const size_t tsz = (dt == GPR_BF16 || dt == GPR_FP16) ? 2 : 4;
-    const int64_t per = 4 + 2 * (int64_t)tsz + (dt == GPR_BF16 ? 8 : 0);
-    const int64_t stride = (((int64_t)n_cap * kPprCols * per) + 255) & ~(int64_t)255;
-    char* ws = (char*)T((size_t)stride * clusters);
-    ppr_launch(jobs_dev, order_dev, nj, queue, ws, stride, clusters, dt, s);
+    // the shape of each class
+    const int forced = env_cluster();
+    int shape[kPprClasses];
+    for (int k = 0; k < kPprClasses; ++k) {
+      shape[k] = kDefaultShape[k];
+      if (members[k].empty()) continue;
+      const std::pair<int, int> key(k, (int)dt);
+      bool have = false;
+      {
+        std::lock_guard<std::mutex> lk(g_ppr_tune_mu);
+        auto it = g_ppr_tuned.find(key);
+        if (it != g_ppr_tuned.end()) {
+          shape[k] = it->second;
+          have = true;
+        }
+      }
+      (void)have;
+      if (tune_all) {
+        double ms[4] = {0, 0, 0, 0};
+        shape[k] = tune_class(dj, cols, members[k], ncap[k], dt, std::max(1, trial_steps), s, T, ms);
+        {
+          std::lock_guard<std::mutex> lk(g_ppr_tune_mu);
+          g_ppr_tuned[key] = shape[k];
+        }
+        if (tres) {
+          const int c = tres->classes++;
+          tres->log2n_max[c] = class_log2n_max(k);
+          tres->jobs[c] = (int32_t)members[k].size();
+          tres->cluster[c] = shape[k];
+          for (int ci = 0; ci < 4; ++ci) {
+            if (kClusterCands[ci] == shape[k]) tres->ms[c] = ms[ci];
+            if (kClusterCands[ci] == 8) tres->ms_cluster8[c] = ms[ci];
+          }
+        }
+      }
+      if (forced) shape[k] = forced;
+    }
+    if (tune_all) {
+      GPR_CUDA(cudaStreamSynchronize(s));
+      for (void* p : tmp) dfree(p, s);
+      return GPR_OK;
+    }
+    GPR_CUDA(cudaMemcpyAsync(cols_dev, flat.data(), flat.size() * sizeof(PprCol), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < kPprClasses; ++k) launch_set(jobs_dev, members[k], ncap[k], dt, shape[k], s, T);
     // per-column results back to the caller
     GPR_CUDA(cudaMemcpyAsync(flat.data(), cols_dev, flat.size() * sizeof(PprCol), cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
@@ -961,14 +1118,25 @@ gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_
     return GPR_OK;
   } catch (const StatusFail& f) {
     for (void* p : tmp) dfree(p, s);
-    set_error("ppr_batch: %s", f.msg.c_str());
+    set_error("%s: %s", tres ? "ppr_tune" : "ppr_batch", f.msg.c_str());
     return f.st;
   } catch (const CudaFail& f) {
     cudaGetLastError();
     for (void* p : tmp) dfree(p, s);
-    set_error("ppr_batch: %s failed: %s", f.what, cudaGetErrorString(f.err));
+    set_error("%s: %s failed: %s", tres ? "ppr_tune" : "ppr_batch", f.what, cudaGetErrorString(f.err));
     return GPR_ECUDA;
   }
+}
+
+gpr_status run_ppr_batch(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max_iters, double tol, gpr_dtype dt,
+                         cudaStream_t s) {
+  return run_ppr(jobs, num_jobs, max_iters, tol, dt, s, false, 8, nullptr);
+}
+
+gpr_status run_ppr_tune(const gpr_ppr_job* jobs, int32_t num_jobs, gpr_dtype dt, int32_t trial_steps,
+                        gpr_ppr_tune_result* out, cudaStream_t s) {
+  gpr_ppr_tune_result local{};
+  return run_ppr(jobs, num_jobs, trial_steps, 0.0, dt, s, true, trial_steps, out ? out : &local);
 }
 
 }  // namespace gpr

@@ -108,9 +108,5 @@ void ppr_chunk_launch(const SlotDesc* slots_dev, const StepItem* items_dev, int3
 void ppr_part_bounds(const int32_t* col_ptr, int32_t n, int64_t m, int32_t nparts, int32_t* part_rows,
                      cudaStream_t s);
 
-int ppr_max_clusters(gpr_dtype dt);
-int ppr_cluster_size();
-void ppr_launch(PprJob* jobs_dev, const int32_t* order_dev, int32_t njobs, uint32_t* queue_dev, char* ws,
-                int64_t ws_stride, int clusters, gpr_dtype dt, cudaStream_t s);
 
 }  // namespace gpr

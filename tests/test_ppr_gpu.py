@@ -175,3 +175,29 @@ def test_rejects_bad_requests(torch):
         with pytest.raises(gpr.GprError) as ei:
             gpr.ppr_batch([(g, seeds, d, out)])
         assert ei.value.status == gpr.EINVAL
+
+
+def test_tuner_picks_a_shape_per_size_class_and_every_shape_is_correct(torch):
+    import os
+    sizes = [(1500, 20_000), (6000, 80_000), (40_000, 600_000)]  # ceil log2 n = 11, 13, 16: three classes
+    graphs = [make_graph(torch, n, m, 70 + i) for i, (n, m) in enumerate(sizes)]
+    reqs = [(g, (np.arange(64, dtype=np.int32) * 37) % g.n, 0.85) for g, _ in graphs]
+    outs = [torch.zeros((g.n, 64), dtype=torch.float32, device="cuda") for g, _ in graphs]
+    res = gpr.ppr_tune([(g, sd, d, o) for (g, sd, d), o in zip(reqs, outs)], trial_steps=5)
+    assert [r["log2n_max"] for r in res] == [11, 13, 17]
+    for r in res:
+        assert r["jobs"] == 1 and r["cluster"] in (1, 2, 4, 8) and r["ms"] > 0 and r["ms_cluster8"] > 0
+        assert r["ms"] <= r["ms_cluster8"]
+    try:
+        for shape in ("1", "2", "4", "8"):
+            os.environ["GPR_PPR_CLUSTER"] = shape
+            xs, res2 = run(torch, reqs, 30)
+            for (g, sd, d), (_, ref), x in zip(reqs, graphs, xs):
+                for k in (0, 17, 63):
+                    xr, _ = oracle.ppr(ref, int(sd[k]), 0.85, 30)
+                    assert l1(x[:, k], xr) <= 1e-5, (shape, g.n, k)
+    finally:
+        os.environ.pop("GPR_PPR_CLUSTER", None)
+    with pytest.raises(gpr.GprError) as ei:
+        gpr.ppr_tune([(graphs[0][0], [0], 0.85, outs[0][:, :1].contiguous())], trial_steps=0)
+    assert ei.value.status == gpr.EINVAL
