@@ -741,6 +741,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
   int32_t* seg = nullptr;
   int* derr = nullptr;
   try {
+    trace_phase(nullptr, s);
     // whole 256-edge chunks are copied: kPad entries past the end, zeroed
     const size_t me = (size_t)m + kPad;
     k->src_lo = (uint16_t*)dalloc(me * 2, s);
@@ -760,7 +761,9 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
                                           kg.kb_bits, keys);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
+      trace_phase("layout: keys", s);
       const uint64_t* sorted = radix_sort_u64(keys, alt, m, kg.kbits, s, derr);
+      trace_phase("layout: sort", s);
       bk_extract_kernel<<<grid, 256, 0, s>>>(sorted, m, sb_bits, kg.kbits, k->n_dense, D, kg.kb_bits, k->dense_bits,
                                              S, nseg, k->src_lo, k->dst_lo, k->vals, seg);
       GPR_CUDA(cudaGetLastError());
@@ -785,6 +788,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
     seg = nullptr;
     derr = nullptr;
     if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "blocked layout: a look-back wait of the sort timed out"};
+    trace_phase("layout: extract + tables", s);
 
     // expand units (source blocks past the dense ones): per source block,
     // runs of consecutive bins' segments of at most unit edges and
@@ -838,6 +842,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
       }
     }
     k->dense_edges = dense_edges;
+    trace_phase("layout: units (host)", s);
     // largest first: the dynamic queues then end with small units
     std::stable_sort(xu.begin(), xu.end(),
                      [](const ExpandUnit& a, const ExpandUnit& b) { return a.hi - a.lo > b.hi - b.lo; });
@@ -864,6 +869,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
     k->xgrid = persistent_grid(bk_expand_kernel, expand_smem(sb_bits));
     k->agrid = std::max(persistent_grid(bk_accum_kernel<float>, accum_smem(w_bits)),
                         persistent_grid(bk_accum_kernel<__nv_bfloat16>, accum_smem(w_bits)));
+    trace_phase("layout: upload", s);
     k->bytes = (int64_t)me * 8 + nseg * (int64_t)sizeof(int2) + (int64_t)xu.size() * sizeof(ExpandUnit) +
                (int64_t)au.size() * sizeof(AccumUnit) + (int64_t)n_split * (int64_t)W * 8 + (int64_t)B * 24;
     return k;

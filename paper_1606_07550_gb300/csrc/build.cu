@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <mutex>
 
 #include "gpr_internal.cuh"
@@ -66,6 +67,26 @@ int num_sms() {
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------------ phase trace --
+// With GPR_TRACE=1 in the environment, trace_phase synchronises the stream and
+// prints the host wall time since the previous mark of this thread to stderr
+// (a timeline of a call's phases); otherwise it does nothing.
+static bool trace_on() {
+  static const bool on = [] {
+    const char* e = getenv("GPR_TRACE");
+    return e && atoi(e) != 0;
+  }();
+  return on;
+}
+void trace_phase(const char* what, cudaStream_t s) {
+  if (!trace_on()) return;
+  static thread_local std::chrono::steady_clock::time_point last;
+  cudaStreamSynchronize(s);
+  const auto now = std::chrono::steady_clock::now();
+  if (what) fprintf(stderr, "[gpr trace] %-28s %9.3f ms\n", what, std::chrono::duration<double, std::milli>(now - last).count());
+  last = now;
+}
 
 // The library allocates with the device's default stream-ordered pool.  The
 // pool is told to keep freed memory mapped (a setting of this process only),
@@ -592,6 +613,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
   Temps tmp{s, {}};
   const int b = g->id_bits;
   try {
+    trace_phase(nullptr, s);
     int* derr = (int*)tmp.get(sizeof(int) * 2);
     GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
     const int32_t* src = src_in;
@@ -603,6 +625,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       GPR_CUDA(cudaMemcpyAsync(d_dev, dst_in, (size_t)m_raw * 4, cudaMemcpyHostToDevice, s));
       src = s_dev;
       dst = d_dev;
+      trace_phase("build: copy of the COO", s);
     }
     // 1. relabelling pi: nodes by descending raw out-degree (ties: ascending id)
     int32_t* odeg = (int32_t*)tmp.get((size_t)n * 4);
@@ -623,6 +646,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
     if (herr & DERR_BAD_ID) throw StatusFail{GPR_EINVAL, "graph_build: an edge id is outside [0, n)"};
+    trace_phase("build: raw out-degrees", s);
     {
       uint64_t* nk = (uint64_t*)tmp.get((size_t)n * 8);
       uint64_t* na = (uint64_t*)tmp.get((size_t)n * 8);
@@ -637,6 +661,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
     }
+    trace_phase("build: relabelling", s);
     // 2. keys (pi(dst), pi(src)), sort, de-duplicate: the CSC in relabelled ids
     g->col_ptr = (int32_t*)dalloc(((size_t)n + 1) * 4, s);
     g->outdeg = (int32_t*)dalloc((size_t)n * 4, s);
@@ -656,6 +681,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       permute_kernel<<<grid_for(n), kThreads, 0, s>>>(odeg, g->plan.old2new, n, g->outdeg);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
+      trace_phase("build: pack", s);
       m = keys_to_csc(keys, alt, m_raw, b, n, hist, g->col_ptr, row_idx_full, g->outdeg, derr, tmp, s,
                       /*presorted=*/false, /*degree_from_raw=*/true);
       GPR_CUDA(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s));
@@ -670,6 +696,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     if (m > 0)
       GPR_CUDA(cudaMemcpyAsync(g->row_idx, row_idx_full, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
     tmp.release();
+    trace_phase("build: sort + dedupe", s);
     // 3. execution layout (degree buckets, chunks, inverse degrees)
     int* derr2 = (int*)dalloc(8, s);
     GPR_CUDA(cudaMemsetAsync(derr2, 0, 8, s));
@@ -683,6 +710,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     GPR_CUDA(cudaStreamSynchronize(s));
     dfree(derr2, s);
     if (herr & DERR_TIMEOUT) throw StatusFail{GPR_ETIMEOUT, "graph_build: a device-side wait timed out"};
+    trace_phase("build: plan", s);
     *out = g;
     return GPR_OK;
   } catch (const StatusFail& f) {

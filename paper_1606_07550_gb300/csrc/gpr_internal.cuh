@@ -50,6 +50,10 @@ void dfree(void* p, cudaStream_t s);
 int num_sms();
 int device_ordinal();
 
+// With GPR_TRACE=1: synchronise s and print the wall time since the previous
+// mark on this thread, labelled `what` (null: just set the mark).
+void trace_phase(const char* what, cudaStream_t s);
+
 // Host-side count of kernels this library has launched (a CUDA graph launch
 // counts its kernel nodes).
 void count_launches(int64_t k);

@@ -617,6 +617,7 @@ static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype 
   drop_exec(w);
   // the capture stream must see the allocations made on `s`
   GPR_CUDA(cudaStreamSynchronize(s));
+  trace_phase(nullptr, s);
   cudaGraph_t graph = nullptr;
   GPR_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
   try {
@@ -632,7 +633,9 @@ static void ensure_exec(gpr_graph* g, PagerankWork* w, int32_t iters, gpr_dtype 
   }
   cudaError_t e = cudaStreamEndCapture(w->cap, &graph);
   if (e != cudaSuccess) throw CudaFail{e, "cudaStreamEndCapture"};
+  trace_phase("pagerank: capture", s);
   e = cudaGraphInstantiate(&w->exec, graph, 0);
+  trace_phase("pagerank: instantiate", s);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     w->exec = nullptr;
@@ -744,9 +747,12 @@ gpr_status run_pagerank(gpr_graph* g, double damping, int32_t iters, gpr_dtype d
   std::lock_guard<std::mutex> lock(g->mu);
   try {
     const auto t_setup0 = std::chrono::steady_clock::now();
+    trace_phase(nullptr, s);
     if (!g->work) g->work = work_make(g, s);
     PagerankWork* w = g->work;
+    trace_phase("pagerank: workspace", s);
     const Choice ch = pick(g, w, flags, dt, s);
+    trace_phase("pagerank: schedule choice", s);
     const int sched = ch.sched;
     if (sched == kSchedBlocked) ensure_layout(g, w, ch, s);
     const bool warm = (flags & GPR_WARM_START) != 0;
