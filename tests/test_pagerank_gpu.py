@@ -305,6 +305,12 @@ def test_rmat25_full_size_against_oracle(torch):
     del s_d, d_d, perm
     torch.cuda.empty_cache()
     assert g.m == meta["m"]
+    # the full-size CSC offsets and out-degrees are the oracle's, bit for bit
+    import hashlib
+    cp, _, od = g.export()
+    assert hashlib.sha256(np.ascontiguousarray(cp, np.int32).tobytes()).hexdigest() == meta["sha256_col_ptr"]
+    assert hashlib.sha256(np.ascontiguousarray(od, np.int32).tobytes()).hexdigest() == meta["sha256_outdeg"]
+    del cp, od
     x = gpu_pr(torch, g, spec.iters)
     rel_l1, mr = sampled_errors(x, meta)
     print(f"rmat25 sampled: relative L1 {rel_l1:.3e}, max rel {mr:.3e}")
