@@ -186,7 +186,14 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t d = (uint32_t)(k[j] >> shift) & 255u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // the lanes holding the same digit: one vote per digit bit
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int bb = 0; bb < 8; ++bb) {
+      const uint32_t bit = (d >> bb) & 1u;
+      const uint32_t vote = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? vote : ~vote;
+    }
     const uint32_t c = s_wcnt[w][d];
     rk[j >> 1] |= (c + __popc(peers & lt)) << (16 * (j & 1));
     __syncwarp();
