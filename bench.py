@@ -494,13 +494,13 @@ def build_graph_dev(torch, gpr, spec, stream=None):
 
 def ppr_bytes_per_step(n, m, dt_name, cols=64):
     """Modelled bytes of one personalised-PageRank step of a 64-column job:
-    indices 4m, offsets 4(n+1), the rank state read and written 8 per row and
-    column, the contributions written and gathered once per edge and column
-    (s bytes each: 4 FP32, 2 FP16 / BF16), and with BF16 deltas the running
-    and sent sums read and written (16 per row and column)."""
+    indices 4m, offsets 4(n+1), the state read and written per row and column
+    (x: 8 B with FP32 and FP16 storage; with BF16 deltas the running and sent
+    sums: 16 B), and the contributions written and gathered once per edge and
+    column (s bytes each: 4 FP32, 2 FP16 / BF16)."""
     sz = 4 if dt_name == "fp32" else 2
-    extra = 16 if dt_name == "bf16" else 0
-    return 4 * m + 4 * (n + 1) + cols * n * (8 + sz + extra) + cols * m * sz
+    state = 16 if dt_name == "bf16" else 8
+    return 4 * m + 4 * (n + 1) + cols * n * (state + sz) + cols * m * sz
 
 
 def run_batched(args, world, rank, local):
@@ -599,9 +599,9 @@ def run_batched(args, world, rank, local):
                      "roofline": {"kernel": "ppr_kernel (one persistent cluster launch over every job)",
                                   "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                   "frac": achieved / peak, "peak_source": peak_kind,
-                                  "bytes_model": "per step and job: 4m + 4(n+1) + 64n(8 + s [+16 BF16]) + 64ms, "
-                                                 "s = stored bytes per contribution; gathers counted once "
-                                                 "per edge and column (cache hits count as bytes)",
+                                  "bytes_model": "per step and job: 4m + 4(n+1) + 64n(state + s) + 64ms, state 8 (x) or "
+                                                 "16 (BF16 running and sent sums), s = stored bytes per contribution; "
+                                                 "gathers counted once per edge and column (cache hits count as bytes)",
                                   "traffic": None}}
     launches = gpr.lib().gpr_kernel_launches() - launches0
     # baselines: one solve at a time, on a sample of (graph, seed) pairs

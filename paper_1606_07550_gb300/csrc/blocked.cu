@@ -47,6 +47,7 @@
 // once), and a bin with many edges is cut into units whose sums meet in a
 // global accumulator.
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "blocked.cuh"
@@ -778,9 +779,10 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
     bk_transpose_kernel<<<grid, 256, 0, s>>>(seg, S, B, k->xseg);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
-    std::vector<int32_t> h((size_t)nseg + 1);
+    // the segment table on the host, source-block major (contiguous per block)
+    std::unique_ptr<int2[]> X(new int2[(size_t)std::max<int64_t>(nseg, 1)]);
     int herr = 0;
-    GPR_CUDA(cudaMemcpyAsync(h.data(), seg, (size_t)(nseg + 1) * 4, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaMemcpyAsync(X.get(), k->xseg, (size_t)nseg * sizeof(int2), cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
     dfree(seg, s);
@@ -802,8 +804,9 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
         first = -1;
         edges = 0;
       };
+      const int2* Xs = X.get() + (size_t)sb * B;
       for (int32_t b = 0; b < B; ++b) {
-        const int32_t lo = h[(size_t)b * S + sb], hi = h[(size_t)b * S + sb + 1];
+        const int32_t lo = Xs[b].x, hi = Xs[b].y;
         const int64_t len = hi - lo;
         if (len == 0) continue;
         if (len > xunit) {
@@ -828,9 +831,12 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
     std::vector<AccumUnit> au;
     int32_t n_split = 0;
     int64_t dense_edges = 0;
+    const int2* X0 = X.get();                    // tiles (b, 0)
+    const int2* XD = X.get() + (size_t)D * B;     // tiles (b, D), the first after the dense ones
+    const int2* XL = X.get() + (size_t)(S - 1) * B;  // tiles (b, S - 1), the last of each bin
     for (int32_t b = 0; b < B; ++b) {
-      const int64_t lo = h[(size_t)b * S], hi = h[(size_t)(b + 1) * S];
-      const int64_t mid = h[(size_t)b * S + D];
+      const int64_t lo = X0[b].x, hi = XL[b].y;
+      const int64_t mid = D < S ? XD[b].x : hi;
       dense_edges += mid - lo;
       const int64_t e = hi - lo;
       const int32_t parts = (int32_t)std::max<int64_t>(1, (e + unit - 1) / unit);

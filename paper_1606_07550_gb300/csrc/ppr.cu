@@ -31,7 +31,9 @@
 // differs from the exact c by one rounding of the last difference c - s,
 // which shrinks with the step-to-step change of x: the rounding of one step
 // is corrected by the next instead of staying in the result.  The state per
-// node and column is x, y and s (FP32); the gathers read 2 bytes.
+// node and column is y and s (FP32); x is not stored: x = d y + b at the
+// seed row (d y elsewhere), b the step's seed coefficient, kept per column;
+// the gathers read 2 bytes.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -126,6 +128,7 @@ struct ColRegs {
   float b0, b1;      // seed coefficient (1 - d) + d D
   int32_t s0, s1;    // relabelled seed rows
   bool l0, l1;       // live
+  float bp0, bp1;    // seed coefficient of the previous step (BF16 deltas: x of the previous step)
 };
 
 // The row's previous state: loaded before the gathers so its latency overlaps them.
@@ -149,24 +152,27 @@ __device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, float2 xo, f
                                                T* __restrict__ Cout, const float* __restrict__ inv_deg, int lane,
                                                float (&acc)[2][3]) {
   const float inv = inv_deg[p];
-  float* xp = X + (int64_t)p * kPprCols + 2 * lane;
   constexpr bool kDelta = std::is_same<T, __nv_bfloat16>::value;
-  if constexpr (kDelta) {  // y holds this step's gathered deltas: add the running sums
-    y.x += ys.x;
-    y.y += ys.y;
-  }
-  const float n0 = c.l0 ? fmaf(c.a0, y.x, p == c.s0 ? c.b0 : 0.f) : xo.x;
-  const float n1 = c.l1 ? fmaf(c.a1, y.y, p == c.s1 ? c.b1 : 0.f) : xo.y;
-  *reinterpret_cast<float2*>(xp) = make_float2(n0, n1);
+  float n0, n1;
   if constexpr (kDelta) {
+    // y holds this step's gathered deltas: add the running sums; x of the
+    // previous step from the previous running sums and seed coefficient
+    const float y0 = ys.x + y.x, y1 = ys.y + y.y;
+    xo.x = fmaf(c.a0, ys.x, p == c.s0 ? c.bp0 : 0.f);
+    xo.y = fmaf(c.a1, ys.y, p == c.s1 ? c.bp1 : 0.f);
+    n0 = fmaf(c.a0, y0, p == c.s0 ? c.b0 : 0.f);
+    n1 = fmaf(c.a1, y1, p == c.s1 ? c.b1 : 0.f);
     // the new contributions as deltas against what was sent (0 for columns
     // that are not running)
     const uint32_t q0 = c.l0 ? bf16_bits_rn(n0 * inv - ys.z) : 0u;
     const uint32_t q1 = c.l1 ? bf16_bits_rn(n1 * inv - ys.w) : 0u;
-    YS[(int64_t)p * 32 + lane] = make_float4(c.l0 ? y.x : ys.x, c.l1 ? y.y : ys.y, ys.z + bf16_bits_to_float(q0),
+    YS[(int64_t)p * 32 + lane] = make_float4(c.l0 ? y0 : ys.x, c.l1 ? y1 : ys.y, ys.z + bf16_bits_to_float(q0),
                                              ys.w + bf16_bits_to_float(q1));
     *reinterpret_cast<uint32_t*>(Cout + (int64_t)p * kPprCols + 2 * lane) = q0 | (q1 << 16);
   } else {
+    n0 = c.l0 ? fmaf(c.a0, y.x, p == c.s0 ? c.b0 : 0.f) : xo.x;
+    n1 = c.l1 ? fmaf(c.a1, y.y, p == c.s1 ? c.b1 : 0.f) : xo.y;
+    *reinterpret_cast<float2*>(X + (int64_t)p * kPprCols + 2 * lane) = make_float2(n0, n1);
     st_pair(Cout + (int64_t)p * kPprCols + 2 * lane, n0 * inv, n1 * inv, 0u);
   }
   acc[0][0] += n0;
@@ -177,6 +183,12 @@ __device__ __forceinline__ void finish_ppr_row(int32_t p, float2 y, float2 xo, f
   }
   acc[0][2] += fabsf(n0 - xo.x);
   acc[1][2] += fabsf(n1 - xo.y);
+}
+
+// x of column k at row p from the BF16 delta state: d y + b at the seed row.
+__device__ __forceinline__ float x_from_ys(const float4* YS, int32_t p, int k, float d, int32_t seed_row, float b) {
+  const float* ysf = reinterpret_cast<const float*>(YS + (int64_t)p * 32 + (k >> 1));
+  return fmaf(d, ysf[k & 1], p == seed_row ? b : 0.f);
 }
 
 // A row costs three 256-byte row accesses (its state read and written, its
@@ -252,6 +264,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
   __shared__ double s_best[kPprCols];
   __shared__ int32_t s_stall[kPprCols];
   __shared__ double s_D[kPprCols], s_res[kPprCols];
+  __shared__ float s_bused[kPprCols];  // seed coefficient of each column's latest step (1 before its first)
   __shared__ int32_t s_status[kPprCols], s_iters[kPprCols], s_maxit[kPprCols], s_newdone[kPprCols];
 
   for (;;) {
@@ -266,13 +279,14 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
     const int32_t* __restrict__ row_idx = J->row_idx;
     const float* __restrict__ inv_deg = J->inv_deg;
     char* base = ws + cid * ws_stride;
-    float* X = (float*)base;
+    // workspace: x (FP32 and FP16 storage only), two contribution buffers,
+    // and with BF16 deltas the running and sent sums
+    constexpr bool kDelta = std::is_same<T, __nv_bfloat16>::value;
+    float* X = kDelta ? nullptr : (float*)base;
     T* Cb[2];
-    Cb[0] = (T*)(base + (int64_t)J->n_cap * kPprCols * 4);
+    Cb[0] = (T*)(base + (kDelta ? 0 : (int64_t)J->n_cap * kPprCols * 4));
     Cb[1] = Cb[0] + (int64_t)J->n_cap * kPprCols;
-    // BF16 deltas: running and sent sums after the two contribution buffers
-    float4* YS = std::is_same<T, __nv_bfloat16>::value ? reinterpret_cast<float4*>(Cb[1] + (int64_t)J->n_cap * kPprCols)
-                                                       : nullptr;
+    float4* YS = kDelta ? reinterpret_cast<float4*>(Cb[1] + (int64_t)J->n_cap * kPprCols) : nullptr;
     int parity = 0;
 
     // this block's rows: split by edges + kRowWeight * rows
@@ -300,6 +314,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         s_res[tid] = 0.0;
         s_best[tid] = INFINITY;
         s_stall[tid] = 0;
+        s_bused[tid] = 1.f;  // x_0 = e_seed
       } else {
         s_seed[tid] = cr.status == kColEmpty ? -1 : J->old2new[cr.seed];
         s_D[tid] = cr.dangling;
@@ -307,6 +322,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         s_res[tid] = cr.residual;
         s_best[tid] = cr.best;
         s_stall[tid] = cr.stall;
+        s_bused[tid] = cr.bused;
       }
       s_d[tid] = cr.damping;
       s_tol[tid] = cr.tol;
@@ -317,7 +333,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
     {
       T* Cc = Cb[parity];
       for (int64_t i = (int64_t)r0 * kPprCols + tid; i < (int64_t)r1 * kPprCols; i += kPprThreads) {
-        X[i] = 0.f;
+        if (X) X[i] = 0.f;
         st_one(Cc + i, 0.f);
       }
       if (YS)
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       if (tid < kPprCols && s_status[tid] == kColFresh) {
         const int32_t s = s_seed[tid];
         if (s >= r0 && s < r1) {
-          X[(int64_t)s * kPprCols + tid] = 1.f;
+          if (X) X[(int64_t)s * kPprCols + tid] = 1.f;
           st_one(Cc + (int64_t)s * kPprCols + tid, inv_deg[s]);
           if (YS) {  // the first delta is the whole contribution: it is what has been sent
             float* ysf = reinterpret_cast<float*>(YS + (int64_t)s * 32 + (tid >> 1));
@@ -362,6 +378,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         c.b1 = (float)((1.0 - (double)s_d[k1]) + (double)s_d[k1] * s_D[k1]);
         c.s0 = s_seed[k0];
         c.s1 = s_seed[k1];
+        c.bp0 = s_bused[k0];
+        c.bp1 = s_bused[k1];
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       // light rows: one warp per row, round-robin (neighbouring rows share
@@ -371,7 +389,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
-        const float2 xo = on ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
+        const float2 xo = on && X ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
         const float4 ys = on ? ld_ys(YS, p, lane) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane, on);
         if (on) finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
@@ -393,8 +411,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
             yy += s_heavy[w][2 * lane + 1];
           }
           if (on)
-            finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), ld_ys(YS, p, lane), c, X, YS, Cout,
-                           inv_deg, lane, acc);
+            finish_ppr_row(p, make_float2(yx, yy), X ? ld_state(X, p, lane) : make_float2(0.f, 0.f),
+                           ld_ys(YS, p, lane), c, X, YS, Cout, inv_deg, lane, acc);
         }
         __syncthreads();
       }
@@ -419,6 +437,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
           tot[1] += pp[kPprCols + tid];
           tot[2] += pp[2 * kPprCols + tid];
         }
+        // the seed coefficient this step used (as the step computed it), then the new D
+        s_bused[tid] = (float)((1.0 - (double)s_d[tid]) + (double)s_d[tid] * s_D[tid]);
         s_D[tid] = tot[1];
         s_res[tid] = tot[2];
         const int32_t k_it = s_iters[tid] + 1;
@@ -449,8 +469,11 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         if (!s_newdone[k]) continue;
         float* out = J->cols[k].out;
         const int32_t ldo = J->cols[k].ldo;
-        for (int32_t v = v0 + tid; v < v1; v += kPprThreads)
-          out[(int64_t)v * ldo] = X[(int64_t)J->old2new[v] * kPprCols + k];
+        for (int32_t v = v0 + tid; v < v1; v += kPprThreads) {
+          const int32_t p = J->old2new[v];
+          out[(int64_t)v * ldo] = kDelta ? x_from_ys(YS, p, k, s_d[k], s_seed[k], s_bused[k])
+                                         : X[(int64_t)p * kPprCols + k];
+        }
       }
     }
     if (crank == 0) {
@@ -462,6 +485,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
         cr->residual = s_res[tid];
         cr->best = s_best[tid];
         cr->stall = s_stall[tid];
+        cr->bused = s_bused[tid];
       }
     }
     cl.sync();  // the workspace and s_job are reused by the next job
@@ -488,14 +512,16 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
   __shared__ int32_t s_seed[kPprCols], s_status[kPprCols], s_iters[kPprCols], s_newdone[kPprCols];
   __shared__ float s_d[kPprCols];
   __shared__ double s_D[kPprCols];
+  __shared__ float s_bprev[kPprCols];  // seed coefficient of each column's previous step
   const int cur = step & 1, prev = cur ^ 1;
   for (int32_t ii = blockIdx.x; ii < nitems; ii += gridDim.x) {
     const StepItem item = items[ii];
     const SlotDesc* S = slots + item.slot;
     const int32_t r0 = S->part_rows[item.part], r1 = S->part_rows[item.part + 1];
     const float* __restrict__ inv_deg = S->inv_deg;
-    float* X = S->X;
-    float4* YS = std::is_same<T, __nv_bfloat16>::value ? S->YS : nullptr;
+    constexpr bool kDelta = std::is_same<T, __nv_bfloat16>::value;
+    float* X = kDelta ? nullptr : S->X;
+    float4* YS = kDelta ? S->YS : nullptr;
 
     // ---- column state for this launch
     if (tid < kPprCols) {
@@ -505,6 +531,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       s_d[tid] = cr.damping;
       int32_t status, iters, stall;
       double D, res, best;
+      float bprev;  // seed coefficient of the column's latest executed step (1 before its first)
       int newdone = 0;
       if (mode == kStepInit) {
         status = cr.status;
@@ -513,7 +540,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         res = cr.residual;
         best = cr.best;
         stall = cr.stall;
+        bprev = cr.bused;
         if (status == kColFresh) {
+          bprev = 1.f;
           status = kColRunning;
           iters = 0;
           res = 0.0;
@@ -533,6 +562,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         res = cs.residual;
         best = cs.best;
         stall = cs.stall;
+        bprev = cs.bused;
         const bool fold = mode == kStepFinish || step > 1;
         if (fold && status == kColRunning) {
           double dsum = 0.0, rsum = 0.0;
@@ -562,6 +592,11 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       s_iters[tid] = iters;
       s_D[tid] = D;
       s_newdone[tid] = newdone;
+      s_bprev[tid] = bprev;
+      // the seed coefficient this launch's step uses (as ColRegs computes it), if it runs one
+      const float bnow = (mode == kStepRun && status == kColRunning)
+                             ? (float)((1.0 - (double)cr.damping) + (double)cr.damping * D)
+                             : bprev;
       if (item.part == 0) {
         if (mode == kStepFinish) {
           PprCol* w = S->rec + tid;
@@ -571,8 +606,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
           w->residual = res;
           w->best = best;
           w->stall = stall;
+          w->bused = bprev;
         } else {
-          S->st[mode == kStepInit ? 0 : cur][tid] = ColState{status, iters, D, res, best, stall, 0};
+          S->st[mode == kStepInit ? 0 : cur][tid] = ColState{status, iters, D, res, best, stall, bnow};
         }
       }
     }
@@ -591,12 +627,12 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
           const int64_t o = (int64_t)p * kPprCols;
           if (f0) {
             const float v = p == sr0 ? 1.f : 0.f;
-            X[o + k0] = v;
+            if (X) X[o + k0] = v;
             st_one(Cc + o + k0, v * idg);
           }
           if (f1) {
             const float v = p == sr1 ? 1.f : 0.f;
-            X[o + k1] = v;
+            if (X) X[o + k1] = v;
             st_one(Cc + o + k1, v * idg);
           }
           if (YS) {  // running sums 0; sent sums = the first delta (the whole contribution)
@@ -627,7 +663,12 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         const int64_t l0 = d0 ? S->rec[k0].ldo : 0, l1 = d1 ? S->rec[k1].ldo : 0;
         for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
           const int64_t v = S->new2old[p];
-          const float2 x = ld_state(X, p, lane);
+          float2 x;
+          if (kDelta)  // x of the column's last step from its running sums
+            x = make_float2(x_from_ys(YS, p, k0, s_d[k0], s_seed[k0], s_bprev[k0]),
+                            x_from_ys(YS, p, k1, s_d[k1], s_seed[k1], s_bprev[k1]));
+          else
+            x = ld_state(X, p, lane);
           if (d0) o0[v * l0] = x.x;
           if (d1) o1[v * l1] = x.y;
         }
@@ -650,6 +691,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
         c.b1 = (float)((1.0 - (double)s_d[k1]) + (double)s_d[k1] * s_D[k1]);
         c.s0 = s_seed[k0];
         c.s1 = s_seed[k1];
+        c.bp0 = s_bprev[k0];
+        c.bp1 = s_bprev[k1];
       }
       float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       const int32_t heavy_deg = S->heavy_deg;
@@ -661,7 +704,7 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       for (int32_t p = wr0; p < wr1; ++p) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
-        const float2 xo = on ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
+        const float2 xo = on && X ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
         const float4 ys = on ? ld_ys(YS, p, lane) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane, on);
         if (on) finish_ppr_row(p, y, xo, ys, c, X, YS, Cout, inv_deg, lane, acc);
@@ -683,8 +726,8 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
             yy += v.y;
           }
         }
-        finish_ppr_row(p, make_float2(yx, yy), ld_state(X, p, lane), ld_ys(YS, p, lane), c, X, YS, Cout, inv_deg,
-                       lane, acc);
+        finish_ppr_row(p, make_float2(yx, yy), X ? ld_state(X, p, lane) : make_float2(0.f, 0.f), ld_ys(YS, p, lane),
+                       c, X, YS, Cout, inv_deg, lane, acc);
       }
       for (int v = 0; v < 3; ++v) {
         s_wpart[warp][v][2 * lane] = acc[0][v];
@@ -881,11 +924,12 @@ static int env_cluster() {
   return (k == 1 || k == 2 || k == 4 || k == 8) ? k : 0;
 }
 
-// Bytes per workspace row (64 columns): the rank state, two contribution
-// buffers, and with BF16 deltas the running and sent sums.
+// Bytes per workspace row (64 columns): the rank state and two contribution
+// buffers, or with BF16 deltas two delta buffers and the running and sent sums.
 static int64_t ws_row_bytes(gpr_dtype dt) {
-  const int64_t tsz = (dt == GPR_BF16 || dt == GPR_FP16) ? 2 : 4;
-  return (int64_t)kPprCols * (4 + 2 * tsz + (dt == GPR_BF16 ? 8 : 0));
+  if (dt == GPR_BF16) return (int64_t)kPprCols * (2 * 2 + 8);  // two delta buffers, running and sent sums
+  const int64_t tsz = dt == GPR_FP16 ? 2 : 4;
+  return (int64_t)kPprCols * (4 + 2 * tsz);  // x and two contribution buffers
 }
 
 // One persistent launch over jobs_dev[order[i]], i < order.size(), whose

@@ -26,6 +26,7 @@ struct PprCol {
   float* out;         // where the finished column goes: out[v * ldo], v = node id
   int32_t ldo;
   int32_t stall;      // steps since the residual last reached a new minimum
+  float bused;        // seed coefficient (1 - d) + d D of the latest step (BF16 deltas recompute x from it)
 };
 
 // A column with tol > 0 also stops once its residual has not reached a new
@@ -58,7 +59,8 @@ struct PprJob {
 struct ColState {
   int32_t status, iters;
   double dangling, residual, best;
-  int32_t stall, pad;
+  int32_t stall;
+  float bused;  // seed coefficient used by the step of the launch that wrote this state (1 before the first)
 };
 
 struct SlotDesc {

@@ -120,9 +120,9 @@ static int32_t parts_for(const gpr_server* S, const gpr_graph* g) {
 
 static int64_t slot_bytes(const gpr_server* S, const gpr_graph* g, gpr_dtype dt) {
   const int64_t P = parts_for(S, g);
-  // per row and column: x, two contribution buffers, and with BF16 deltas
-  // the running and sent sums
-  return (int64_t)g->n * kPprCols * (4 + 2 * (int64_t)elem_bytes(dt) + (dt == GPR_BF16 ? 8 : 0)) + (P + 1) * 4 +
+  // per row and column: x and two contribution buffers, or with BF16 deltas
+  // two delta buffers and the running and sent sums
+  return (int64_t)g->n * kPprCols * (dt == GPR_BF16 ? 2 * 2 + 8 : 4 + 2 * (int64_t)elem_bytes(dt)) + (P + 1) * 4 +
          kPprCols * (int64_t)(sizeof(PprCol) + 2 * sizeof(ColState)) + 2 * P * 3 * kPprCols * 8 +
          (int64_t)std::max(g->plan.nchunks, 1) * kPprCols * 4;
 }
@@ -210,7 +210,7 @@ static bool try_admit(gpr_server* S, Req& r, bool existing_only = false) {
       sl->bytes = slot_bytes(S, g, r.dt);
       sl->nparts = parts_for(S, g);
       try {
-        sl->X = (float*)dalloc((size_t)g->n * kPprCols * 4, S->stream);
+        if (r.dt != GPR_BF16) sl->X = (float*)dalloc((size_t)g->n * kPprCols * 4, S->stream);
         sl->C0 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
         sl->C1 = dalloc((size_t)g->n * kPprCols * elem_bytes(r.dt), S->stream);
         if (r.dt == GPR_BF16) sl->YS = (float4*)dalloc((size_t)g->n * kPprCols * 8, S->stream);
