@@ -329,12 +329,16 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       s_maxit[tid] = cr.max_iters;
     }
     __syncthreads();
-    // every column starts at e_seed in X and in the current contribution buffer
+    // every column starts at e_seed in X and in the current contribution
+    // buffer; the other buffer starts at 0 too (rows without in-edges are
+    // never written again: their x stays 0 for every column not seeded there)
     {
       T* Cc = Cb[parity];
+      T* Co = Cb[parity ^ 1];
       for (int64_t i = (int64_t)r0 * kPprCols + tid; i < (int64_t)r1 * kPprCols; i += kPprThreads) {
         if (X) X[i] = 0.f;
         st_one(Cc + i, 0.f);
+        st_one(Co + i, 0.f);
       }
       if (YS)
         for (int64_t i = (int64_t)r0 * 32 + tid; i < (int64_t)r1 * 32; i += kPprThreads)
@@ -389,6 +393,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_kernel(PprJob* __restrict_
       for (int32_t p = r0 + warp; p < r1; p += kPprWarps) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
+        // a row without in-edges keeps x = 0 (and contributions 0) unless it
+        // is a running column's seed
+        if (e0 == e1 && !__any_sync(0xffffffffu, (c.l0 && p == c.s0) || (c.l1 && p == c.s1))) continue;
         const float2 xo = on && X ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
         const float4 ys = on ? ld_ys(YS, p, lane) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane, on);
@@ -616,8 +623,11 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
 
     // ---- fresh columns start at e_seed (X and the current contributions)
     if (mode == kStepInit) {
-      // one pass over the part's rows: every fresh column of a row at once
+      // one pass over the part's rows: every fresh column of a row at once;
+      // the other contribution buffer starts at 0 too (rows without in-edges
+      // are skipped by the steps: their x stays 0 unless seeded there)
       T* Cc = (T*)S->C[S->parity];
+      T* Co = (T*)S->C[S->parity ^ 1];
       const int k0 = 2 * lane, k1 = 2 * lane + 1;
       const bool f0 = S->rec[k0].status == kColFresh, f1 = S->rec[k1].status == kColFresh;
       const int32_t sr0 = s_seed[k0], sr1 = s_seed[k1];
@@ -629,11 +639,13 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
             const float v = p == sr0 ? 1.f : 0.f;
             if (X) X[o + k0] = v;
             st_one(Cc + o + k0, v * idg);
+            st_one(Co + o + k0, 0.f);
           }
           if (f1) {
             const float v = p == sr1 ? 1.f : 0.f;
             if (X) X[o + k1] = v;
             st_one(Cc + o + k1, v * idg);
+            st_one(Co + o + k1, 0.f);
           }
           if (YS) {  // running sums 0; sent sums = the first delta (the whole contribution)
             float4 r = YS[(int64_t)p * 32 + lane];
@@ -704,6 +716,9 @@ __global__ void __launch_bounds__(kPprThreads, 1) ppr_step_kernel(const SlotDesc
       for (int32_t p = wr0; p < wr1; ++p) {
         const int32_t e0 = col_ptr[p], e1 = col_ptr[p + 1];
         if (e1 - e0 > heavy_deg) continue;
+        // a row without in-edges keeps x = 0 (and contributions 0) unless it
+        // is a running column's seed
+        if (e0 == e1 && !__any_sync(0xffffffffu, (c.l0 && p == c.s0) || (c.l1 && p == c.s1))) continue;
         const float2 xo = on && X ? ld_state(X, p, lane) : make_float2(0.f, 0.f);
         const float4 ys = on ? ld_ys(YS, p, lane) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 y = gather_row(row_idx, Cin, e0, e1, lane, on);
