@@ -107,9 +107,21 @@ __device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx
   for (int32_t e = e0; e < e1; e += 32) {
     const int32_t idx = (e + lane < e1) ? __ldcs(row_idx + e + lane) : 0;
     const int cnt = min(32, e1 - e);
-    for (int j = 0; j < cnt; j += 8) {
-      // eight 256-byte row gathers in flight per warp; the tail of a group
-      // is masked (warp-uniform), never gathered one load at a time
+    int j = 0;
+    // eight 256-byte row gathers in flight per warp (128 bytes with 16-bit
+    // storage); whole groups unmasked, then the tail in a group of eight or,
+    // for at most four edges (most rows of a power-law graph), of four
+    for (; j + 8 <= cnt; j += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int32_t u = __shfl_sync(0xffffffffu, idx, j + q);
+        v[q] = on ? ld_pair(C + (int64_t)u * kPprCols + 2 * lane) : make_float2(0.f, 0.f);
+      }
+      ax += ((v[0].x + v[1].x) + (v[2].x + v[3].x)) + ((v[4].x + v[5].x) + (v[6].x + v[7].x));
+      ay += ((v[0].y + v[1].y) + (v[2].y + v[3].y)) + ((v[4].y + v[5].y) + (v[6].y + v[7].y));
+    }
+    if (cnt - j > 4) {
       float2 v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -118,6 +130,15 @@ __device__ __forceinline__ float2 gather_row(const int32_t* __restrict__ row_idx
       }
       ax += ((v[0].x + v[1].x) + (v[2].x + v[3].x)) + ((v[4].x + v[5].x) + (v[6].x + v[7].x));
       ay += ((v[0].y + v[1].y) + (v[2].y + v[3].y)) + ((v[4].y + v[5].y) + (v[6].y + v[7].y));
+    } else if (cnt - j > 0) {
+      float2 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t u = __shfl_sync(0xffffffffu, idx, (j + q) & 31);
+        v[q] = (on && j + q < cnt) ? ld_pair(C + (int64_t)u * kPprCols + 2 * lane) : make_float2(0.f, 0.f);
+      }
+      ax += (v[0].x + v[1].x) + (v[2].x + v[3].x);
+      ay += (v[0].y + v[1].y) + (v[2].y + v[3].y);
     }
   }
   return make_float2(ax, ay);
