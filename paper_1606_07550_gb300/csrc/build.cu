@@ -610,6 +610,31 @@ __global__ void transpose_keys_kernel(const int32_t* __restrict__ col_ptr, const
 void graph_free_device(gpr_graph* g, cudaStream_t s);
 void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
 
+// The copy stream and events of a chunked host-to-device COO copy, one set
+// per device, made on first use and kept for the process.  Builds that take
+// host input on one device are serialised by its mutex.
+constexpr int kCopyChunks = 8;
+struct CopyLane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t start = nullptr;
+  cudaEvent_t done[kCopyChunks] = {};
+  std::mutex mu;
+};
+static CopyLane& copy_lane() {
+  static CopyLane lanes[64];
+  static std::once_flag made[64];
+  int d = device_ordinal();
+  if (d < 0 || d >= 64) d = 0;
+  CopyLane& l = lanes[d];
+  std::call_once(made[d], [&l] {
+    cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&l.start, cudaEventDisableTiming);
+    for (int c = 0; c < kCopyChunks; ++c) cudaEventCreateWithFlags(&l.done[c], cudaEventDisableTiming);
+  });
+  if (!l.stream || !l.start) throw CudaFail{cudaErrorUnknown, "creating the copy stream of a host COO"};
+  return l;
+}
+
 gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_raw, int32_t n, int flags,
                        cudaStream_t s, gpr_graph** out) {
   gpr_graph* g = new gpr_graph();
@@ -625,21 +650,36 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
     const int32_t* src = src_in;
     const int32_t* dst = dst_in;
-    if ((flags & GPR_PTR_HOST) && m_raw > 0) {
-      int32_t* s_dev = (int32_t*)tmp.get((size_t)m_raw * 4);
-      int32_t* d_dev = (int32_t*)tmp.get((size_t)m_raw * 4);
-      GPR_CUDA(cudaMemcpyAsync(s_dev, src_in, (size_t)m_raw * 4, cudaMemcpyHostToDevice, s));
-      GPR_CUDA(cudaMemcpyAsync(d_dev, dst_in, (size_t)m_raw * 4, cudaMemcpyHostToDevice, s));
-      src = s_dev;
-      dst = d_dev;
-      trace_phase("build: copy of the COO", s);
-    }
     // 1. relabelling pi: nodes by descending raw out-degree (ties: ascending id)
     int32_t* odeg = (int32_t*)tmp.get((size_t)n * 4);
     int32_t* maxd = (int32_t*)tmp.get(8);
     GPR_CUDA(cudaMemsetAsync(odeg, 0, (size_t)n * 4, s));
     GPR_CUDA(cudaMemsetAsync(maxd, 0, 8, s));
-    if (m_raw > 0) {
+    if ((flags & GPR_PTR_HOST) && m_raw > 0) {
+      // a host COO goes up in chunks on a copy stream; each chunk's raw
+      // out-degrees are counted on `s` while the next chunk is in flight
+      int32_t* s_dev = (int32_t*)tmp.get((size_t)m_raw * 4);
+      int32_t* d_dev = (int32_t*)tmp.get((size_t)m_raw * 4);
+      CopyLane& cp = copy_lane();
+      std::lock_guard<std::mutex> lk(cp.mu);
+      GPR_CUDA(cudaEventRecord(cp.start, s));  // the copy stream waits for the allocations and memsets
+      GPR_CUDA(cudaStreamWaitEvent(cp.stream, cp.start, 0));
+      const int64_t chunk = (m_raw + kCopyChunks - 1) / kCopyChunks;
+      for (int c = 0; c < kCopyChunks; ++c) {
+        const int64_t off = c * chunk, len = std::min<int64_t>(chunk, m_raw - off);
+        if (len <= 0) break;
+        GPR_CUDA(cudaMemcpyAsync(s_dev + off, src_in + off, (size_t)len * 4, cudaMemcpyHostToDevice, cp.stream));
+        GPR_CUDA(cudaMemcpyAsync(d_dev + off, dst_in + off, (size_t)len * 4, cudaMemcpyHostToDevice, cp.stream));
+        GPR_CUDA(cudaEventRecord(cp.done[c], cp.stream));
+        GPR_CUDA(cudaStreamWaitEvent(s, cp.done[c], 0));
+        degree_kernel<<<grid_for(len), kThreads, 0, s>>>(s_dev + off, d_dev + off, len, n, odeg, derr);
+        GPR_CUDA(cudaGetLastError());
+        count_launches(1);
+      }
+      src = s_dev;
+      dst = d_dev;
+      trace_phase("build: copy of the COO + raw out-degrees", s);
+    } else if (m_raw > 0) {
       degree_kernel<<<grid_for(m_raw), kThreads, 0, s>>>(src, dst, m_raw, n, odeg, derr);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
