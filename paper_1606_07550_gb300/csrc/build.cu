@@ -154,18 +154,18 @@ __global__ void digit_starts_kernel(const uint32_t* __restrict__ hist, uint32_t*
   starts[p * 256 + t] = s[t] - v;
 }
 
-// One stable counting pass on digit (key >> shift) & 255.  Keys of a tile are
+// One stable counting pass on digit (key >> kShift) & 255.  Keys of a tile are
 // held warp-striped (item j of warp w is tile position w*512 + j*32 + lane),
 // so (warp, item, lane) order is input order and the per-warp match-based
 // ranking keeps the sort stable.
+template <int kShift>
 __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
-    const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
+    const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
     const uint32_t* __restrict__ dstart, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
     uint32_t epoch, int* __restrict__ derr) {
   __shared__ uint64_t s_keys[kTile];
   __shared__ uint32_t s_wcnt[kWarps][256];
-  __shared__ uint32_t s_tstart[256];
-  __shared__ uint64_t s_gbase[256];
+  __shared__ uint64_t s_goff[256];
   __shared__ uint32_t s_wsum[kWarps];
   __shared__ uint32_t s_tile;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
-    const uint32_t d = (uint32_t)(k[j] >> shift) & 255u;
+    const uint32_t d = (uint32_t)(k[j] >> kShift) & 255u;
     // the lanes holding the same digit: one vote per digit bit
     uint32_t peers = 0xffffffffu;
 #pragma unroll
@@ -223,32 +223,52 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     if (lane >= o) v += y;
   }
   if (lane == 31) s_wsum[w] = v;
+  __syncthreads();
+  uint32_t woff = 0;
+  for (int ww = 0; ww < w; ++ww) woff += s_wsum[ww];
+  const uint32_t tstart = woff + v - cnt;
+  // s_wcnt[w][d]: where warp w's first key of digit d goes in the tile
+#pragma unroll
+  for (int ww = 0; ww < kWarps; ++ww) s_wcnt[ww][t] += tstart;
+  __syncthreads();
+
+  // the tile in digit order in shared memory, before the look-back, so that
+  // no key is held in registers while the predecessors are waited for
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const uint32_t d = (uint32_t)(k[j] >> kShift) & 255u;
+    s_keys[s_wcnt[w][d] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu)] = k[j];
+  }
 
   uint64_t excl = 0;
   if (tile != 0) {
     excl = lookback(status + t, tile, 256, epoch, derr);
     st_relaxed_u64(status + tile * 256 + t, lb_word(epoch, kFlagInc, excl + cnt));
   }
-  s_gbase[t] = (uint64_t)dstart[t] + excl;
+  // output index of tile position i with digit d: s_goff[d] + i (the digit's
+  // global start is at least its tile-local start, so no wrap)
+  s_goff[t] = (uint64_t)dstart[t] + excl - tstart;
   __syncthreads();
-  uint32_t woff = 0;
-  for (int ww = 0; ww < w; ++ww) woff += s_wsum[ww];
-  s_tstart[t] = woff + v - cnt;
-  __syncthreads();
-
-#pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const uint32_t d = (uint32_t)(k[j] >> shift) & 255u;
-    s_keys[s_tstart[d] + s_wcnt[w][d] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu)] = k[j];
-  }
-  __syncthreads();
-  for (int i = t; i < kTile; i += kThreads) {
-    const uint64_t key = s_keys[i];
-    const uint32_t d = (uint32_t)(key >> shift) & 255u;
-    const uint64_t dst = s_gbase[d] + (uint64_t)(i - (int)s_tstart[d]);
-    if (dst < (uint64_t)n) out[dst] = key;
+  if ((tile + 1) * kTile <= n) {  // a full tile: every index is below n
+#pragma unroll 4
+    for (int i = t; i < kTile; i += kThreads) {
+      const uint64_t key = s_keys[i];
+      out[s_goff[(uint32_t)(key >> kShift) & 255u] + (uint64_t)i] = key;
+    }
+  } else {
+    for (int i = t; i < kTile; i += kThreads) {
+      const uint64_t key = s_keys[i];
+      const uint64_t dst = s_goff[(uint32_t)(key >> kShift) & 255u] + (uint64_t)i;
+      if (dst < (uint64_t)n) out[dst] = key;
+    }
   }
 }
+
+using SweepKernel = void (*)(const uint64_t*, uint64_t*, int64_t, const uint32_t*, uint64_t*, uint32_t*, uint32_t,
+                            int*);
+static const SweepKernel kSweeps[8] = {onesweep_kernel<0>,  onesweep_kernel<8>,  onesweep_kernel<16>,
+                                       onesweep_kernel<24>, onesweep_kernel<32>, onesweep_kernel<40>,
+                                       onesweep_kernel<48>, onesweep_kernel<56>};
 
 uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cudaStream_t s,
                          int* derr, uint32_t* hist_in) {
@@ -280,14 +300,14 @@ uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cud
     count_launches(1);
     static std::once_flag carveout;  // four 44 KB blocks per SM need the largest shared-memory carve-out
     std::call_once(carveout, [] {
-      cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           (int)cudaSharedmemCarveoutMaxShared);
+      for (SweepKernel f : kSweeps)
+        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     });
     uint64_t* a = keys;
     uint64_t* b = alt;
     for (int p = 0; p < passes; ++p) {
-      onesweep_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(a, b, n, 8 * p, starts + 256 * p, status,
-                                                          ctr + p, (uint32_t)(p + 1), derr);
+      kSweeps[p]<<<(unsigned)tiles, kThreads, 0, s>>>(a, b, n, starts + 256 * p, status, ctr + p, (uint32_t)(p + 1),
+                                                      derr);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       std::swap(a, b);
@@ -307,17 +327,35 @@ uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cud
 }
 
 // ------------------------------------------------- relabelling (pi) --
+// L2 eviction priority "last" for the node-sized arrays that random accesses
+// hit (the counters, the relabelling map), so that the streamed edge arrays
+// do not push them out.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int32_t ld_keep(const int32_t* a, uint64_t pol) {
+  int32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void red_add_keep(int32_t* a, int32_t v, uint64_t pol) {
+  asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+
 // Raw out-degree counts (duplicates included) of the COO stream, and the
 // id check: an id outside [0, n) raises DERR_BAD_ID.
 __global__ void degree_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
                               int32_t n, int32_t* __restrict__ odeg, int* __restrict__ derr) {
   bool bad = false;
+  const uint64_t keep = l2_keep_policy();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = __ldcs(src + i), v = __ldcs(dst + i);
     if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
       bad = true;
     } else if (u != v) {
-      atomicAdd(odeg + u, 1);
+      red_add_keep(odeg + u, 1, keep);
     }
   }
   if (bad) atomicOr(derr, DERR_BAD_ID);
@@ -364,6 +402,7 @@ __global__ void pack_kernel(const int32_t* __restrict__ src, const int32_t* __re
   extern __shared__ uint32_t sh[];
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) sh[i] = 0;
   __syncthreads();
+  const uint64_t keep = l2_keep_policy();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t u = __ldcs(src + i), v = __ldcs(dst + i);
     uint64_t key;
@@ -371,12 +410,12 @@ __global__ void pack_kernel(const int32_t* __restrict__ src, const int32_t* __re
       key = kSentinel;
     } else {
       if (map) {
-        u = map[u];
-        v = map[v];
+        u = ld_keep(map + u, keep);
+        v = ld_keep(map + v, keep);
       }
       key = ((uint64_t)(uint32_t)v << b) | (uint32_t)u;
     }
-    keys[i] = key;
+    __stcs(keys + i, key);
     for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((key >> (8 * p)) & 255)], 1u);
   }
   __syncthreads();
@@ -573,6 +612,7 @@ static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b,
   if (!degree_from_raw) GPR_CUDA(cudaMemsetAsync(outdeg, 0, (size_t)n * 4, s));
   if (m_keys == 0) return 0;
   uint64_t* sorted = presorted ? keys : radix_sort_u64(keys, alt, m_keys, 2 * b, s, derr, hist);
+  trace_phase("build: sort", s);
   const int64_t tiles = (m_keys + kTile - 1) / kTile;
   uint64_t* status = (uint64_t*)tmp.get((size_t)tiles * 8);
   uint32_t* ctr = (uint32_t*)tmp.get(8);
@@ -743,7 +783,7 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     if (m > 0)
       GPR_CUDA(cudaMemcpyAsync(g->row_idx, row_idx_full, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
     tmp.release();
-    trace_phase("build: sort + dedupe", s);
+    trace_phase("build: dedupe", s);
     // 3. execution layout (degree buckets, chunks, inverse degrees)
     int* derr2 = (int*)dalloc(8, s);
     GPR_CUDA(cudaMemsetAsync(derr2, 0, 8, s));

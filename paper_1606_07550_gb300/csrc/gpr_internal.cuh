@@ -226,18 +226,35 @@ __device__ __forceinline__ uint64_t lb_word(uint32_t epoch, uint64_t flag, uint6
 // Decoupled look-back (Merrill and Garland, "Single-pass parallel prefix scan
 // with decoupled look-back", 2016): the exclusive prefix of tile `tile` from
 // the status words of tiles tile-1, tile-2, ... (stride `stride` words apart).
-// Every wait is bounded; on timeout it sets DERR_TIMEOUT and returns what it
-// has.
+// The words of kLookBatch predecessors are read at once, so one round trip to
+// L2 walks past up to kLookBatch aggregates.  Every wait is bounded; on
+// timeout it sets DERR_TIMEOUT and returns what it has.
+constexpr int kLookBatch = 4;
 __device__ __forceinline__ uint64_t lookback(const uint64_t* status, int64_t tile, int64_t stride,
                                              uint32_t epoch, int* derr) {
   uint64_t excl = 0;
   int64_t k = tile - 1;
   uint32_t spins = 0;
   while (k >= 0) {
-    uint64_t w = ld_relaxed_u64(status + k * stride);
-    uint32_t ep = (uint32_t)(w >> 60);
-    uint64_t fl = (w >> 58) & 3;
-    if (ep != epoch || fl == 0) {
+    uint64_t w[kLookBatch];
+#pragma unroll
+    for (int j = 0; j < kLookBatch; ++j) w[j] = k - j >= 0 ? ld_relaxed_u64(status + (k - j) * stride) : 0ull;
+    // take the published words in order, up to the first inclusive one
+    int took = 0;
+    bool inc = false;
+#pragma unroll
+    for (int j = 0; j < kLookBatch; ++j) {
+      const uint64_t fl = (w[j] >> 58) & 3;
+      const bool ok = (uint32_t)(w[j] >> 60) == epoch && fl != 0;
+      if (took == j && !inc && ok) {
+        excl += w[j] & kValMask;
+        took = j + 1;
+        inc = fl == kFlagInc;
+      }
+    }
+    if (inc) break;
+    k -= took;
+    if (took == 0) {
       if (++spins > kSpinLimit) {
         atomicOr(derr, DERR_TIMEOUT);
         return excl;
@@ -247,11 +264,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* status, int64_t til
         // once any waiter has given up, the rest of the grid stops waiting too
         if ((spins & 255) == 0 && (*(volatile int*)derr & DERR_TIMEOUT)) return excl;
       }
-      continue;
     }
-    excl += w & kValMask;
-    if (fl == kFlagInc) break;
-    --k;
   }
   return excl;
 }

@@ -204,6 +204,7 @@ void plan_build(gpr_graph* g, cudaStream_t s, int* derr) {
     int bb = 1;
     while ((1 << bb) < nb) ++bb;
     uint64_t* sorted = radix_sort_u64(keys, alt, n, b + bb, s, derr, nullptr);
+    trace_phase("plan: bucket keys + sort", s);
     row_lists_kernel<<<grid_for(n), kPThreads, 0, s>>>(sorted, n, b, P.rows, pd);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
@@ -227,6 +228,7 @@ void plan_build(gpr_graph* g, cudaStream_t s, int* derr) {
     P.hot_H = 0;
     const char* hot_env = getenv("GPR_HOT");
     if (hot_env) P.hot_H = std::max<int32_t>(0, std::min<int32_t>(std::min(hot_capacity(), n), atoi(hot_env))) & ~7;
+    trace_phase("plan: bucket lists", s);
     P.split = (int32_t*)dalloc((size_t)n * 4, s);
     split_kernel<<<grid_for(n), kPThreads, 0, s>>>(g->col_ptr, g->row_idx, n, P.hot_H, P.split);
     GPR_CUDA(cudaGetLastError());
@@ -286,6 +288,7 @@ void plan_build(gpr_graph* g, cudaStream_t s, int* derr) {
     P.split_cbeg = up(scb);
     P.split_cend = up(sce);
     GPR_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
+    trace_phase("plan: split + long-row chunks", s);
     for (void* p : tmp) dfree(p, s);
   } catch (...) {
     for (void* p : tmp) dfree(p, s);
