@@ -83,7 +83,7 @@ def workload(name):
 
 # sources of the kernels a recorded DRAM-traffic figure depends on (the
 # graph layout and the PageRank step)
-TRAFFIC_SOURCES = ("blocked.cu", "blocked.cuh", "pr_step.cuh")  # the measured kernels and their layout
+TRAFFIC_SOURCES = ("blocked_kernels.cuh", "pr_step.cuh")  # the measured kernels and the layout kernels
 
 
 def src_hash():
@@ -428,34 +428,35 @@ def run_gpr(args, world, rank, local):
         g = gpr.graph_build(hs, hd, n, stream=stream)
         gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream, spmv=args.spmv)
         g.free()
-        # this host's pinned host-to-device bandwidth on the whole source
-        # buffer (the copy's share of the end-to-end step differs from host to
-        # host, and with the host memory's state)
-        probe = torch.empty(m_raw, dtype=torch.int32, device="cuda")
-        h2d_gbs = 0.0
-        for _ in range(2):
+        # the host link's pinned host-to-device rate (1 GiB of the source
+        # buffer), probed after each step outside its time: on a machine
+        # shared with other jobs it varies from copy to copy
+        probe = torch.empty(1 << 28, dtype=torch.int32, device="cuda")
+
+        def link_gbs():
             torch.cuda.synchronize()
             tp = time.perf_counter()
-            probe.copy_(hs, non_blocking=True)
+            probe.copy_(hs[:1 << 28], non_blocking=True)
             torch.cuda.synchronize()
-            h2d_gbs = max(h2d_gbs, 4 * m_raw / (time.perf_counter() - tp) / 1e9)
-        del probe
+            return (1 << 30) / (time.perf_counter() - tp) / 1e9
+
         barrier(world)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        each = []
+        each, link = [], [link_gbs()]
         for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
             ts = time.perf_counter()
             g = gpr.graph_build(hs, hd, n, stream=stream)
             gpr.pagerank(g, hout, damping=DAMPING, iters=iters, stream=stream, spmv=args.spmv)
             g.free()
-            each.append((time.perf_counter() - ts) * 1e3)  # pagerank into host memory returns after the copy
-        torch.cuda.synchronize()
-        t_e2e = (time.perf_counter() - t0) / args.e2e_steps
+            torch.cuda.synchronize()
+            each.append((time.perf_counter() - ts) * 1e3)
+            link.append(link_gbs())
+        del probe
+        t_e2e = sum(each) / len(each) * 1e-3
         t_e2e = max_over_ranks(world, t_e2e)
         e2e = {"value": edges_all * iters / t_e2e / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": 8 * m_raw, "d2h_bytes_per_step": 4 * n, "ms_per_step": t_e2e * 1e3,
-               "pinned_h2d_gbs": h2d_gbs, "ms_each": each}
+               "ms_each": each, "host_link_gbs": link}
 
     if rank != 0:
         return

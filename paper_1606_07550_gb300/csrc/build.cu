@@ -7,9 +7,10 @@
 //   pack     key = dst << b | src  (b = id bits); self-loops and invalid ids
 //            become the sentinel ~0, which sorts last; the per-pass digit
 //            histograms of the radix sort are counted in the same pass
-//   sort     LSD radix sort, 8-bit digits, one read + one write of the keys
-//            per pass (onesweep: Adinets and Merrill, 2022), tile prefixes by
-//            decoupled look-back
+//   sort     LSD radix sort, 8-bit digits (the last ones 9 bits wide where
+//            that saves a pass: 50-bit keys in 6 passes), one read + one write
+//            of the keys per pass (onesweep: Adinets and Merrill, 2022), tile
+//            prefixes by decoupled look-back
 //   dedupe   keep the first of each run of equal keys, drop sentinels;
 //            compaction by decoupled look-back; writes row_idx, the CSC
 //            offsets (row starts plus gap fill) and out-degrees in one pass
@@ -123,54 +124,87 @@ void dfree(void* p, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ histograms --
-__global__ void hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int passes,
+// Digits of an LSD sort of `bits`-bit keys: 8-bit digits, or, where that takes
+// a pass fewer, the last (bits - 8 * passes) digits 9 bits wide; with 9-bit
+// digits the passes cover exactly `bits` bits, with 8-bit ones whole bytes.
+DigitPlan digit_plan(int bits) {
+  DigitPlan d{};
+  bits = std::max(0, std::min(bits, 64));
+  const int p8 = (bits + 7) / 8, p9 = (bits + 8) / 9;
+  d.passes = p9 < p8 ? p9 : p8;
+  const int nine = p9 < p8 ? bits - 8 * p9 : 0;  // the last `nine` passes are 9 bits wide
+  int sh = 0;
+  for (int p = 0; p < d.passes; ++p) {
+    d.shift[p] = sh;
+    d.width[p] = p >= d.passes - nine ? 9 : 8;
+    sh += d.width[p];
+  }
+  return d;
+}
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, const DigitPlan& dp, int p) {
+  return (uint32_t)(k >> dp.shift[p]) & ((1u << dp.width[p]) - 1u);
+}
+
+// Digit counts of every pass: hist[p * kMaxRadix + digit].
+__global__ void hist_kernel(const uint64_t* __restrict__ keys, int64_t n, DigitPlan dp,
                             uint32_t* __restrict__ hist) {
   extern __shared__ uint32_t sh[];
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) sh[i] = 0;
+  for (int i = threadIdx.x; i < dp.passes * kMaxRadix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t k = keys[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255)], 1u);
+    const uint64_t k = keys[i];
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p)
+      if (p < dp.passes) atomicAdd(&sh[p * kMaxRadix + digit_of(k, dp, p)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
+  for (int i = threadIdx.x; i < dp.passes * kMaxRadix; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// Exclusive scan of each pass's 256 digit counts (block p = pass p).
-__global__ void digit_starts_kernel(const uint32_t* __restrict__ hist, uint32_t* __restrict__ starts) {
-  __shared__ uint32_t s[256];
+// Exclusive scan of each pass's digit counts (block p = pass p, kMaxRadix
+// threads).
+__global__ void digit_starts_kernel(const uint32_t* __restrict__ hist, DigitPlan dp, uint32_t* __restrict__ starts) {
+  __shared__ uint32_t s[kMaxRadix];
   const int p = blockIdx.x, t = threadIdx.x;
-  const uint32_t v = hist[p * 256 + t];
+  const uint32_t v = t < (1 << dp.width[p]) ? hist[p * kMaxRadix + t] : 0u;
   s[t] = v;
   __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
+  for (int o = 1; o < kMaxRadix; o <<= 1) {
     uint32_t a = t >= o ? s[t - o] : 0;
     __syncthreads();
     s[t] += a;
     __syncthreads();
   }
-  starts[p * 256 + t] = s[t] - v;
+  starts[p * kMaxRadix + t] = s[t] - v;
 }
 
-// One stable counting pass on digit (key >> kShift) & 255.  Keys of a tile are
-// held warp-striped (item j of warp w is tile position w*512 + j*32 + lane),
-// so (warp, item, lane) order is input order and the per-warp match-based
-// ranking keeps the sort stable.
-template <int kShift>
+// One stable counting pass on the kBits-bit digit (key >> shift); the shift
+// is kShift, or the argument where kShift is -1.  Keys of a tile are held
+// warp-striped (item j of warp w is tile position w*512 + j*32 + lane), so
+// (warp, item, lane) order is input order and the per-warp match-based
+// ranking keeps the sort stable.  Thread t owns digits kDPT*t .. kDPT*t +
+// kDPT - 1 for the tile's scans and look-backs.
+template <int kBits, int kShift>
 __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
-    const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
+    const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift_arg,
     const uint32_t* __restrict__ dstart, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
     uint32_t epoch, int* __restrict__ derr) {
+  const int shift = kShift >= 0 ? kShift : shift_arg;
+  constexpr int kRadix = 1 << kBits;
+  constexpr uint32_t kMask = kRadix - 1;
+  constexpr int kDPT = kRadix / kThreads;
+  static_assert(kDPT >= 1 && kDPT * kThreads == kRadix, "whole digits per thread");
   __shared__ uint64_t s_keys[kTile];
-  __shared__ uint32_t s_wcnt[kWarps][256];
-  __shared__ uint64_t s_goff[256];
+  __shared__ uint32_t s_wcnt[kWarps][kRadix];
+  __shared__ uint64_t s_goff[kRadix];
   __shared__ uint32_t s_wsum[kWarps];
   __shared__ uint32_t s_tile;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (t == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  for (int i = t; i < kWarps * 256; i += kThreads) (&s_wcnt[0][0])[i] = 0;
+  for (int i = t; i < kWarps * kRadix; i += kThreads) (&s_wcnt[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t base = tile * kTile + (int64_t)w * (kItems * 32) + lane;
@@ -185,11 +219,11 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
-    const uint32_t d = (uint32_t)(k[j] >> kShift) & 255u;
+    const uint32_t d = (uint32_t)(k[j] >> shift) & kMask;
     // the lanes holding the same digit: one vote per digit bit
     uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int bb = 0; bb < 8; ++bb) {
+    for (int bb = 0; bb < kBits; ++bb) {
       const uint32_t bit = (d >> bb) & 1u;
       const uint32_t vote = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? vote : ~vote;
@@ -202,21 +236,29 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
   }
   __syncthreads();
 
-  // thread t owns digit t: per-warp exclusive offsets and the tile count
-  uint32_t cnt = 0;
+  // per owned digit: per-warp exclusive offsets and the tile count
+  uint32_t cnt[kDPT];
+  uint32_t tsum = 0;
 #pragma unroll
-  for (int ww = 0; ww < kWarps; ++ww) {
-    uint32_t v = s_wcnt[ww][t];
-    s_wcnt[ww][t] = cnt;
-    cnt += v;
+  for (int q = 0; q < kDPT; ++q) {
+    const int d = kDPT * t + q;
+    uint32_t c = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      const uint32_t v = s_wcnt[ww][d];
+      s_wcnt[ww][d] = c;
+      c += v;
+    }
+    cnt[q] = c;
+    tsum += c;
+    if (tile == 0)
+      st_relaxed_u64(status + d, lb_word(epoch, kFlagInc, c));
+    else
+      st_relaxed_u64(status + tile * kRadix + d, lb_word(epoch, kFlagAgg, c));
   }
-  if (tile == 0)
-    st_relaxed_u64(status + t, lb_word(epoch, kFlagInc, cnt));
-  else
-    st_relaxed_u64(status + tile * 256 + t, lb_word(epoch, kFlagAgg, cnt));
 
-  // tile-local exclusive scan over digits
-  uint32_t v = cnt;
+  // tile-local exclusive scan over digits (thread order is digit order)
+  uint32_t v = tsum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
@@ -226,55 +268,69 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
   __syncthreads();
   uint32_t woff = 0;
   for (int ww = 0; ww < w; ++ww) woff += s_wsum[ww];
-  const uint32_t tstart = woff + v - cnt;
+  uint32_t tstart[kDPT];
+  tstart[0] = woff + v - tsum;
+#pragma unroll
+  for (int q = 1; q < kDPT; ++q) tstart[q] = tstart[q - 1] + cnt[q - 1];
   // s_wcnt[w][d]: where warp w's first key of digit d goes in the tile
 #pragma unroll
-  for (int ww = 0; ww < kWarps; ++ww) s_wcnt[ww][t] += tstart;
+  for (int q = 0; q < kDPT; ++q)
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) s_wcnt[ww][kDPT * t + q] += tstart[q];
   __syncthreads();
 
   // the tile in digit order in shared memory, before the look-back, so that
   // no key is held in registers while the predecessors are waited for
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
-    const uint32_t d = (uint32_t)(k[j] >> kShift) & 255u;
+    const uint32_t d = (uint32_t)(k[j] >> shift) & kMask;
     s_keys[s_wcnt[w][d] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu)] = k[j];
   }
 
-  uint64_t excl = 0;
-  if (tile != 0) {
-    excl = lookback(status + t, tile, 256, epoch, derr);
-    st_relaxed_u64(status + tile * 256 + t, lb_word(epoch, kFlagInc, excl + cnt));
+#pragma unroll
+  for (int q = 0; q < kDPT; ++q) {
+    const int d = kDPT * t + q;
+    uint64_t excl = 0;
+    if (tile != 0) {
+      excl = lookback(status + d, tile, kRadix, epoch, derr);
+      st_relaxed_u64(status + tile * kRadix + d, lb_word(epoch, kFlagInc, excl + cnt[q]));
+    }
+    // output index of tile position i with digit d: s_goff[d] + i (the digit's
+    // global start is at least its tile-local start, so no wrap)
+    s_goff[d] = (uint64_t)dstart[d] + excl - tstart[q];
   }
-  // output index of tile position i with digit d: s_goff[d] + i (the digit's
-  // global start is at least its tile-local start, so no wrap)
-  s_goff[t] = (uint64_t)dstart[t] + excl - tstart;
   __syncthreads();
   if ((tile + 1) * kTile <= n) {  // a full tile: every index is below n
 #pragma unroll 4
     for (int i = t; i < kTile; i += kThreads) {
       const uint64_t key = s_keys[i];
-      out[s_goff[(uint32_t)(key >> kShift) & 255u] + (uint64_t)i] = key;
+      out[s_goff[(uint32_t)(key >> shift) & kMask] + (uint64_t)i] = key;
     }
   } else {
     for (int i = t; i < kTile; i += kThreads) {
       const uint64_t key = s_keys[i];
-      const uint64_t dst = s_goff[(uint32_t)(key >> kShift) & 255u] + (uint64_t)i;
+      const uint64_t dst = s_goff[(uint32_t)(key >> shift) & kMask] + (uint64_t)i;
       if (dst < (uint64_t)n) out[dst] = key;
     }
   }
 }
 
-using SweepKernel = void (*)(const uint64_t*, uint64_t*, int64_t, const uint32_t*, uint64_t*, uint32_t*, uint32_t,
-                            int*);
-static const SweepKernel kSweeps[8] = {onesweep_kernel<0>,  onesweep_kernel<8>,  onesweep_kernel<16>,
-                                       onesweep_kernel<24>, onesweep_kernel<32>, onesweep_kernel<40>,
-                                       onesweep_kernel<48>, onesweep_kernel<56>};
+using SweepKernel = void (*)(const uint64_t*, uint64_t*, int64_t, int, const uint32_t*, uint64_t*, uint32_t*,
+                            uint32_t, int*);
+// 8-bit passes at whole bytes (shift fixed at compile time), 9-bit passes
+static const SweepKernel kSweep8[8] = {onesweep_kernel<8, 0>,  onesweep_kernel<8, 8>,  onesweep_kernel<8, 16>,
+                                       onesweep_kernel<8, 24>, onesweep_kernel<8, 32>, onesweep_kernel<8, 40>,
+                                       onesweep_kernel<8, 48>, onesweep_kernel<8, 56>};
+static const SweepKernel kSweep9 = onesweep_kernel<9, -1>;
 
 uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cudaStream_t s,
                          int* derr, uint32_t* hist_in) {
-  const int passes = (bits + 7) / 8;
+  const DigitPlan dp = digit_plan(bits);
+  const int passes = dp.passes;
   if (n <= 1 || passes == 0) return keys;
   const int64_t tiles = (n + kTile - 1) / kTile;
+  int radix = 0;
+  for (int p = 0; p < passes; ++p) radix = std::max(radix, 1 << dp.width[p]);
   uint32_t* hist = hist_in;
   uint32_t* own_hist = nullptr;
   uint32_t* starts = nullptr;
@@ -282,32 +338,36 @@ uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cud
   uint32_t* ctr = nullptr;
   try {
     if (!hist) {
-      own_hist = (uint32_t*)dalloc(passes * 256 * sizeof(uint32_t), s);
+      own_hist = (uint32_t*)dalloc(passes * kMaxRadix * sizeof(uint32_t), s);
       hist = own_hist;
-      GPR_CUDA(cudaMemsetAsync(hist, 0, passes * 256 * sizeof(uint32_t), s));
+      GPR_CUDA(cudaMemsetAsync(hist, 0, passes * kMaxRadix * sizeof(uint32_t), s));
       int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)num_sms() * 8);
-      hist_kernel<<<grid, kThreads, passes * 256 * sizeof(uint32_t), s>>>(keys, n, passes, hist);
+      hist_kernel<<<grid, kThreads, passes * kMaxRadix * sizeof(uint32_t), s>>>(keys, n, dp, hist);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
     }
-    starts = (uint32_t*)dalloc(passes * 256 * sizeof(uint32_t), s);
-    status = (uint64_t*)dalloc((size_t)tiles * 256 * sizeof(uint64_t), s);
+    starts = (uint32_t*)dalloc(passes * kMaxRadix * sizeof(uint32_t), s);
+    status = (uint64_t*)dalloc((size_t)tiles * radix * sizeof(uint64_t), s);
     ctr = (uint32_t*)dalloc(passes * sizeof(uint32_t), s);
-    GPR_CUDA(cudaMemsetAsync(status, 0, (size_t)tiles * 256 * sizeof(uint64_t), s));
+    GPR_CUDA(cudaMemsetAsync(status, 0, (size_t)tiles * radix * sizeof(uint64_t), s));
     GPR_CUDA(cudaMemsetAsync(ctr, 0, passes * sizeof(uint32_t), s));
-    digit_starts_kernel<<<passes, 256, 0, s>>>(hist, starts);
+    digit_starts_kernel<<<passes, kMaxRadix, 0, s>>>(hist, dp, starts);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
-    static std::once_flag carveout;  // four 44 KB blocks per SM need the largest shared-memory carve-out
+    static std::once_flag carveout;  // four blocks per SM need the largest shared-memory carve-out
     std::call_once(carveout, [] {
-      for (SweepKernel f : kSweeps)
+      for (SweepKernel f : kSweep8)
         cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+      cudaFuncSetAttribute(kSweep9, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
     });
     uint64_t* a = keys;
     uint64_t* b = alt;
     for (int p = 0; p < passes; ++p) {
-      kSweeps[p]<<<(unsigned)tiles, kThreads, 0, s>>>(a, b, n, starts + 256 * p, status, ctr + p, (uint32_t)(p + 1),
-                                                      derr);
+      // 8-bit digits start at whole bytes until the first 9-bit one
+      const SweepKernel f = dp.width[p] == 9 ? kSweep9 : kSweep8[dp.shift[p] / 8];
+      f<<<(unsigned)tiles, kThreads, 0, s>>>(a, b, n, dp.shift[p], starts + kMaxRadix * p, status, ctr + p,
+                                             (uint32_t)(p + 1), derr);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       std::swap(a, b);
@@ -395,12 +455,13 @@ __global__ void perm_from_sorted_kernel(const uint64_t* __restrict__ sorted, int
 // -------------------------------------------------------------- packing --
 // key = map(dst) << b | map(src) (map = identity if null); a self-loop or an
 // id outside [0, n) becomes the sentinel, which sorts last.  Counts the digit
-// histograms of all radix passes on the way.
+// histograms of all radix passes on the way (hist[p * kMaxRadix + digit];
+// none when dp.passes is 0).
 __global__ void pack_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                            int32_t n, int b, const int32_t* __restrict__ map, int passes,
+                            int32_t n, int b, const int32_t* __restrict__ map, DigitPlan dp,
                             uint64_t* __restrict__ keys, uint32_t* __restrict__ hist) {
   extern __shared__ uint32_t sh[];
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) sh[i] = 0;
+  for (int i = threadIdx.x; i < dp.passes * kMaxRadix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const uint64_t keep = l2_keep_policy();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -416,10 +477,12 @@ __global__ void pack_kernel(const int32_t* __restrict__ src, const int32_t* __re
       key = ((uint64_t)(uint32_t)v << b) | (uint32_t)u;
     }
     __stcs(keys + i, key);
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((key >> (8 * p)) & 255)], 1u);
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p)
+      if (p < dp.passes) atomicAdd(&sh[p * kMaxRadix + digit_of(key, dp, p)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
+  for (int i = threadIdx.x; i < dp.passes * kMaxRadix; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
@@ -652,8 +715,17 @@ void plan_build(gpr_graph* g, cudaStream_t s, int* derr);
 
 // The copy stream and events of a chunked host-to-device COO copy, one set
 // per device, made on first use and kept for the process.  Builds that take
-// host input on one device are serialised by its mutex.
+// host input on one device are serialised by its mutex.  GPR_COPY_CHUNKS
+// (1..8) sets the number of chunks.
 constexpr int kCopyChunks = 8;
+static int copy_chunks() {
+  static const int c = [] {
+    const char* e = getenv("GPR_COPY_CHUNKS");
+    const int v = e ? atoi(e) : kCopyChunks;
+    return v < 1 ? 1 : (v > kCopyChunks ? kCopyChunks : v);
+  }();
+  return c;
+}
 struct CopyLane {
   cudaStream_t stream = nullptr;
   cudaEvent_t start = nullptr;
@@ -704,8 +776,9 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       std::lock_guard<std::mutex> lk(cp.mu);
       GPR_CUDA(cudaEventRecord(cp.start, s));  // the copy stream waits for the allocations and memsets
       GPR_CUDA(cudaStreamWaitEvent(cp.stream, cp.start, 0));
-      const int64_t chunk = (m_raw + kCopyChunks - 1) / kCopyChunks;
-      for (int c = 0; c < kCopyChunks; ++c) {
+      const int nch = copy_chunks();
+      const int64_t chunk = (m_raw + nch - 1) / nch;
+      for (int c = 0; c < nch; ++c) {
         const int64_t off = c * chunk, len = std::min<int64_t>(chunk, m_raw - off);
         if (len <= 0) break;
         GPR_CUDA(cudaMemcpyAsync(s_dev + off, src_in + off, (size_t)len * 4, cudaMemcpyHostToDevice, cp.stream));
@@ -755,13 +828,13 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     int64_t m = 0;
     int32_t* row_idx_full = nullptr;
     if (m_raw > 0) {
-      const int passes = (2 * b + 7) / 8;
+      const DigitPlan dp = digit_plan(2 * b);  // the plan radix_sort_u64 follows for these keys
       uint64_t* keys = (uint64_t*)tmp.get((size_t)m_raw * 8);
       uint64_t* alt = (uint64_t*)tmp.get((size_t)m_raw * 8);
-      uint32_t* hist = (uint32_t*)tmp.get(passes * 256 * 4);
-      GPR_CUDA(cudaMemsetAsync(hist, 0, passes * 256 * 4, s));
-      pack_kernel<<<grid_for(m_raw), kThreads, passes * 256 * 4, s>>>(src, dst, m_raw, n, b, g->plan.old2new,
-                                                                      passes, keys, hist);
+      uint32_t* hist = (uint32_t*)tmp.get(dp.passes * kMaxRadix * 4);
+      GPR_CUDA(cudaMemsetAsync(hist, 0, dp.passes * kMaxRadix * 4, s));
+      pack_kernel<<<grid_for(m_raw), kThreads, dp.passes * kMaxRadix * 4, s>>>(src, dst, m_raw, n, b,
+                                                                              g->plan.old2new, dp, keys, hist);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       row_idx_full = (int32_t*)tmp.get((size_t)m_raw * 4);
@@ -1031,6 +1104,29 @@ __global__ void tile_scan_kernel(const int32_t* __restrict__ v, int64_t m, const
   }
 }
 
+// Exclusive prefix sums of v[0, m) into out (the total must fit in int32 for
+// out's entries) and their total, read back to the host (synchronises s).
+int64_t exclusive_scan_i32(const int32_t* v, int64_t m, int32_t* out, cudaStream_t s) {
+  if (m <= 0) return 0;
+  const int64_t nt = (m + kScanTile - 1) / kScanTile;
+  int64_t* sums = (int64_t*)dalloc((size_t)(nt + 1) * sizeof(int64_t), s);
+  int64_t total = 0;
+  try {
+    tile_sums_kernel<<<(unsigned)nt, kThreads, 0, s>>>(v, m, sums);
+    scan_sums_kernel<<<1, 32, 0, s>>>(sums, nt, sums + nt);
+    tile_scan_kernel<<<(unsigned)nt, kThreads, 0, s>>>(v, m, sums, out);
+    GPR_CUDA(cudaGetLastError());
+    count_launches(3);
+    GPR_CUDA(cudaMemcpyAsync(&total, sums + nt, sizeof total, cudaMemcpyDeviceToHost, s));
+    GPR_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    dfree(sums, s);
+    throw;
+  }
+  dfree(sums, s);
+  return total;
+}
+
 // merged[kpos[i] + #(inserts <= key)] = key for every kept old key
 __global__ void place_kept_kernel(const uint64_t* __restrict__ keys, int64_t m, const int32_t* __restrict__ keep,
                                   const int32_t* __restrict__ kpos, const uint64_t* __restrict__ ins, int64_t ni,
@@ -1063,7 +1159,8 @@ static int64_t batch_keys(const gpr_graph* g, const int32_t* src, const int32_t*
   if (k <= 0) return 0;
   uint64_t* keys = (uint64_t*)tmp.get((size_t)k * 8);
   uint64_t* alt = (uint64_t*)tmp.get((size_t)k * 8);
-  pack_kernel<<<grid_for(k), kThreads, 0, s>>>(src, dst, k, g->n, g->id_bits, g->plan.old2new, 0, keys, nullptr);
+  pack_kernel<<<grid_for(k), kThreads, 0, s>>>(src, dst, k, g->n, g->id_bits, g->plan.old2new, DigitPlan{}, keys,
+                                                nullptr);
   GPR_CUDA(cudaGetLastError());
   count_launches(1);
   uint64_t* sorted = radix_sort_u64(keys, alt, k, 64, s, derr, nullptr);  // sentinels need every bit

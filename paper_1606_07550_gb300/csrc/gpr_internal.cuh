@@ -53,6 +53,9 @@ int device_ordinal();
 // With GPR_TRACE=1: synchronise s and print the wall time since the previous
 // mark on this thread, labelled `what` (null: just set the mark).
 void trace_phase(const char* what, cudaStream_t s);
+// Exclusive prefix sums of v[0, m) into out; returns their total (read back to
+// the host: synchronises s).
+int64_t exclusive_scan_i32(const int32_t* v, int64_t m, int32_t* out, cudaStream_t s);
 
 // Host-side count of kernels this library has launched (a CUDA graph launch
 // counts its kernel nodes).
@@ -64,10 +67,22 @@ int64_t launches_so_far();
 int32_t hot_capacity();
 
 // ---- radix sort of 64-bit keys (onesweep-style, build.cu) -----------------
-// Sorts keys[0..n) ascending on the low `bits` bits (stable LSD, 8-bit
-// digits), using `alt` (n entries) as the second buffer.  Returns the buffer
-// holding the result (keys or alt).  hist_ready: the caller already filled
-// `hist` (passes x 256 digit counts, device); otherwise it is computed.
+// The digits of a sort of `bits`-bit keys: 8 bits wide, or, where that saves
+// a pass, the last ones 9 bits wide (then exactly `bits` bits are sorted).
+constexpr int kMaxRadix = 512;
+constexpr int kMaxPasses = 8;
+struct DigitPlan {
+  int passes;
+  int shift[kMaxPasses];
+  int width[kMaxPasses];
+};
+DigitPlan digit_plan(int bits);
+
+// Sorts keys[0..n) ascending on the low `bits` bits (stable LSD, the digits of
+// digit_plan(bits)), using `alt` (n entries) as the second buffer.  Returns
+// the buffer holding the result (keys or alt).  hist: the caller already
+// filled it (passes x kMaxRadix digit counts, device, digit_plan(bits)'s
+// digits); if null it is computed.
 uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, cudaStream_t s,
                          int* derr, uint32_t* hist = nullptr);
 

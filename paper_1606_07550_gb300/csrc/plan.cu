@@ -140,16 +140,55 @@ __global__ void split_kernel(const int32_t* __restrict__ col_ptr, const int32_t*
   }
 }
 
-// (row, first edge, first cold edge, end edge) of each row of one list range.
-__global__ void row_spans_kernel(const int32_t* __restrict__ rows, int32_t i0, int32_t i1,
-                                 const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ split,
-                                 int32_t* __restrict__ spans) {
+// Hot and cold chunk counts of the long rows rows[i0, i1): ceil(hot prefix /
+// C) and ceil(cold suffix / C).
+__global__ void chunk_counts_kernel(const int32_t* __restrict__ rows, int32_t i0, int32_t i1,
+                                    const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ split, int32_t C,
+                                    int32_t* __restrict__ hc, int32_t* __restrict__ cc) {
   for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = rows[i];
-    spans[4 * (i - i0)] = r;
-    spans[4 * (i - i0) + 1] = col_ptr[r];
-    spans[4 * (i - i0) + 2] = split[r];
-    spans[4 * (i - i0) + 3] = col_ptr[r + 1];
+    const int64_t e0 = col_ptr[r], sp = split[r], e1 = col_ptr[r + 1];
+    hc[i - i0] = (int32_t)((sp - e0 + C - 1) / C);
+    cc[i - i0] = (int32_t)((e1 - sp + C - 1) / C);
+  }
+}
+
+// The chunk entries and split records of the long rows rows[i0, i1), one warp
+// per row: its hot chunks at hot_base + hoff, its cold chunks at cold_base +
+// coff, its record at split_base + (i - i0).
+struct ChunkLists {
+  int32_t *chunk_row, *chunk_begin, *chunk_end;
+  int32_t *split_row, *split_hbeg, *split_hend, *split_cbeg, *split_cend;
+};
+__global__ void chunk_lists_kernel(const int32_t* __restrict__ rows, int32_t i0, int32_t i1,
+                                   const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ split, int32_t C,
+                                   const int32_t* __restrict__ hoff, const int32_t* __restrict__ coff,
+                                   int32_t split_base, int32_t hot_base, int32_t cold_base, ChunkLists L) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wi < i1 - i0; wi += nwarps) {
+    const int32_t r = rows[i0 + wi];
+    const int64_t e0 = col_ptr[r], sp = split[r], e1 = col_ptr[r + 1];
+    const int32_t nh = (int32_t)((sp - e0 + C - 1) / C), nc = (int32_t)((e1 - sp + C - 1) / C);
+    const int32_t h0 = hot_base + hoff[wi], c0 = cold_base + coff[wi];
+    if (lane == 0) {
+      const int32_t k = split_base + (int32_t)wi;
+      L.split_row[k] = r;
+      L.split_hbeg[k] = h0;
+      L.split_hend[k] = h0 + nh;
+      L.split_cbeg[k] = c0;
+      L.split_cend[k] = c0 + nc;
+    }
+    for (int32_t j = lane; j < nh; j += 32) {
+      L.chunk_row[h0 + j] = r;
+      L.chunk_begin[h0 + j] = (int32_t)(e0 + (int64_t)j * C);
+      L.chunk_end[h0 + j] = (int32_t)min(sp, e0 + (int64_t)(j + 1) * C);
+    }
+    for (int32_t j = lane; j < nc; j += 32) {
+      L.chunk_row[c0 + j] = r;
+      L.chunk_begin[c0 + j] = (int32_t)(sp + (int64_t)j * C);
+      L.chunk_end[c0 + j] = (int32_t)min(e1, sp + (int64_t)(j + 1) * C);
+    }
   }
 }
 
@@ -234,60 +273,62 @@ void plan_build(gpr_graph* g, cudaStream_t s, int* derr) {
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
 
-    // chunk lists of the long-row bucket(s): hot prefixes first, then cold suffixes
-    std::vector<int32_t> hrow, hbeg, hend, crow, cbeg, cend, srow, shb, she, scb, sce;
+    // chunk lists of the long-row bucket(s): hot prefixes first, then cold
+    // suffixes; counts per row, their prefix sums, then the entries
+    struct LongRange {
+      int32_t i0, i1;
+      int32_t *hoff, *coff;
+      int64_t hot, cold;
+    };
+    std::vector<LongRange> lr;
+    int64_t n_hot = 0, n_cold = 0, n_long = 0;
     for (int k = 0; k < nb; ++k) {
       if (P.bucket[k].lanes != 0) continue;
-      const int32_t i0 = P.bucket[k].row_begin, i1 = P.bucket[k].row_end;
-      if (i1 <= i0) continue;
-      int32_t* spans = (int32_t*)T((size_t)(i1 - i0) * 16);
-      row_spans_kernel<<<grid_for(i1 - i0), kPThreads, 0, s>>>(P.rows, i0, i1, g->col_ptr, P.split, spans);
+      LongRange R{P.bucket[k].row_begin, P.bucket[k].row_end, nullptr, nullptr, 0, 0};
+      const int32_t len = R.i1 - R.i0;
+      if (len <= 0) continue;
+      int32_t* hc = (int32_t*)T((size_t)len * 4);
+      int32_t* cc = (int32_t*)T((size_t)len * 4);
+      R.hoff = (int32_t*)T((size_t)len * 4);
+      R.coff = (int32_t*)T((size_t)len * 4);
+      chunk_counts_kernel<<<grid_for(len), kPThreads, 0, s>>>(P.rows, R.i0, R.i1, g->col_ptr, P.split, P.chunk_edges,
+                                                             hc, cc);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
-      std::vector<int32_t> hs((size_t)(i1 - i0) * 4);
-      GPR_CUDA(cudaMemcpyAsync(hs.data(), spans, hs.size() * 4, cudaMemcpyDeviceToHost, s));
-      GPR_CUDA(cudaStreamSynchronize(s));
-      for (int32_t i = 0; i < i1 - i0; ++i) {
-        const int32_t r = hs[4 * i], e0 = hs[4 * i + 1], sp = hs[4 * i + 2], e1 = hs[4 * i + 3];
-        srow.push_back(r);
-        shb.push_back((int32_t)hrow.size());
-        for (int64_t e = e0; e < sp; e += P.chunk_edges) {
-          hrow.push_back(r);
-          hbeg.push_back((int32_t)e);
-          hend.push_back((int32_t)std::min<int64_t>(sp, e + P.chunk_edges));
-        }
-        she.push_back((int32_t)hrow.size());
-        scb.push_back((int32_t)crow.size());
-        for (int64_t e = sp; e < e1; e += P.chunk_edges) {
-          crow.push_back(r);
-          cbeg.push_back((int32_t)e);
-          cend.push_back((int32_t)std::min<int64_t>(e1, e + P.chunk_edges));
-        }
-        sce.push_back((int32_t)crow.size());
-      }
+      R.hot = exclusive_scan_i32(hc, len, R.hoff, s);
+      R.cold = exclusive_scan_i32(cc, len, R.coff, s);
+      n_hot += R.hot;
+      n_cold += R.cold;
+      n_long += len;
+      lr.push_back(R);
     }
-    P.n_hot_chunks = (int32_t)hrow.size();
-    P.nchunks = (int32_t)(hrow.size() + crow.size());
-    for (auto& v : scb) v += P.n_hot_chunks;
-    for (auto& v : sce) v += P.n_hot_chunks;
-    hrow.insert(hrow.end(), crow.begin(), crow.end());
-    hbeg.insert(hbeg.end(), cbeg.begin(), cbeg.end());
-    hend.insert(hend.end(), cend.begin(), cend.end());
-    P.nsplit = (int32_t)srow.size();
-    auto up = [&](const std::vector<int32_t>& v) {
-      int32_t* d = (int32_t*)dalloc(std::max<size_t>(v.size(), 1) * 4, s);
-      if (!v.empty()) GPR_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * 4, cudaMemcpyHostToDevice, s));
-      return d;
-    };
-    P.chunk_row = up(hrow);
-    P.chunk_begin = up(hbeg);
-    P.chunk_end = up(hend);
-    P.split_row = up(srow);
-    P.split_hbeg = up(shb);
-    P.split_hend = up(she);
-    P.split_cbeg = up(scb);
-    P.split_cend = up(sce);
-    GPR_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
+    if (n_hot + n_cold > INT32_MAX) throw StatusFail{GPR_EINVAL, "too many long-row chunks"};
+    P.n_hot_chunks = (int32_t)n_hot;
+    P.nchunks = (int32_t)(n_hot + n_cold);
+    P.nsplit = (int32_t)n_long;
+    auto arr = [&](int64_t k) { return (int32_t*)dalloc((size_t)std::max<int64_t>(k, 1) * 4, s); };
+    P.chunk_row = arr(P.nchunks);
+    P.chunk_begin = arr(P.nchunks);
+    P.chunk_end = arr(P.nchunks);
+    P.split_row = arr(P.nsplit);
+    P.split_hbeg = arr(P.nsplit);
+    P.split_hend = arr(P.nsplit);
+    P.split_cbeg = arr(P.nsplit);
+    P.split_cend = arr(P.nsplit);
+    const ChunkLists L{P.chunk_row,  P.chunk_begin, P.chunk_end,  P.split_row,
+                       P.split_hbeg, P.split_hend,  P.split_cbeg, P.split_cend};
+    int64_t sb = 0, hb = 0, cb = n_hot;
+    for (const LongRange& R : lr) {
+      const int32_t len = R.i1 - R.i0;
+      chunk_lists_kernel<<<grid_for((int64_t)len * 32), kPThreads, 0, s>>>(
+          P.rows, R.i0, R.i1, g->col_ptr, P.split, P.chunk_edges, R.hoff, R.coff, (int32_t)sb, (int32_t)hb,
+          (int32_t)cb, L);
+      GPR_CUDA(cudaGetLastError());
+      count_launches(1);
+      sb += len;
+      hb += R.hot;
+      cb += R.cold;
+    }
     trace_phase("plan: split + long-row chunks", s);
     for (void* p : tmp) dfree(p, s);
   } catch (...) {
