@@ -131,8 +131,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
   const int32_t S = k->S, B = k->B, D = k->D;
   const int64_t nseg = (int64_t)S * B;
   const KeyGeom kg = key_geom(S, B, k->n_dense, sb_bits);
-  uint64_t* keys = nullptr;
-  uint64_t* alt = nullptr;
+  std::unique_ptr<SortScratch> sc;  // the sort's two key buffers, until the segment table is read
   int32_t* seg = nullptr;
   int* derr = nullptr;
   try {
@@ -150,8 +149,10 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
     GPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * 2, s));
     const int grid = num_sms() * 8;
     if (m > 0) {
-      keys = (uint64_t*)dalloc((size_t)m * 8, s);
-      alt = (uint64_t*)dalloc((size_t)m * 8, s);
+      sc.reset(new SortScratch((size_t)m, s));
+      uint64_t* keys = sc->a;
+      uint64_t* alt = sc->b;
+      trace_phase("layout: allocations", s);
       bk_keys_kernel<<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, n, sb_bits, w_bits, kg.kbits, k->n_dense, D,
                                           kg.kb_bits, keys);
       GPR_CUDA(cudaGetLastError());
@@ -163,9 +164,6 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
                                              S, nseg, k->src_lo, k->dst_lo, k->vals, seg);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
-      dfree(keys, s);
-      dfree(alt, s);
-      keys = alt = nullptr;
     } else {
       GPR_CUDA(cudaMemsetAsync(seg, 0, (size_t)(nseg + 1) * 4, s));
     }
@@ -173,9 +171,9 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
     bk_transpose_kernel<<<grid, 256, 0, s>>>(seg, S, B, k->xseg);
     GPR_CUDA(cudaGetLastError());
     count_launches(1);
-    // the segment table on the host, source-block major (contiguous per block)
-    // the segment table on the host, in pinned staging memory kept for the
-    // process (one layout build at a time uses it)
+    // the segment table on the host, source-block major (contiguous per
+    // block), in pinned staging memory kept for the process (one layout
+    // build at a time uses it)
     static std::mutex stage_mu;
     static int2* stage = nullptr;
     static size_t stage_cap = 0;
@@ -193,6 +191,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
     GPR_CUDA(cudaMemcpyAsync(X, k->xseg, (size_t)nseg * sizeof(int2), cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GPR_CUDA(cudaStreamSynchronize(s));
+    sc.reset();
     dfree(seg, s);
     dfree(derr, s);
     seg = nullptr;
@@ -288,8 +287,7 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
                (int64_t)au.size() * sizeof(AccumUnit) + (int64_t)n_split * (int64_t)W * 8 + (int64_t)B * 24;
     return k;
   } catch (...) {
-    dfree(keys, s);
-    dfree(alt, s);
+    sc.reset();
     dfree(seg, s);
     dfree(derr, s);
     blocked_free(k, s);

@@ -123,6 +123,58 @@ void dfree(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
+// ------------------------------------------------------------ sort scratch --
+struct Slot {
+  std::mutex mu;
+  uint64_t* a = nullptr;
+  uint64_t* b = nullptr;
+  size_t cap = 0;  // keys per buffer
+};
+static Slot g_scratch[64];
+
+SortScratch::SortScratch(size_t keys, cudaStream_t s) : s_(s) {
+  int d = device_ordinal();
+  if (d < 0 || d >= 64) d = 0;
+  Slot& sl = g_scratch[d];
+  if (!sl.mu.try_lock()) {  // lent: a pair of this call's own
+    a = (uint64_t*)dalloc(keys * 8, s);
+    try {
+      b = (uint64_t*)dalloc(keys * 8, s);
+    } catch (...) {
+      dfree(a, s);
+      throw;
+    }
+    return;
+  }
+  try {
+    if (sl.cap < keys) {  // the last borrower synchronised its stream: the old pair is idle
+      dfree(sl.a, s);
+      dfree(sl.b, s);
+      sl.a = sl.b = nullptr;
+      sl.cap = 0;
+      sl.a = (uint64_t*)dalloc(keys * 8, s);
+      sl.b = (uint64_t*)dalloc(keys * 8, s);
+      sl.cap = keys;
+    }
+  } catch (...) {
+    sl.mu.unlock();
+    throw;
+  }
+  slot_ = &sl;
+  a = sl.a;
+  b = sl.b;
+}
+
+SortScratch::~SortScratch() {
+  if (slot_) {
+    cudaStreamSynchronize(s_);
+    slot_->mu.unlock();
+  } else {
+    dfree(a, s_);
+    dfree(b, s_);
+  }
+}
+
 // ------------------------------------------------------------ histograms --
 // Digits of an LSD sort of `bits`-bit keys: 8-bit digits, or, where that takes
 // a pass fewer, the last (bits - 8 * passes) digits 9 bits wide; with 9-bit
@@ -829,15 +881,20 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
     int32_t* row_idx_full = nullptr;
     if (m_raw > 0) {
       const DigitPlan dp = digit_plan(2 * b);  // the plan radix_sort_u64 follows for these keys
-      uint64_t* keys = (uint64_t*)tmp.get((size_t)m_raw * 8);
-      uint64_t* alt = (uint64_t*)tmp.get((size_t)m_raw * 8);
+      SortScratch sc((size_t)m_raw, s);
+      uint64_t* keys = sc.a;
+      uint64_t* alt = sc.b;
       uint32_t* hist = (uint32_t*)tmp.get(dp.passes * kMaxRadix * 4);
       GPR_CUDA(cudaMemsetAsync(hist, 0, dp.passes * kMaxRadix * 4, s));
       pack_kernel<<<grid_for(m_raw), kThreads, dp.passes * kMaxRadix * 4, s>>>(src, dst, m_raw, n, b,
                                                                               g->plan.old2new, dp, keys, hist);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
-      row_idx_full = (int32_t*)tmp.get((size_t)m_raw * 4);
+      // the row ids go straight into the graph (capacity m_raw: the kept edges
+      // are not known yet); a build that drops many duplicates copies them
+      // into an array of their own size below
+      g->row_idx = (int32_t*)dalloc((size_t)m_raw * 4, s);
+      row_idx_full = g->row_idx;
       permute_kernel<<<grid_for(n), kThreads, 0, s>>>(odeg, g->plan.old2new, n, g->outdeg);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
@@ -852,9 +909,12 @@ gpr_status build_graph(const int32_t* src_in, const int32_t* dst_in, int64_t m_r
       GPR_CUDA(cudaMemsetAsync(g->outdeg, 0, (size_t)n * 4, s));
     }
     g->m = m;
-    g->row_idx = (int32_t*)dalloc((size_t)std::max<int64_t>(m, 1) * 4, s);
-    if (m > 0)
-      GPR_CUDA(cudaMemcpyAsync(g->row_idx, row_idx_full, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+    if (!row_idx_full || m < m_raw - m_raw / 8) {
+      int32_t* exact = (int32_t*)dalloc((size_t)std::max<int64_t>(m, 1) * 4, s);
+      if (m > 0) GPR_CUDA(cudaMemcpyAsync(exact, row_idx_full, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+      dfree(row_idx_full, s);
+      g->row_idx = exact;
+    }
     tmp.release();
     trace_phase("build: dedupe", s);
     // 3. execution layout (degree buckets, chunks, inverse degrees)

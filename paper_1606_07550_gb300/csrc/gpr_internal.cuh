@@ -66,6 +66,27 @@ int64_t launches_so_far();
 // memory (FP32), a multiple of 8.
 int32_t hot_capacity();
 
+// ---- sort scratch (build.cu) -----------------------------------------------
+// Two buffers of `keys` 64-bit keys for a large sort.  One pair per device is
+// kept for the process and lent to one call at a time (stream-ordered
+// allocations of tens of GB cost milliseconds per call even when the pool
+// holds the memory); a call that finds it lent allocates its own pair.  The
+// destructor synchronises the stream before the pair is lent again, so the
+// caller's work on it is complete.  Throws like dalloc.
+class SortScratch {
+ public:
+  SortScratch(size_t keys, cudaStream_t s);
+  ~SortScratch();
+  SortScratch(const SortScratch&) = delete;
+  SortScratch& operator=(const SortScratch&) = delete;
+  uint64_t* a = nullptr;
+  uint64_t* b = nullptr;
+
+ private:
+  cudaStream_t s_;
+  struct Slot* slot_ = nullptr;
+};
+
 // ---- radix sort of 64-bit keys (onesweep-style, build.cu) -----------------
 // The digits of a sort of `bits`-bit keys: 8 bits wide, or, where that saves
 // a pass, the last ones 9 bits wide (then exactly `bits` bits are sorted).
