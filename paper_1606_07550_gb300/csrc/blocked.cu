@@ -6,11 +6,135 @@
 #include <algorithm>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "blocked_kernels.cuh"
 
 namespace gpr {
+
+// ---- layout construction --------------------------------------------------
+
+// The sort index of an edge: bin b, then its dense source u (u < n_dense),
+// or n_dense + (its source block - D); kb_bits bits per bin.
+__device__ __forceinline__ uint64_t bk_index(uint64_t b, uint32_t u, int sb_bits, int32_t n_dense, int32_t D,
+                                             int kb_bits) {
+  const uint64_t j = u < (uint32_t)n_dense ? (uint64_t)u : (uint64_t)n_dense + ((u >> sb_bits) - (uint32_t)D);
+  return (b << kb_bits) | j;
+}
+// The segment (b, s) of a sort index.
+__device__ __forceinline__ int64_t bk_segment(uint64_t kidx, int sb_bits, int32_t n_dense, int32_t D, int kb_bits,
+                                              int32_t S) {
+  const int64_t b = (int64_t)(kidx >> kb_bits);
+  const uint64_t j = kidx & ((1ull << kb_bits) - 1);
+  const int64_t s = j < (uint64_t)n_dense ? (int64_t)(j >> sb_bits) : (int64_t)D + (int64_t)(j - (uint64_t)n_dense);
+  return b * S + s;
+}
+
+// key = row-in-bin | source-in-block | sort index, one per CSC edge, in CSC
+// order (256 threads per block).
+__global__ void __launch_bounds__(256) bk_keys_kernel(const int32_t* __restrict__ col_ptr,
+                                                      const int32_t* __restrict__ row_idx, int32_t n, int sb_bits,
+                                                      int w_bits, int kbits, int32_t n_dense, int32_t D, int kb_bits,
+                                                      uint64_t* __restrict__ keys) {
+  __shared__ int32_t s_rows[8][kMarkStride];
+  const uint32_t sb_mask = (1u << sb_bits) - 1;
+  for_each_edge_with_row_marked(col_ptr, n, s_rows[threadIdx.x >> 5], [&](int64_t e, int32_t p) {
+    const uint64_t b = (uint64_t)(p >> w_bits);
+    const uint64_t hi = (uint64_t)(p & ((1 << w_bits) - 1)) << (sb_bits + kbits);
+    const uint32_t u = (uint32_t)row_idx[e];
+    keys[e] = hi | ((uint64_t)(u & sb_mask) << kbits) | bk_index(b, u, sb_bits, n_dense, D, kb_bits);
+  });
+}
+
+// From the keys sorted (stably) on their low kbits bits, in bin-major edge
+// order: the packed word of every dense-source edge, the local ids of every
+// other edge, and seg[k] = first edge of segment k (seg[nseg] = m).  A thread
+// takes four consecutive edges; a bin's dense edges precede its others, so
+// four are nearly always of one kind and go out as one vector store.
+__global__ void bk_extract_kernel(const uint64_t* __restrict__ keys, int64_t m, int sb_bits, int kbits,
+                                  int32_t n_dense, int32_t D, int kb_bits, int dense_bits, int32_t S, int64_t nseg,
+                                  uint16_t* __restrict__ src_lo, uint16_t* __restrict__ dst_lo,
+                                  uint32_t* __restrict__ vals, int32_t* __restrict__ seg) {
+  const uint64_t kmask = (1ull << kbits) - 1;
+  const uint64_t jmask = (1ull << kb_bits) - 1;
+  const uint32_t smask = (1u << sb_bits) - 1;
+  const int64_t nq = (m + 3) / 4;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 4 * q;
+    const bool full = i0 + 4 <= m;
+    uint64_t key[4];
+    if (full) {
+      const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(keys + i0);
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(keys + i0 + 2);
+      key[0] = a.x;
+      key[1] = a.y;
+      key[2] = b.x;
+      key[3] = b.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) key[j] = i0 + j < m ? keys[i0 + j] : 0ull;
+    }
+    int64_t prev = i0 > 0 ? bk_segment(keys[i0 - 1] & kmask, sb_bits, n_dense, D, kb_bits, S) : -1;
+    uint32_t v[4];
+    uint16_t sl[4], dl[4];
+    int ndense = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t kidx = key[j] & kmask;
+      const uint64_t jj = kidx & jmask;
+      const uint32_t r = (uint32_t)(key[j] >> (kbits + sb_bits));
+      const bool dn = jj < (uint64_t)n_dense;
+      ndense += dn;
+      v[j] = (uint32_t)jj | (r << dense_bits);
+      sl[j] = (uint16_t)((key[j] >> kbits) & smask);
+      dl[j] = (uint16_t)r;
+      if (i0 + j < m) {
+        const int64_t k = bk_segment(kidx, sb_bits, n_dense, D, kb_bits, S);
+        for (int64_t kk = prev + 1; kk <= k; ++kk) seg[kk] = (int32_t)(i0 + j);
+        prev = k;
+        if (i0 + j == m - 1)
+          for (int64_t kk = k + 1; kk <= nseg; ++kk) seg[kk] = (int32_t)m;
+        if (!full) {
+          if (dn) {
+            vals[i0 + j] = v[j];
+          } else {
+            src_lo[i0 + j] = sl[j];
+            dst_lo[i0 + j] = dl[j];
+          }
+        }
+      }
+    }
+    if (!full) continue;
+    if (ndense == 4) {
+      *reinterpret_cast<uint4*>(vals + i0) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else if (ndense == 0) {
+      *reinterpret_cast<uint2*>(src_lo + i0) =
+          make_uint2((uint32_t)sl[0] | ((uint32_t)sl[1] << 16), (uint32_t)sl[2] | ((uint32_t)sl[3] << 16));
+      *reinterpret_cast<uint2*>(dst_lo + i0) =
+          make_uint2((uint32_t)dl[0] | ((uint32_t)dl[1] << 16), (uint32_t)dl[2] | ((uint32_t)dl[3] << 16));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (((key[j] & kmask) & jmask) < (uint64_t)n_dense) {
+          vals[i0 + j] = v[j];
+        } else {
+          src_lo[i0 + j] = sl[j];
+          dst_lo[i0 + j] = dl[j];
+        }
+      }
+    }
+  }
+}
+
+// xseg[s * B + b] = edges of segment (b, s).
+__global__ void bk_transpose_kernel(const int32_t* __restrict__ seg, int32_t S, int32_t B, int2* __restrict__ xseg) {
+  const int64_t nseg = (int64_t)S * B;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nseg; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = k / S, s = k - b * S;
+    xseg[s * B + b] = make_int2(seg[k], seg[k + 1]);
+  }
+}
 
 // ---- host side --------------------------------------------------------------
 
@@ -153,8 +277,13 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
       uint64_t* keys = sc->a;
       uint64_t* alt = sc->b;
       trace_phase("layout: allocations", s);
-      bk_keys_kernel<<<grid, 256, 0, s>>>(g->col_ptr, g->row_idx, n, sb_bits, w_bits, kg.kbits, k->n_dense, D,
-                                          kg.kb_bits, keys);
+      static const int keys_per_sm = [] {  // resident blocks: the chunks are dealt out statically
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bk_keys_kernel, 256, 0);
+        return std::max(b, 1);
+      }();
+      bk_keys_kernel<<<num_sms() * keys_per_sm, 256, 0, s>>>(g->col_ptr, g->row_idx, n, sb_bits, w_bits, kg.kbits,
+                                                             k->n_dense, D, kg.kb_bits, keys);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       trace_phase("layout: keys", s);
@@ -201,38 +330,55 @@ Blocked* blocked_build(const gpr_graph* g, int sb_bits, int w_bits, int32_t n_de
 
     // expand units (source blocks past the dense ones): per source block,
     // runs of consecutive bins' segments of at most unit edges and
-    // kMaxUnitSegs segments; a longer segment is cut into pieces of its own
-    std::vector<ExpandUnit> xu;
-    for (int32_t sb = D; sb < S; ++sb) {
-      int32_t first = -1, last = -1, clo = 0, chi = 0;
-      int64_t edges = 0;
-      auto flush = [&]() {
-        if (first >= 0 && edges > 0) xu.push_back(ExpandUnit{sb, first, last + 1, clo, chi});
-        first = -1;
-        edges = 0;
-      };
-      const int2* Xs = X + (size_t)sb * B;
-      for (int32_t b = 0; b < B; ++b) {
-        const int32_t lo = Xs[b].x, hi = Xs[b].y;
-        const int64_t len = hi - lo;
-        if (len == 0) continue;
-        if (len > xunit) {
-          flush();
-          for (int64_t o = 0; o < len; o += xunit)
-            xu.push_back(ExpandUnit{sb, b, b + 1, (int32_t)(lo + o), (int32_t)std::min<int64_t>(hi, lo + o + xunit)});
-          continue;
+    // kMaxUnitSegs segments; a longer segment is cut into pieces of its own.
+    // Source blocks are independent: a few host threads take a range each
+    // and the lists are joined in block order.
+    auto expand_units = [&](int32_t sb0, int32_t sb1, std::vector<ExpandUnit>& xu) {
+      for (int32_t sb = sb0; sb < sb1; ++sb) {
+        int32_t first = -1, last = -1, clo = 0, chi = 0;
+        int64_t edges = 0;
+        auto flush = [&]() {
+          if (first >= 0 && edges > 0) xu.push_back(ExpandUnit{sb, first, last + 1, clo, chi});
+          first = -1;
+          edges = 0;
+        };
+        const int2* Xs = X + (size_t)sb * B;
+        for (int32_t b = 0; b < B; ++b) {
+          const int32_t lo = Xs[b].x, hi = Xs[b].y;
+          const int64_t len = hi - lo;
+          if (len == 0) continue;
+          if (len > xunit) {
+            flush();
+            for (int64_t o = 0; o < len; o += xunit)
+              xu.push_back(
+                  ExpandUnit{sb, b, b + 1, (int32_t)(lo + o), (int32_t)std::min<int64_t>(hi, lo + o + xunit)});
+            continue;
+          }
+          if (first >= 0 && (edges + len > xunit || b - first >= kMaxUnitSegs)) flush();
+          if (first < 0) {
+            first = b;
+            clo = lo;
+          }
+          last = b;
+          chi = hi;
+          edges += len;
         }
-        if (first >= 0 && (edges + len > xunit || b - first >= kMaxUnitSegs)) flush();
-        if (first < 0) {
-          first = b;
-          clo = lo;
-        }
-        last = b;
-        chi = hi;
-        edges += len;
+        flush();
       }
-      flush();
+    };
+    const int32_t nblk = S - D;
+    const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(8, (int64_t)nblk * B / (1 << 18)));
+    std::vector<std::vector<ExpandUnit>> xparts(nth);
+    {
+      std::vector<std::thread> pool;
+      for (int t = 1; t < nth; ++t)
+        pool.emplace_back(expand_units, D + (int32_t)((int64_t)nblk * t / nth),
+                          D + (int32_t)((int64_t)nblk * (t + 1) / nth), std::ref(xparts[t]));
+      expand_units(D, D + (int32_t)((int64_t)nblk / nth), xparts[0]);
+      for (std::thread& th : pool) th.join();
     }
+    std::vector<ExpandUnit> xu;
+    for (const auto& v : xparts) xu.insert(xu.end(), v.begin(), v.end());
     // accumulate units: each bin whole, or cut into near-equal edge ranges;
     // each knows where the bin's dense-source edges end
     std::vector<AccumUnit> au;

@@ -47,9 +47,9 @@
 // once), and a bin with many edges is cut into units whose sums meet in a
 // global accumulator.
 //
-// This header holds the device side: the layout construction kernels, the
-// expand and accumulate kernels and the code conversions; blocked.cu builds
-// the layout and records the steps.
+// This header holds the device side of a step: the expand and accumulate
+// kernels and the code conversions; blocked.cu builds the layout (with its
+// construction kernels) and records the steps.
 #pragma once
 
 #include "blocked.cuh"
@@ -128,75 +128,6 @@ __device__ __forceinline__ void red_add_nonzero(uint32_t addr, uint32_t v) {
   asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr),
                "r"(v)
                : "memory");
-}
-
-// ---- layout construction --------------------------------------------------
-
-// The sort index of an edge: bin b, then its dense source u (u < n_dense),
-// or n_dense + (its source block - D); kb_bits bits per bin.
-__device__ __forceinline__ uint64_t bk_index(uint64_t b, uint32_t u, int sb_bits, int32_t n_dense, int32_t D,
-                                             int kb_bits) {
-  const uint64_t j = u < (uint32_t)n_dense ? (uint64_t)u : (uint64_t)n_dense + ((u >> sb_bits) - (uint32_t)D);
-  return (b << kb_bits) | j;
-}
-// The segment (b, s) of a sort index.
-__device__ __forceinline__ int64_t bk_segment(uint64_t kidx, int sb_bits, int32_t n_dense, int32_t D, int kb_bits,
-                                              int32_t S) {
-  const int64_t b = (int64_t)(kidx >> kb_bits);
-  const uint64_t j = kidx & ((1ull << kb_bits) - 1);
-  const int64_t s = j < (uint64_t)n_dense ? (int64_t)(j >> sb_bits) : (int64_t)D + (int64_t)(j - (uint64_t)n_dense);
-  return b * S + s;
-}
-
-// key = row-in-bin | source-in-block | sort index, one per CSC edge, in CSC
-// order.
-__global__ void bk_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
-                               int sb_bits, int w_bits, int kbits, int32_t n_dense, int32_t D, int kb_bits,
-                               uint64_t* __restrict__ keys) {
-  const uint32_t sb_mask = (1u << sb_bits) - 1;
-  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
-    const uint64_t b = (uint64_t)(p >> w_bits);
-    const uint64_t hi = (uint64_t)(p & ((1 << w_bits) - 1)) << (sb_bits + kbits);
-    const uint32_t u = (uint32_t)row_idx[e];
-    keys[e] = hi | ((uint64_t)(u & sb_mask) << kbits) | bk_index(b, u, sb_bits, n_dense, D, kb_bits);
-  });
-}
-
-// From the keys sorted (stably) on their low kbits bits, in bin-major edge
-// order: the packed word of every dense-source edge, the local ids of every
-// other edge, and seg[k] = first edge of segment k (seg[nseg] = m).
-__global__ void bk_extract_kernel(const uint64_t* __restrict__ keys, int64_t m, int sb_bits, int kbits,
-                                  int32_t n_dense, int32_t D, int kb_bits, int dense_bits, int32_t S, int64_t nseg,
-                                  uint16_t* __restrict__ src_lo, uint16_t* __restrict__ dst_lo,
-                                  uint32_t* __restrict__ vals, int32_t* __restrict__ seg) {
-  const uint64_t kmask = (1ull << kbits) - 1;
-  const uint64_t jmask = (1ull << kb_bits) - 1;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t key = keys[i];
-    const uint64_t kidx = key & kmask;
-    const uint64_t j = kidx & jmask;
-    const uint32_t r = (uint32_t)(key >> (kbits + sb_bits));
-    if (j < (uint64_t)n_dense) {
-      vals[i] = (uint32_t)j | (r << dense_bits);
-    } else {
-      src_lo[i] = (uint16_t)((key >> kbits) & ((1u << sb_bits) - 1));
-      dst_lo[i] = (uint16_t)r;
-    }
-    const int64_t k = bk_segment(kidx, sb_bits, n_dense, D, kb_bits, S);
-    const int64_t first = i > 0 ? bk_segment(keys[i - 1] & kmask, sb_bits, n_dense, D, kb_bits, S) + 1 : 0;
-    for (int64_t kk = first; kk <= k; ++kk) seg[kk] = (int32_t)i;
-    if (i == m - 1)
-      for (int64_t kk = k + 1; kk <= nseg; ++kk) seg[kk] = (int32_t)m;
-  }
-}
-
-// xseg[s * B + b] = edges of segment (b, s).
-__global__ void bk_transpose_kernel(const int32_t* __restrict__ seg, int32_t S, int32_t B, int2* __restrict__ xseg) {
-  const int64_t nseg = (int64_t)S * B;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nseg; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = k / S, s = k - b * S;
-    xseg[s * B + b] = make_int2(seg[k], seg[k + 1]);
-  }
 }
 
 // ---- asynchronous copies to shared memory (cp.async) ------------------------

@@ -243,6 +243,73 @@ __device__ __forceinline__ void for_each_edge_with_row(const int32_t* __restrict
     }
   }
 }
+// f(e, p) for every edge e of the CSC with its row p, through row marks in
+// shared memory: a warp takes kMarkChunk consecutive edges (the warps of the
+// grid take consecutive chunks, so the streams stay close together), marks
+// the first edge of each row that starts among them (the largest row where
+// empty rows share a start), and a running maximum gives each edge its row;
+// edges are then visited lane-strided (coalesced).  s_rows: kMarkStride ints
+// per warp.
+constexpr int kMarkChunk = 1024;
+constexpr int kMarkStride = kMarkChunk + kMarkChunk / 32;  // lane l's 32 positions start in bank l
+__device__ __forceinline__ int mark_slot(int i) { return i + (i >> 5); }
+template <typename F>
+__device__ __forceinline__ void for_each_edge_with_row_marked(const int32_t* __restrict__ col_ptr, int32_t n,
+                                                              int32_t* s_row, F f) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t m = col_ptr[n];
+  for (int64_t cb = warp * kMarkChunk; cb < m; cb += nwarps * kMarkChunk) {
+    const int len = (int)(m - cb < kMarkChunk ? m - cb : kMarkChunk);
+    int32_t p0 = 0, hi = n;  // the row of edge cb: the last p with col_ptr[p] <= cb
+    while (hi - p0 > 1) {
+      const int32_t mid = p0 + (hi - p0) / 2;
+      if (col_ptr[mid] <= cb)
+        p0 = mid;
+      else
+        hi = mid;
+    }
+    for (int i = lane; i < kMarkChunk; i += 32) s_row[mark_slot(i)] = -1;
+    __syncwarp();
+    if (lane == 0) s_row[0] = p0;  // rows after p0 start after cb
+    __syncwarp();
+    for (int32_t r0 = p0 + 1; r0 < n; r0 += 32) {  // starts do not decrease: stop at the first batch past the chunk
+      const int32_t r = r0 + lane;
+      const int64_t st = r < n ? (int64_t)col_ptr[r] : m;
+      const bool in = r < n && st < cb + len;
+      if (in) atomicMax(&s_row[mark_slot((int)(st - cb))], r);
+      if (!__shfl_sync(0xffffffffu, in, 31)) break;
+    }
+    __syncwarp();
+    // running maximum: lane l owns positions 32l .. 32l + 31
+    int32_t mx = -1;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) mx = max(mx, s_row[mark_slot(32 * lane + i)]);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, mx, o);
+      if (lane >= o) mx = max(mx, y);
+    }
+    int32_t run = __shfl_up_sync(0xffffffffu, mx, 1);
+    if (lane == 0) run = -1;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+      const int k = mark_slot(32 * lane + i);
+      run = max(run, s_row[k]);
+      s_row[k] = run;
+    }
+    __syncwarp();
+    if (len == kMarkChunk) {
+#pragma unroll 8
+      for (int i = lane; i < kMarkChunk; i += 32) f(cb + i, s_row[mark_slot(i)]);
+    } else {
+      for (int i = lane; i < len; i += 32) f(cb + i, s_row[mark_slot(i)]);
+    }
+    __syncwarp();
+  }
+}
+
 __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
