@@ -716,6 +716,15 @@ static int grid_for(int64_t items, int per_sm = 8) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((items + kThreads - 1) / kThreads, (int64_t)num_sms() * per_sm));
 }
 
+// The blocks of a kThreads-thread kernel that fit on the device at once (for
+// kernels that deal their work out statically over the whole grid).
+template <typename K>
+static int resident_grid(K kernel) {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, 0);
+  return num_sms() * std::max(b, 1);
+}
+
 // Sorted unique-or-not keys (length m_keys) -> CSC arrays; returns m.
 // degree_from_raw: outdeg already holds each source's count of non-loop keys
 // (duplicates included), and the de-duplication subtracts the duplicates;
@@ -755,9 +764,11 @@ static int64_t keys_to_csc(uint64_t* keys, uint64_t* alt, int64_t m_keys, int b,
 }
 
 // Keys (src << b | dst) of every edge of a CSC, in CSC order.
-__global__ void transpose_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
-                                      int32_t n, int b, uint64_t* __restrict__ keys) {
-  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
+__global__ void __launch_bounds__(kThreads) transpose_keys_kernel(const int32_t* __restrict__ col_ptr,
+                                                                  const int32_t* __restrict__ row_idx, int32_t n,
+                                                                  int b, uint64_t* __restrict__ keys) {
+  __shared__ int32_t s_rows[kWarps][kMarkStride];
+  for_each_edge_with_row_marked(col_ptr, n, s_rows[threadIdx.x >> 5], [&](int64_t e, int32_t p) {
     keys[e] = ((uint64_t)(uint32_t)row_idx[e] << b) | (uint64_t)p;
   });
 }
@@ -973,7 +984,8 @@ gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s) {
     if (g->m > 0) {
       uint64_t* keys = (uint64_t*)tmp.get((size_t)g->m * 8);
       uint64_t* alt = (uint64_t*)tmp.get((size_t)g->m * 8);
-      transpose_keys_kernel<<<grid_for(n), kThreads, 0, s>>>(g->col_ptr, g->row_idx, n, b, keys);
+      transpose_keys_kernel<<<resident_grid(transpose_keys_kernel), kThreads, 0, s>>>(g->col_ptr, g->row_idx, n,
+                                                                                     b, keys);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       m = keys_to_csc(keys, alt, g->m, b, n, nullptr, t->col_ptr, t->row_idx, t->outdeg, derr, tmp, s);
@@ -1000,10 +1012,12 @@ gpr_graph* build_transposed(const gpr_graph* g, cudaStream_t s) {
 }
 
 // Keys (caller src << b | caller dst) of every edge.
-__global__ void caller_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
-                                   const int32_t* __restrict__ new2old, int32_t n, int b,
-                                   uint64_t* __restrict__ keys) {
-  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
+__global__ void __launch_bounds__(kThreads) caller_keys_kernel(const int32_t* __restrict__ col_ptr,
+                                                               const int32_t* __restrict__ row_idx,
+                                                               const int32_t* __restrict__ new2old, int32_t n, int b,
+                                                               uint64_t* __restrict__ keys) {
+  __shared__ int32_t s_rows[kWarps][kMarkStride];
+  for_each_edge_with_row_marked(col_ptr, n, s_rows[threadIdx.x >> 5], [&](int64_t e, int32_t p) {
     keys[e] = ((uint64_t)(uint32_t)new2old[row_idx[e]] << b) | (uint64_t)(uint32_t)new2old[p];
   });
 }
@@ -1026,7 +1040,8 @@ void build_caller_out_adjacency(const gpr_graph* g, cudaStream_t s, int32_t** ou
     if (g->m > 0) {
       uint64_t* keys = (uint64_t*)tmp.get((size_t)g->m * 8);
       uint64_t* alt = (uint64_t*)tmp.get((size_t)g->m * 8);
-      caller_keys_kernel<<<grid_for(n), kThreads, 0, s>>>(g->col_ptr, g->row_idx, g->plan.new2old, n, b, keys);
+      caller_keys_kernel<<<resident_grid(caller_keys_kernel), kThreads, 0, s>>>(g->col_ptr, g->row_idx,
+                                                                               g->plan.new2old, n, b, keys);
       GPR_CUDA(cudaGetLastError());
       count_launches(1);
       m = keys_to_csc(keys, alt, g->m, b, n, nullptr, ptr, adj, indeg, derr, tmp, s);
@@ -1067,9 +1082,11 @@ __global__ void check_ids_kernel(const int32_t* __restrict__ src, const int32_t*
 }
 
 // key = row << b | source for every edge of a CSC, in CSC (= key) order.
-__global__ void own_keys_kernel(const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx, int32_t n,
-                                int b, uint64_t* __restrict__ keys) {
-  for_each_edge_with_row(col_ptr, n, [&](int32_t e, int32_t p) {
+__global__ void __launch_bounds__(kThreads) own_keys_kernel(const int32_t* __restrict__ col_ptr,
+                                                            const int32_t* __restrict__ row_idx, int32_t n, int b,
+                                                            uint64_t* __restrict__ keys) {
+  __shared__ int32_t s_rows[kWarps][kMarkStride];
+  for_each_edge_with_row_marked(col_ptr, n, s_rows[threadIdx.x >> 5], [&](int64_t e, int32_t p) {
     keys[e] = ((uint64_t)p << b) | (uint64_t)(uint32_t)row_idx[e];
   });
 }
@@ -1275,7 +1292,7 @@ gpr_status update_graph(gpr_graph* g, const int32_t* ins_src, const int32_t* ins
     int32_t* kpos = (int32_t*)tmp.get((size_t)std::max<int64_t>(m, 1) * 4);
     int64_t kept = 0;
     if (m > 0) {
-      own_keys_kernel<<<grid_for(n), kThreads, 0, s>>>(g->col_ptr, g->row_idx, n, b, keys);
+      own_keys_kernel<<<resident_grid(own_keys_kernel), kThreads, 0, s>>>(g->col_ptr, g->row_idx, n, b, keys);
       keep_kernel<<<grid_for(m), kThreads, 0, s>>>(keys, m, del, nd, keep);
       const int64_t nt = (m + kScanTile - 1) / kScanTile;
       int64_t* sums = (int64_t*)tmp.get((size_t)nt * 8 + 8);

@@ -196,53 +196,6 @@ void pagerank_work_free(PagerankWork* w);
 
 // ---- device helpers -----------------------------------------------------
 
-// Calls f(e, p) for every edge e of a CSC (rows [0, n), m = col_ptr[n]
-// edges), p the row holding it.  Warps take chunks of 4,096 consecutive
-// edges, so long rows are shared out like any others; a chunk's first row is
-// found by binary search, then each batch of 32 edges finds its rows in a
-// window of 32 row starts (one per lane) by a five-step search over
-// shuffles, moving the window on past rows the batch has left behind.
-// Every lane of the block must call it (it uses full-warp shuffles).
-constexpr int64_t kEdgeChunk = 4096;
-template <typename F>
-__device__ __forceinline__ void for_each_edge_with_row(const int32_t* __restrict__ col_ptr, int32_t n, F f) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t m = col_ptr[n];
-  for (int64_t cb = warp * kEdgeChunk; cb < m; cb += nwarps * kEdgeChunk) {
-    const int64_t ce = cb + kEdgeChunk < m ? cb + kEdgeChunk : m;
-    int32_t p = 0, hi = n;  // the row of edge cb: col_ptr[p] <= cb < col_ptr[hi]
-    while (hi - p > 1) {
-      const int32_t mid = p + (hi - p) / 2;
-      if (col_ptr[mid] <= cb)
-        p = mid;
-      else
-        hi = mid;
-    }
-    for (int64_t e0 = cb; e0 < ce; e0 += 32) {
-      const int64_t e = e0 + lane;
-      const bool live = e < ce;
-      int32_t row = -1;
-      for (;;) {  // rows only grow, so the window moves forward; ends within (rows passed) / 32 steps
-        const int32_t start = col_ptr[p + lane < n ? p + lane : n];
-        const int32_t wend = col_ptr[p + 32 < n ? p + 32 : n];
-        int q = 0;  // the last row start <= e in the window: starts do not decrease
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int32_t sv = __shfl_sync(0xffffffffu, start, q + step);
-          if (sv <= e) q += step;
-        }
-        if (live && row < 0 && e < wend) row = p + q;
-        if (!__any_sync(0xffffffffu, live && row < 0)) break;
-        p += 32;
-      }
-      if (live) f(e, row);
-      const int32_t last = __shfl_sync(0xffffffffu, row, 31);  // the batch's last row (or -1 at a chunk's end)
-      if (last >= 0) p = last;
-    }
-  }
-}
 // f(e, p) for every edge e of the CSC with its row p, through row marks in
 // shared memory: a warp takes kMarkChunk consecutive edges (the warps of the
 // grid take consecutive chunks, so the streams stay close together), marks
