@@ -974,6 +974,7 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
     // at most 1, within the fixed-point range of the blocked sums
     Choice bc{kSchedBlocked, 15, 14, default_unit(g)};
     if (w->tuned && w->choice.sched == kSchedBlocked) bc = w->choice;
+    env_block_shape(&bc);
     bool blocked = (flags & GPR_SPMV_BLOCKED) || (!(flags & GPR_SPMV_PULL) && g->m >= kTuneMinEdges);
     blocked = blocked && blocked_eligible(g, bc.sb, bc.wb) && (kind == 0 || blocked_eligible(t, bc.sb, bc.wb));
     if (blocked) {
