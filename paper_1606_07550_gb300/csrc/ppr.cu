@@ -1144,16 +1144,11 @@ static gpr_status run_ppr(const gpr_ppr_job* jobs, int32_t num_jobs, int32_t max
       shape[k] = kDefaultShape[k];
       if (members[k].empty()) continue;
       const std::pair<int, int> key(k, (int)dt);
-      bool have = false;
       {
         std::lock_guard<std::mutex> lk(g_ppr_tune_mu);
         auto it = g_ppr_tuned.find(key);
-        if (it != g_ppr_tuned.end()) {
-          shape[k] = it->second;
-          have = true;
-        }
+        if (it != g_ppr_tuned.end()) shape[k] = it->second;
       }
-      (void)have;
       if (tune_all) {
         double ms[4] = {0, 0, 0, 0};
         shape[k] = tune_class(dj, cols, members[k], ncap[k], dt, std::max(1, trial_steps), s, T, ms);
