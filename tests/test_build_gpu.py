@@ -45,6 +45,49 @@ def test_random_coo_bit_exact(torch, n, m_raw, seed):
     build_and_compare(torch, n, src, dst)
 
 
+def test_wide_ids_sort_with_nine_bit_digits(torch):
+    # 2^25 + 3 nodes need 26-bit ids: the (dst, src) keys have 52 bits, sorted
+    # in six passes of 8, 8, 9, 9, 9 and 9 bits, so digits start off byte
+    # boundaries (bits 16, 25, 34, 43); the CSC must still be bit-exact
+    n = (1 << 25) + 3
+    rng = np.random.default_rng(12)
+    src, dst = random_coo_with_dups(rng, n, 1 << 20)
+    src[:1000] = n - 1 - np.arange(1000, dtype=np.int32)  # the highest ids take part
+    build_and_compare(torch, n, src, dst)
+
+
+def test_concurrent_builds_on_two_streams(torch):
+    # builds from two threads at once: one borrows the device's sort scratch,
+    # the other finds it lent and sorts in buffers of its own; both exact
+    from concurrent.futures import ThreadPoolExecutor
+    cases = [(200_000, 3_000_000, 21), (150_000, 2_500_000, 22)]
+    inputs = []
+    for n, m_raw, seed in cases:
+        src, dst = random_coo_with_dups(np.random.default_rng(seed), n, m_raw)
+        inputs.append((n, src, dst, oracle.build_csc(n, src, dst)))
+
+    def run(case):
+        n, src, dst, ref = case
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            s_d, d_d = torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda()
+            stream.synchronize()
+            outs = []
+            for _ in range(3):
+                g = gpr.graph_build(s_d, d_d, n, stream=stream)
+                outs.append(g.export())
+                g.free()
+        return outs, ref
+
+    with ThreadPoolExecutor(2) as ex:
+        results = list(ex.map(run, inputs))
+    for outs, ref in results:
+        for cp, ri, od in outs:
+            np.testing.assert_array_equal(cp, ref.col_ptr)
+            np.testing.assert_array_equal(ri, ref.row_idx)
+            np.testing.assert_array_equal(od, ref.outdeg)
+
+
 def test_host_pointers(torch):
     rng = np.random.default_rng(11)
     src, dst = random_coo_with_dups(rng, 3000, 20_000)
