@@ -972,7 +972,14 @@ gpr_status run_centrality(gpr_graph* g, int kind, int32_t iters, float* out_x, f
     // the blocked schedule (unit weights: c = x) when asked for, or on a large
     // graph; vectors are L1-normalised between products, so every row sum is
     // at most 1, within the fixed-point range of the blocked sums
+    // The layout's shape is the one PageRank uses on this graph: its
+    // autotuner's choice (tuned now if this shape has not been), the products
+    // being PageRank's step kernels with unit weights.
     Choice bc{kSchedBlocked, 15, 14, default_unit(g)};
+    if (!(flags & GPR_SPMV_PULL) && g->m >= kTuneMinEdges) {
+      const Choice ch = pick(g, w, 0, GPR_FP32, s);
+      if (ch.sched == kSchedBlocked) bc = ch;
+    }
     if (w->tuned && w->choice.sched == kSchedBlocked) bc = w->choice;
     env_block_shape(&bc);
     bool blocked = (flags & GPR_SPMV_BLOCKED) || (!(flags & GPR_SPMV_PULL) && g->m >= kTuneMinEdges);
