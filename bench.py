@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpr", "reference"], default="gpr")
-    ap.add_argument("--workload", choices=["rmat25", "rmat-lj", "er10k", "batched", "serve", "hits", "wcc", "dynamic",
+    ap.add_argument("--workload", choices=["rmat25", "rmat23", "rmat-lj", "er10k", "batched", "serve", "hits", "wcc", "dynamic",
                                            "target"],
                     default="rmat25")
     ap.add_argument("--graphs", type=int, default=4096, help="batched: number of graphs")
@@ -78,7 +78,8 @@ def rmat_spec(scale):
 
 def workload(name):
     from gen import workloads
-    return {"rmat25": workloads.RMAT_25, "rmat-lj": workloads.RMAT_LJ, "er10k": workloads.ER_10K}[name]
+    return {"rmat25": workloads.RMAT_25, "rmat23": workloads.RMAT_23, "rmat-lj": workloads.RMAT_LJ,
+            "er10k": workloads.ER_10K}[name]
 
 
 # sources of the kernels a recorded DRAM-traffic figure depends on (the
@@ -257,9 +258,9 @@ def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
         return
-    if args.workload not in ("rmat25", "rmat-lj", "er10k"):
+    if args.workload not in ("rmat25", "rmat23", "rmat-lj", "er10k"):
         print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on the PageRank "
-                                                             "workloads only (rmat25, rmat-lj, er10k)"}), flush=True)
+                                                             "workloads only (rmat25, rmat23, rmat-lj, er10k)"}), flush=True)
         return
     spec = workload(args.workload)
     scale = min(args.cpu_sample_scale - 1, spec.scale)
@@ -469,8 +470,9 @@ def run_gpr(args, world, rank, local):
             "workload": spec.name, "n": n, "m_raw": m_raw, "m": m, "iters": iters, "damping": DAMPING,
             "step": "graph_build (COO resident in HBM) + PageRank iterations + rank write-back",
             "value_counts": "m * iters / (build + iterate) per step",
-            "l2": "inputs larger than L2 (COO 8 GiB, CSC 4 GiB per replica)" if m_raw > (1 << 25) else
-                  "small graph: L2-resident (launch-bound)",
+            "l2": (f"inputs larger than L2 (COO {8 * m_raw / 2**30:.3g} GiB, CSC {4 * m / 2**30:.3g} GiB per replica)"
+                   if m_raw > (1 << 25) else
+                   "small graph: L2-resident (launch-bound)"),
             "parallelism": f"replicas x{world}",
         },
         "build_ms": t_build, "iterate_ms": t_iter, "pagerank_gteps": pr_gteps,

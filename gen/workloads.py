@@ -40,6 +40,10 @@ ER_10K = GraphSpec("er-10k-100k", "er", 10_000, 100_000, seed=1, iters=50)
 RMAT_LJ = GraphSpec("rmat-lj-4.8m-69m", "rmat", 4_800_000, 69_000_000, seed=2, iters=100)
 # Twitter2010-scale R-MAT: scale 25, edge factor 32, 100 iterations.
 RMAT_25 = GraphSpec("rmat-s25-ef32", "rmat", 1 << 25, 1 << 30, seed=3, iters=100)
+# The same recipe at scale 23 (a quarter of the edges): the case the step
+# kernels' DRAM traffic is measured on, larger than L2 and small enough for
+# multi-pass counter captures.
+RMAT_23 = GraphSpec("rmat-s23-ef32", "rmat", 1 << 23, 1 << 28, seed=3, iters=100)
 
 
 def batched_specs(num_graphs: int = 4096, n_lo: float = 1e3, n_hi: float = 2e5,
